@@ -1,0 +1,44 @@
+"""Seeded input generator: determinism, element balance, coverage and state sanity."""
+import numpy as np
+import pytest
+
+from paper_2312_05800_gb300 import synth
+
+
+@pytest.mark.parametrize("name,N,R,ntroe,n3b", [("c1", 9, 20, 0, 4), ("c2", 30, 180, 18, 27), ("c5", 53, 325, 33, 49)])
+def test_mechanism_shape_and_balance(name, N, R, ntroe, n3b):
+    m = synth.get_mech(name)
+    assert (m.N, m.R) == (N, R)
+    assert int((m.rtype == 2).sum()) == ntroe and int((m.rtype == 1).sum()) == n3b
+    nr, npd = m.nu()
+    assert np.all((npd - nr) @ m.elem == 0)
+    used = (nr + npd).sum(axis=0) > 0
+    assert used.sum() == N - 1 and not used[m.bath]
+    fresh = synth.make_mech(name, N, R, ntroe, n3b, m.elements, {"c1": 1001, "c2": 1002, "c5": 1005}[name])
+    assert synth.mech_to_bytes(fresh) == synth.mech_to_bytes(m)
+
+
+def test_states_sum_to_one_and_are_seeded():
+    m = synth.mech_c2()
+    a = synth.states_profiles(m, 1000, 9)
+    b = synth.states_profiles(m, 1000, 9)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    T, p, Y = a
+    assert np.abs(Y[:, :1000].sum(axis=0) - 1).max() < 1e-14
+    assert T[:1000].min() >= 300.0 and T[:1000].max() < 2800.0
+    assert np.all(Y[:, :1000] > 0)
+    # the bath species has the largest mean mass fraction
+    assert int(np.argmax(Y[:, :1000].mean(axis=1))) == m.bath
+    m1 = synth.mech_c1()
+    T, p, Y = synth.states_dirichlet(m1, 4096, 2001)
+    assert T.shape[0] % 4 == 0 and np.all(p[:4096] == synth.P_ATM)
+
+
+def test_perturbation_fraction():
+    m = synth.mech_c2()
+    T, p, Y = synth.states_profiles(m, 5000, 3)
+    T2, Y2, mask = synth.perturb_off_manifold(T, Y, 5000, 0.02, 4)
+    assert mask.sum() == 100
+    assert np.allclose(np.abs(T2[mask] - T[mask])[T[mask] > 600], 300.0)
+    assert np.abs(Y2[:, :5000].sum(axis=0) - 1).max() < 1e-14
