@@ -1,0 +1,163 @@
+/*
+ * chemgb.h -- C ABI of the GB300 (sm_103a) per-cell chemistry and properties
+ * library (libchemgb.so).
+ *
+ * The operation behind every entry point is the per-cell step of the paper's
+ * GPU-ANN LES method (Zhang et al., arXiv 2312.05800): given the thermochemical
+ * state (T, p, Y) of every cell, evaluate the thermal and transport properties
+ * (Sec. 2) and advance the composition over one flow step dt (Sec. 3.1: the
+ * reaction ODEs integrated over dt = 1 us; Sec. 3.2: the network maps
+ * x(t) = {T, p, F(Y)} to u*(t) = Y(t + dt) - Y(t)).
+ *
+ * Conventions shared by all entry points
+ *  - Cell data are structure-of-arrays with a leading dimension ld >= ncells:
+ *    T[i], p[i] for cell i and Y[k * ld + i] for species k. ld must be a
+ *    multiple of 4 (16-byte rows for FP32, 32-byte for FP64) and every array
+ *    pointer 16-byte aligned; otherwise the call returns CHEM_EINVAL.
+ *  - Unless an argument says "host", array pointers are DEVICE pointers owned
+ *    by the caller; the library never frees them. Mechanism and network
+ *    handles are owned by the library (create / free pairs).
+ *  - Calls are asynchronous on the given CUDA stream (0 = legacy default
+ *    stream). Results are valid once the stream reaches that point.
+ *  - Units are SI: K, Pa, kg, m, s, mol, J.
+ *  - Return codes: CHEM_OK (0) on success; a negative code otherwise, with a
+ *    message available from chem_last_error() on the calling thread. Errors
+ *    that belong to one cell (a step limit hit, a non-finite state) never fail
+ *    the call: they are reported in the per-cell status array.
+ *  - No host fallback exists: on a machine without an sm_103 device every
+ *    compute call returns CHEM_EUNSUPPORTED.
+ */
+#ifndef CHEMGB_H
+#define CHEMGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *chem_stream_t; /* a cudaStream_t */
+
+enum {
+    CHEM_OK = 0,
+    CHEM_EINVAL = -1,      /* null pointer, bad size, misalignment, mismatched handles */
+    CHEM_ECUDA = -2,       /* a CUDA runtime error (launch, allocation at load time) */
+    CHEM_EUNSUPPORTED = -3,/* no sm_103 device, or a feature not built */
+    CHEM_EIO = -4          /* a file could not be read or has a bad format */
+};
+
+/* per-cell status codes written by the stepping entry points */
+enum {
+    CHEM_CELL_OK = 0,          /* integrated (stiff) or predicted (ANN) */
+    CHEM_CELL_FALLBACK = 1,    /* ANN step: routed to the stiff integrator, which succeeded */
+    CHEM_CELL_MAXSTEPS = 2,    /* stiff: step limit reached before dt */
+    CHEM_CELL_UNDERFLOW = 3,   /* stiff: step size fell below 1e-20 dt */
+    CHEM_CELL_NONFINITE = 4    /* a non-finite state or right-hand side */
+};
+
+enum { CHEM_F32 = 0, CHEM_F64 = 1 };
+
+/* ---------------------------------------------------------------------------
+ * Mechanism
+ * ---------------------------------------------------------------------------
+ * A reaction mechanism with NASA-7 thermodynamics, transport fits and reaction
+ * data (the paper's chemistry, Sec. 3.1; its own mechanism is DRM19, which any
+ * file in this format can stand in for).
+ *
+ * File format (little-endian, packed, in this order):
+ *   char magic[8] = "CHMECH01"
+ *   int32 N, R, E, bath                     species, reactions, elements, bath index
+ *   float64 P_std, T_lo, T_mid, T_hi        standard pressure (Pa), NASA ranges (K)
+ *   float64 W[N]                            molar masses, kg/mol
+ *   float64 nasa_lo[N][7], nasa_hi[N][7]    NASA-7 rows; T >= T_mid uses nasa_hi
+ *   int32   elem[N][E]                      atom counts
+ *   float64 sigma[N], eps_k[N]              Lennard-Jones data (informational)
+ *   float64 visc_fit[N][5]                  ln(mu_k / Pa s) = sum_n c_n x^n, x = ln(T / 1000 K)
+ *   float64 diff_fit[N][N][5]               g_jk = p T^-1.5 / D_jk = sum_n c_n x^n (g_kk = 0)
+ *   int32   rtype[R]                        0 elementary, 1 three-body, 2 Troe fall-off
+ *   int32   reac[R][3], prod[R][3]          species indices, -1 padded, repeated for nu = 2
+ *   float64 A[R], beta[R], Ea[R]            k = A T^beta exp(-Ea / RT) (k_inf for fall-off), SI
+ *   float64 A0[R], beta0[R], Ea0[R]         low-pressure limit (fall-off only)
+ *   float64 troe[R][4]                      a, T***, T*, T**
+ *   float64 eff[R][N]                       third-body efficiencies
+ * Limits: 1 <= N <= 64, 1 <= R <= 4096.
+ */
+typedef struct chem_mech chem_mech;
+
+/* Reads a mechanism file (host path) and uploads its tables to the current
+ * device. *out receives a library-owned handle. Returns CHEM_EIO on a bad
+ * file, CHEM_EINVAL on a null argument or out-of-range sizes. */
+int chem_mech_load(const char *path, chem_mech **out);
+/* Same from an in-memory image of the file format above (host bytes). */
+int chem_mech_load_bytes(const void *data, size_t nbytes, chem_mech **out);
+/* Frees the handle and its device tables (synchronises the device). */
+int chem_mech_free(chem_mech *mech);
+/* Number of species / reactions of a loaded mechanism (-1 on a null handle). */
+int chem_mech_nspecies(const chem_mech *mech);
+int chem_mech_nreactions(const chem_mech *mech);
+
+/* ---------------------------------------------------------------------------
+ * props_eval -- thermal and transport properties of every cell
+ * ---------------------------------------------------------------------------
+ * Sec. 2: thermal and transport properties are computed on the GPU each step;
+ * Sec. 3.1 names the Hirschfelder-Curtiss mixture-averaged transport model.
+ * Per cell: NASA-7 mixture cp (J/kg/K) and h (J/kg); Wilke mixture viscosity
+ * mu (Pa s); the conductivity lambda (W/m/K) with Eucken species values and
+ * the same Wilke weights; and the mixture-averaged diffusion coefficients
+ * D_k = (1 - Y_k) / sum_{j != k} X_j / D_jk (m^2/s), D_jk from the fits.
+ *
+ * dtype = CHEM_F32 (float arrays) or CHEM_F64 (double arrays) for all of
+ * T, p, Y (inputs, [ld], [ld], [N][ld]) and cp, h, mu, lambda ([ld]) and
+ * Dk ([N][ld]) (outputs). Any of the outputs may be NULL to skip it (mu,
+ * lambda and Dk together select the transport part). ncells == 0 is a no-op.
+ */
+int props_eval(const chem_mech *mech, int64_t ncells, int64_t ld, int dtype,
+               const void *T, const void *p, const void *Y,
+               void *cp, void *h, void *mu, void *lambda, void *Dk, chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * chem_step_stiff -- the plain method: stiff reactor integration over dt
+ * ---------------------------------------------------------------------------
+ * Sec. 3.1 integrates every composition over dt = 1 us with CVODE; Sec. 4.2
+ * calls this direct integration "CPU-DI". Here each cell is an adiabatic
+ * constant-pressure reactor, dY_k/dt = W_k wdot_k / rho and
+ * dT/dt = -sum_k H_k wdot_k / (rho cp), integrated in FP64 by the embedded
+ * L-stable Rosenbrock method Rodas3 (Sandu et al. 1997, 4 stages, order 3(2))
+ * with an analytic dense Jacobian, LU with partial pivoting, and the
+ * step-size control described by chem_ode_opts.
+ *
+ * T [ld] and Y [N][ld] (double, device) are updated in place; p [ld] is read.
+ * status [ld] (int32, device) receives a CHEM_CELL_* code and nsteps [ld]
+ * (int32, device, may be NULL) the number of attempted steps. opts is a host
+ * pointer (NULL = defaults below).
+ *
+ * Scratch: a work-queue counter inside the mechanism handle; two calls with
+ * the same handle must not overlap on the device (stream-order them).
+ */
+typedef struct {
+    double rtol;      /* relative tolerance (default 1e-6) */
+    double atol_Y;    /* absolute tolerance on mass fractions (default 1e-12) */
+    double atol_T;    /* absolute tolerance on temperature, K (default 1e-6) */
+    double h0;        /* first trial step, s (default 1e-9; clipped to dt) */
+    int32_t max_steps;/* attempted-step limit per cell (default 10000) */
+    int32_t _pad;
+} chem_ode_opts;
+
+/* Fills *o with the defaults listed above. */
+void chem_ode_opts_default(chem_ode_opts *o);
+
+int chem_step_stiff(const chem_mech *mech, int64_t ncells, int64_t ld, double dt, const chem_ode_opts *opts,
+                    double *T, const double *p, double *Y, int32_t *status, int32_t *nsteps,
+                    chem_stream_t stream);
+
+/* Last error message of the calling thread ("" if none). */
+const char *chem_last_error(void);
+
+/* Library build string (compiler, target architecture). */
+const char *chem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CHEMGB_H */

@@ -1,0 +1,78 @@
+// internal.cuh -- device-side mechanism layout and helpers shared by the
+// library's translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "chemgb.h"
+
+#define CHEMGB_STR2(x) #x
+#define CHEMGB_STR(x) CHEMGB_STR2(x)
+
+namespace chemgb {
+
+constexpr double kR = 8.314462618;        // J/mol/K
+constexpr int kMaxSpecies = 64;
+constexpr int kMaxReactions = 4096;
+
+// Device tables of one mechanism. Every pointer is device memory owned by the
+// chem_mech handle. Square per-pair tables are stored row k, column j with a
+// padded row length Np (a multiple of 4) so that rows start on 16 bytes.
+template <typename real>
+struct PropTables {
+    const real *invW;      // [N] 1 / W_k
+    const real *nasa_cp;   // [2][N][5] cp/R Horner coefficients, range 0 = low, 1 = high
+    const real *nasa_h;    // [2][N][6] H/RT: a1, a2/2, a3/3, a4/4, a5/5, a6
+    const real *visc;      // [N][5] ln mu_k polynomial in x = ln(T/1000)
+    const real *wilke;     // [3][N][Np] T0 = c_kj, T1 = 2 c_kj w_jk, T2 = c_kj w_jk^2
+    const real *diff;      // [N][Np][5]... stored as [5][N][Np]: coefficient n of g_jk at (k, j)
+};
+
+struct DevMech {
+    int N, R, Np, n_tb;
+    double P_std, T_mid;
+    PropTables<float> f32;
+    PropTables<double> f64;
+    // FP64 kinetics
+    const double *W;        // [N]
+    const double *nasa;     // [2][N][7] raw NASA-7 rows (low, high)
+    const int *rtype;       // [R]
+    const int *reac;        // [R][3]
+    const int *prod;        // [R][3]
+    const double *lnA;      // [R]
+    const double *beta;     // [R]
+    const double *EaR;      // [R] Ea / R (K)
+    const double *lnA0;     // [R]
+    const double *beta0;    // [R]
+    const double *Ea0R;     // [R]
+    const double *troe;     // [R][4]
+    const int *tb_row;      // [R] row in eff, or -1
+    const double *eff;      // [n_tb][N]
+    const int *inc_ptr;     // [N+1] species -> reactions incidence (CSR)
+    const int2 *inc;        // (reaction, signed nu)
+    const int *dnu;         // [R] sum of nu over the reaction
+    unsigned int *counters; // [kNumCounters] work-queue counters (scratch)
+};
+
+constexpr int kNumCounters = 8;
+
+}  // namespace chemgb
+
+struct chem_mech {
+    int N, R, E, bath;
+    double P_std, T_lo, T_mid, T_hi;
+    chemgb::DevMech dev;
+    void *blob;            // single device allocation holding every table
+    size_t blob_bytes;
+    int device;
+};
+
+namespace chemgb {
+int set_error(int code, const std::string &msg);
+int check_cuda(cudaError_t e, const char *what);
+bool device_ok(std::string *why);
+inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+}  // namespace chemgb

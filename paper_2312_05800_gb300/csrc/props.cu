@@ -1,0 +1,223 @@
+// props.cu -- props_eval: NASA-7 mixture thermo and mixture-averaged
+// transport for every cell (Sec. 2: thermal and transport properties on the
+// GPU; Sec. 3.1: Hirschfelder-Curtiss mixture-averaged model).
+//
+// One thread per cell, persistent grid-stride loop. Cell data are SoA, so a
+// warp's loads of T, p and each Y_k row are 128-byte coalesced. The per-pair
+// tables (Wilke weights, binary-resistance fits) are read with uniform
+// addresses (one broadcast per warp) through the read-only cache. The
+// per-cell vectors X_j, X_j / r_j and X_j / r_j^2 (r = sqrt(mu)) live in
+// registers: the inner species loop is unrolled to a compile-time bound NMAX.
+//
+// Wilke: sum_j X_j Phi_kj with Phi_kj = c_kj (1 + w_jk r_k / r_j)^2 is
+// evaluated as T0.X + r_k (T1.(X/r) + r_k T2.(X/r^2)) with constant tables
+// T0 = c, T1 = 2 c w, T2 = c w^2 (expanded once at load time).
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace chemgb {
+namespace {
+
+template <typename real>
+__device__ __forceinline__ void load4(const real *p, real &a, real &b, real &c, real &d) {
+    if constexpr (sizeof(real) == 4) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        a = v.x; b = v.y; c = v.z; d = v.w;
+    } else {
+        double2 v0 = __ldg(reinterpret_cast<const double2 *>(p));
+        double2 v1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+    }
+}
+
+template <typename real, int NMAX>
+__global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, PropTables<real> tb, int64_t ncells,
+                                                    int64_t ld, const real *__restrict__ Tg,
+                                                    const real *__restrict__ pg, const real *__restrict__ Yg,
+                                                    real *__restrict__ cpg, real *__restrict__ hg,
+                                                    real *__restrict__ mug, real *__restrict__ lamg,
+                                                    real *__restrict__ Dkg) {
+    const real R = real(kR);
+    const bool transport = (mug != nullptr) || (lamg != nullptr) || (Dkg != nullptr);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
+        const real T = Tg[i];
+        const real p = pg[i];
+        const int rng = (T >= T_mid) ? 1 : 0;
+        const real x = log(T) - real(6.907755278982137);   // ln(T / 1000)
+        real S = 0, cpm = 0, hm = 0;
+        real X[NMAX], xr[NMAX], xr2[NMAX];
+        // pass 1: thermo sums; keep Y_k / W_k
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < N) {
+                const real y = Yg[(int64_t)k * ld + i];
+                const real iw = __ldg(tb.invW + k);
+                const real *a = tb.nasa_cp + (rng * N + k) * 5;
+                const real *b = tb.nasa_h + (rng * N + k) * 6;
+                real cpR = __ldg(a + 4);
+                cpR = fma(cpR, T, __ldg(a + 3));
+                cpR = fma(cpR, T, __ldg(a + 2));
+                cpR = fma(cpR, T, __ldg(a + 1));
+                cpR = fma(cpR, T, __ldg(a + 0));
+                real hR = __ldg(b + 4);
+                hR = fma(hR, T, __ldg(b + 3));
+                hR = fma(hR, T, __ldg(b + 2));
+                hR = fma(hR, T, __ldg(b + 1));
+                hR = fma(hR, T, __ldg(b + 0));
+                hR = hR + __ldg(b + 5) / T;                      // H_k / (R T)
+                const real yw = y * iw;
+                S += yw;
+                cpm = fma(yw, cpR, cpm);
+                hm = fma(yw, hR, hm);
+                X[k] = yw;
+            } else {
+                X[k] = 0;
+            }
+        }
+        if (cpg) cpg[i] = cpm * R;
+        if (hg) hg[i] = hm * R * T;
+        if (!transport) continue;
+        const real Wbar = real(1) / S;
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < N) {
+                const real *c = tb.visc + k * 5;
+                real lm = __ldg(c + 4);
+                lm = fma(lm, x, __ldg(c + 3));
+                lm = fma(lm, x, __ldg(c + 2));
+                lm = fma(lm, x, __ldg(c + 1));
+                lm = fma(lm, x, __ldg(c + 0));
+                const real ir = exp(real(-0.5) * lm);              // 1 / sqrt(mu_k)
+                X[k] = X[k] * Wbar;
+                xr[k] = X[k] * ir;
+                xr2[k] = xr[k] * ir;
+            } else {
+                xr[k] = 0;
+                xr2[k] = 0;
+            }
+        }
+        const real T15 = T * sqrt(T);
+        real mu = 0, lam = 0;
+        for (int k = 0; k < N; ++k) {
+            // per-species values, recomputed from the tables (no dynamic register indexing)
+            const real y = Yg[(int64_t)k * ld + i];
+            const real iw = __ldg(tb.invW + k);
+            const real Xk = y * iw * Wbar;
+            const real *c = tb.visc + k * 5;
+            real lm = __ldg(c + 4);
+            lm = fma(lm, x, __ldg(c + 3));
+            lm = fma(lm, x, __ldg(c + 2));
+            lm = fma(lm, x, __ldg(c + 1));
+            lm = fma(lm, x, __ldg(c + 0));
+            const real muk = exp(lm);
+            const real rk = sqrt(muk);
+            const real *a = tb.nasa_cp + (rng * N + k) * 5;
+            real cpR = __ldg(a + 4);
+            cpR = fma(cpR, T, __ldg(a + 3));
+            cpR = fma(cpR, T, __ldg(a + 2));
+            cpR = fma(cpR, T, __ldg(a + 1));
+            cpR = fma(cpR, T, __ldg(a + 0));
+            const real lamk = muk * (cpR + real(1.25)) * R * iw;   // Eucken
+            const real *t0 = tb.wilke + (0 * N + k) * Np;
+            const real *t1 = tb.wilke + (1 * N + k) * Np;
+            const real *t2 = tb.wilke + (2 * N + k) * Np;
+            const real *d0 = tb.diff + (0 * N + k) * Np;
+            const real *d1 = tb.diff + (1 * N + k) * Np;
+            const real *d2 = tb.diff + (2 * N + k) * Np;
+            const real *d3 = tb.diff + (3 * N + k) * Np;
+            const real *d4 = tb.diff + (4 * N + k) * Np;
+            real a0 = 0, a1 = 0, a2 = 0, ds = 0, gs = 0;
+#pragma unroll
+            for (int j4 = 0; j4 < NMAX; j4 += 4) {
+                if (j4 < N) {
+                    real w0[4], w1[4], w2[4], g0[4], g1[4], g2[4], g3[4], g4[4];
+                    load4(t0 + j4, w0[0], w0[1], w0[2], w0[3]);
+                    load4(t1 + j4, w1[0], w1[1], w1[2], w1[3]);
+                    load4(t2 + j4, w2[0], w2[1], w2[2], w2[3]);
+                    load4(d0 + j4, g0[0], g0[1], g0[2], g0[3]);
+                    load4(d1 + j4, g1[0], g1[1], g1[2], g1[3]);
+                    load4(d2 + j4, g2[0], g2[1], g2[2], g2[3]);
+                    load4(d3 + j4, g3[0], g3[1], g3[2], g3[3]);
+                    load4(d4 + j4, g4[0], g4[1], g4[2], g4[3]);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int j = j4 + u;   // padded columns have zero weights
+                        a0 = fma(w0[u], X[j], a0);
+                        a1 = fma(w1[u], xr[j], a1);
+                        a2 = fma(w2[u], xr2[j], a2);
+                        real g = fma(fma(fma(fma(g4[u], x, g3[u]), x, g2[u]), x, g1[u]), x, g0[u]);
+                        ds = fma(g, X[j], ds);
+                        gs += g;
+                    }
+                }
+            }
+            const real den = fma(rk, fma(rk, a2, a1), a0);
+            mu = fma(Xk, muk / den, mu);
+            lam = fma(Xk, lamk / den, lam);
+            if (Dkg) {
+                real D;
+                if (real(1) - Xk < real(1e-12)) D = T15 / (p * gs / real(N - 1));   // pure species k
+                else D = (real(1) - y) * T15 / (p * ds);
+                Dkg[(int64_t)k * ld + i] = D;
+            }
+        }
+        if (mug) mug[i] = mu;
+        if (lamg) lamg[i] = lam;
+    }
+}
+
+template <typename real, int NMAX>
+int launch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
+                 void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
+    static int max_blocks = 0;
+    if (max_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, props_kernel<real, NMAX>, 128, 0);
+        max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    int64_t need = (ncells + 127) / 128;
+    int blocks = (int)(need < max_blocks ? need : max_blocks);
+    const PropTables<real> &tb = (sizeof(real) == 4) ? *reinterpret_cast<const PropTables<real> *>(&m->dev.f32)
+                                                      : *reinterpret_cast<const PropTables<real> *>(&m->dev.f64);
+    props_kernel<real, NMAX><<<blocks, 128, 0, st>>>(
+        m->N, m->dev.Np, real(m->T_mid), tb, ncells, ld, static_cast<const real *>(T), static_cast<const real *>(p),
+        static_cast<const real *>(Y), static_cast<real *>(cp), static_cast<real *>(h), static_cast<real *>(mu),
+        static_cast<real *>(lam), static_cast<real *>(Dk));
+    return check_cuda(cudaGetLastError(), "props_eval launch");
+}
+
+template <typename real>
+int dispatch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
+                   void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
+    if (m->N <= 16) return launch_props<real, 16>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
+    if (m->N <= 32) return launch_props<real, 32>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
+    return launch_props<real, 64>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
+}
+
+}  // namespace
+}  // namespace chemgb
+
+using namespace chemgb;
+
+extern "C" int props_eval(const chem_mech *m, int64_t ncells, int64_t ld, int dtype, const void *T, const void *p,
+                          const void *Y, void *cp, void *h, void *mu, void *lambda, void *Dk,
+                          chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "props_eval: null mechanism");
+    if (ncells < 0 || ld < ncells || (ld & 3) != 0)
+        return set_error(CHEM_EINVAL, "props_eval: need 0 <= ncells <= ld and ld a multiple of 4");
+    if (dtype != CHEM_F32 && dtype != CHEM_F64) return set_error(CHEM_EINVAL, "props_eval: bad dtype");
+    if (ncells == 0) return CHEM_OK;
+    if (!T || !p || !Y) return set_error(CHEM_EINVAL, "props_eval: null input array");
+    const void *ptrs[] = {T, p, Y, cp, h, mu, lambda, Dk};
+    for (const void *q : ptrs)
+        if (q && !aligned16(q)) return set_error(CHEM_EINVAL, "props_eval: arrays must be 16-byte aligned");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "props_eval: " + why);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (dtype == CHEM_F32) return dispatch_props<float>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
+    return dispatch_props<double>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
+}
