@@ -56,7 +56,11 @@ enum {
     CHEM_CELL_NONFINITE = 4    /* a non-finite state or right-hand side */
 };
 
-enum { CHEM_F32 = 0, CHEM_F64 = 1 };
+enum {
+    CHEM_F32 = 0,        /* float inputs, float arithmetic, float outputs */
+    CHEM_F64 = 1,        /* double inputs, double arithmetic, double outputs */
+    CHEM_F64_IN_F32 = 2  /* double inputs (the stepped FP64 state), float arithmetic, float outputs */
+};
 
 /* ---------------------------------------------------------------------------
  * Mechanism
@@ -109,7 +113,8 @@ int chem_mech_nreactions(const chem_mech *mech);
  *
  * dtype = CHEM_F32 (float arrays) or CHEM_F64 (double arrays) for all of
  * T, p, Y (inputs, [ld], [ld], [N][ld]) and cp, h, mu, lambda ([ld]) and
- * Dk ([N][ld]) (outputs). Any of the outputs may be NULL to skip it (mu,
+ * Dk ([N][ld]) (outputs); CHEM_F64_IN_F32 reads double inputs (the FP64
+ * state the stepping calls update) and computes and writes in float. Any of the outputs may be NULL to skip it (mu,
  * lambda and Dk together select the transport part). ncells == 0 is a no-op.
  */
 int props_eval(const chem_mech *mech, int64_t ncells, int64_t ld, int dtype,

@@ -15,7 +15,7 @@ from typing import Optional
 from . import build as _build
 
 CHEM_OK, CHEM_EINVAL, CHEM_ECUDA, CHEM_EUNSUPPORTED, CHEM_EIO = 0, -1, -2, -3, -4
-CHEM_F32, CHEM_F64 = 0, 1
+CHEM_F32, CHEM_F64, CHEM_F64_IN_F32 = 0, 1, 2
 CELL_OK, CELL_FALLBACK, CELL_MAXSTEPS, CELL_UNDERFLOW, CELL_NONFINITE = 0, 1, 2, 3, 4
 
 _lib = None

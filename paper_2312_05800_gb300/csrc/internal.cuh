@@ -54,6 +54,13 @@ struct DevMech {
     const int *inc_ptr;     // [N+1] species -> reactions incidence (CSR)
     const int2 *inc;        // (reaction, signed nu)
     const int *dnu;         // [R] sum of nu over the reaction
+    // derived FP64 tables of the stiff integrator
+    const double *nasa_s;   // [2][N][6] S/R: a1 (times ln T), a2, a3/2, a4/3, a5/4, a7
+    const double *troe_r;   // [R][4] a, 1/T***, 1/T*, T**
+    const int *rsp;         // [R][6] distinct species of reaction j (first-occurrence order), -1 pad
+    const int *rnu;         // [R][6] their net stoichiometric coefficients
+    const int *tb_list;     // [n_tb] reactions with a third body, ascending
+    double lnPR;            // ln(P_std / R)
     unsigned int *counters; // [kNumCounters] work-queue counters (scratch)
 };
 

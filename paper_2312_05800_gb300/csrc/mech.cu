@@ -215,12 +215,44 @@ extern "C" int chem_mech_load_bytes(const void *data, size_t nbytes, chem_mech *
     inc_ptr[N] = (int)inc.size();
     if (inc.empty()) inc.push_back(make_int2(0, 0));
     std::vector<uint32_t> counters(kNumCounters, 0u);
+    std::vector<double> nasa_s(2 * N * 6), troe_r(4 * R);
+    for (int r = 0; r < 2; ++r)
+        for (int k = 0; k < N; ++k) {
+            const double *a = (r == 0 ? lo.data() : hi.data()) + 7 * k;
+            double *o = nasa_s.data() + (r * N + k) * 6;
+            o[0] = a[0]; o[1] = a[1]; o[2] = a[2] / 2.0; o[3] = a[3] / 3.0; o[4] = a[4] / 4.0; o[5] = a[6];
+        }
+    for (int j = 0; j < R; ++j) {
+        troe_r[4 * j + 0] = troe[4 * j + 0];
+        troe_r[4 * j + 1] = (troe[4 * j + 1] != 0.0) ? 1.0 / troe[4 * j + 1] : 0.0;
+        troe_r[4 * j + 2] = (troe[4 * j + 2] != 0.0) ? 1.0 / troe[4 * j + 2] : 0.0;
+        troe_r[4 * j + 3] = troe[4 * j + 3];
+    }
+    std::vector<int32_t> rsp(6 * R, -1), rnu(6 * R, 0), tb_list;
+    for (int j = 0; j < R; ++j) {
+        int cnt = 0;
+        for (int slot = 0; slot < 6; ++slot) {
+            int sp = slot < 3 ? reac[3 * j + slot] : prod[3 * j + slot - 3];
+            if (sp < 0) continue;
+            bool seen = false;
+            for (int u = 0; u < cnt; ++u) seen |= (rsp[6 * j + u] == sp);
+            if (seen) continue;
+            int nu = 0;
+            for (int i = 0; i < 3; ++i) nu += (prod[3 * j + i] == sp) - (reac[3 * j + i] == sp);
+            rsp[6 * j + cnt] = sp;
+            rnu[6 * j + cnt] = nu;
+            ++cnt;
+        }
+        if (rtype[j] != 0) tb_list.push_back(j);
+    }
+    if (tb_list.empty()) tb_list.push_back(0);
 
     size_t off_W = bb.add(W), off_nasa = bb.add(nasa), off_rtype = bb.add(rtype), off_reac = bb.add(reac),
            off_prod = bb.add(prod), off_lnA = bb.add(lnA), off_beta = bb.add(beta), off_EaR = bb.add(EaR),
            off_lnA0 = bb.add(lnA0), off_beta0 = bb.add(beta0), off_Ea0R = bb.add(Ea0R), off_troe = bb.add(troe),
            off_tb = bb.add(tb_row), off_eff = bb.add(effc), off_incp = bb.add(inc_ptr), off_inc = bb.add(inc),
-           off_dnu = bb.add(dnu), off_cnt = bb.add(counters);
+           off_dnu = bb.add(dnu), off_cnt = bb.add(counters), off_nasa_s = bb.add(nasa_s),
+           off_troe_r = bb.add(troe_r), off_rsp = bb.add(rsp), off_rnu = bb.add(rnu), off_tbl = bb.add(tb_list);
 
     std::string why;
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mech_load: " + why);
@@ -260,6 +292,12 @@ extern "C" int chem_mech_load_bytes(const void *data, size_t nbytes, chem_mech *
     d.inc = reinterpret_cast<const int2 *>(base + off_inc);
     d.dnu = reinterpret_cast<const int *>(base + off_dnu);
     d.counters = reinterpret_cast<unsigned int *>(base + off_cnt);
+    d.nasa_s = reinterpret_cast<const double *>(base + off_nasa_s);
+    d.troe_r = reinterpret_cast<const double *>(base + off_troe_r);
+    d.rsp = reinterpret_cast<const int *>(base + off_rsp);
+    d.rnu = reinterpret_cast<const int *>(base + off_rnu);
+    d.tb_list = reinterpret_cast<const int *>(base + off_tbl);
+    d.lnPR = std::log(th[0] / kR);
     *out = m;
     return CHEM_OK;
 }

@@ -31,10 +31,10 @@ __device__ __forceinline__ void load4(const real *p, real &a, real &b, real &c, 
     }
 }
 
-template <typename real, int NMAX>
+template <typename real, typename in_t, int NMAX>
 __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, PropTables<real> tb, int64_t ncells,
-                                                    int64_t ld, const real *__restrict__ Tg,
-                                                    const real *__restrict__ pg, const real *__restrict__ Yg,
+                                                    int64_t ld, const in_t *__restrict__ Tg,
+                                                    const in_t *__restrict__ pg, const in_t *__restrict__ Yg,
                                                     real *__restrict__ cpg, real *__restrict__ hg,
                                                     real *__restrict__ mug, real *__restrict__ lamg,
                                                     real *__restrict__ Dkg) {
@@ -42,8 +42,8 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
     const bool transport = (mug != nullptr) || (lamg != nullptr) || (Dkg != nullptr);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
-        const real T = Tg[i];
-        const real p = pg[i];
+        const real T = real(Tg[i]);
+        const real p = real(pg[i]);
         const int rng = (T >= T_mid) ? 1 : 0;
         const real x = log(T) - real(6.907755278982137);   // ln(T / 1000)
         real S = 0, cpm = 0, hm = 0;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
             if (k < N) {
-                const real y = Yg[(int64_t)k * ld + i];
+                const real y = real(Yg[(int64_t)k * ld + i]);
                 const real iw = __ldg(tb.invW + k);
                 const real *a = tb.nasa_cp + (rng * N + k) * 5;
                 const real *b = tb.nasa_h + (rng * N + k) * 6;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
         real mu = 0, lam = 0;
         for (int k = 0; k < N; ++k) {
             // per-species values, recomputed from the tables (no dynamic register indexing)
-            const real y = Yg[(int64_t)k * ld + i];
+            const real y = real(Yg[(int64_t)k * ld + i]);
             const real iw = __ldg(tb.invW + k);
             const real Xk = y * iw * Wbar;
             const real *c = tb.visc + k * 5;
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
     }
 }
 
-template <typename real, int NMAX>
+template <typename real, typename in_t, int NMAX>
 int launch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
                  void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
     static int max_blocks = 0;
@@ -176,26 +176,26 @@ int launch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, 
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, props_kernel<real, NMAX>, 128, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, props_kernel<real, in_t, NMAX>, 128, 0);
         max_blocks = sms * (per_sm > 0 ? per_sm : 1);
     }
     int64_t need = (ncells + 127) / 128;
     int blocks = (int)(need < max_blocks ? need : max_blocks);
     const PropTables<real> &tb = (sizeof(real) == 4) ? *reinterpret_cast<const PropTables<real> *>(&m->dev.f32)
                                                       : *reinterpret_cast<const PropTables<real> *>(&m->dev.f64);
-    props_kernel<real, NMAX><<<blocks, 128, 0, st>>>(
-        m->N, m->dev.Np, real(m->T_mid), tb, ncells, ld, static_cast<const real *>(T), static_cast<const real *>(p),
-        static_cast<const real *>(Y), static_cast<real *>(cp), static_cast<real *>(h), static_cast<real *>(mu),
+    props_kernel<real, in_t, NMAX><<<blocks, 128, 0, st>>>(
+        m->N, m->dev.Np, real(m->T_mid), tb, ncells, ld, static_cast<const in_t *>(T), static_cast<const in_t *>(p),
+        static_cast<const in_t *>(Y), static_cast<real *>(cp), static_cast<real *>(h), static_cast<real *>(mu),
         static_cast<real *>(lam), static_cast<real *>(Dk));
     return check_cuda(cudaGetLastError(), "props_eval launch");
 }
 
-template <typename real>
+template <typename real, typename in_t>
 int dispatch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
                    void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
-    if (m->N <= 16) return launch_props<real, 16>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
-    if (m->N <= 32) return launch_props<real, 32>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
-    return launch_props<real, 64>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
+    if (m->N <= 16) return launch_props<real, in_t, 16>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
+    if (m->N <= 32) return launch_props<real, in_t, 32>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
+    return launch_props<real, in_t, 64>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
 }
 
 }  // namespace
@@ -209,7 +209,8 @@ extern "C" int props_eval(const chem_mech *m, int64_t ncells, int64_t ld, int dt
     if (!m) return set_error(CHEM_EINVAL, "props_eval: null mechanism");
     if (ncells < 0 || ld < ncells || (ld & 3) != 0)
         return set_error(CHEM_EINVAL, "props_eval: need 0 <= ncells <= ld and ld a multiple of 4");
-    if (dtype != CHEM_F32 && dtype != CHEM_F64) return set_error(CHEM_EINVAL, "props_eval: bad dtype");
+    if (dtype != CHEM_F32 && dtype != CHEM_F64 && dtype != CHEM_F64_IN_F32)
+        return set_error(CHEM_EINVAL, "props_eval: bad dtype");
     if (ncells == 0) return CHEM_OK;
     if (!T || !p || !Y) return set_error(CHEM_EINVAL, "props_eval: null input array");
     const void *ptrs[] = {T, p, Y, cp, h, mu, lambda, Dk};
@@ -218,6 +219,8 @@ extern "C" int props_eval(const chem_mech *m, int64_t ncells, int64_t ld, int dt
     std::string why;
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "props_eval: " + why);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (dtype == CHEM_F32) return dispatch_props<float>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
-    return dispatch_props<double>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
+    if (dtype == CHEM_F32) return dispatch_props<float, float>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
+    if (dtype == CHEM_F64_IN_F32)
+        return dispatch_props<float, double>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
+    return dispatch_props<double, double>(m, ncells, ld, T, p, Y, cp, h, mu, lambda, Dk, st);
 }

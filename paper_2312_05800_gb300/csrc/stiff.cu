@@ -42,16 +42,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 struct Slice {                 // one warp's shared-memory slice
-    double *G;                 // [n][n] Jacobian / LU
+    double *G;                 // [n][n] Jacobian, then its LU factors
     double *bsw;               // [n] permutation buffer
-    double *C, *HRT, *SR, *cpR, *dcpR, *wdot, *wT, *JCC;   // [N]
-    double *rF, *rkf, *rkr, *rrop, *rdFdC, *rq, *rdqT;      // [R]
+    double *invd;              // [n] reciprocal diagonal of U
+    double *C, *HRT, *SR, *cpR, *wdot, *wT, *JCC, *U, *V;   // [N]
+    double *rq, *rdqT, *rc3;   // [R] rate of progress, d q / dT, third-body coefficient
+    double *rdq;               // [R][6] d q / d C_l for the reaction's distinct species
     int *piv;                  // [n]
 };
 
 __host__ __device__ inline size_t slice_doubles(int N, int R) {
     int n = N + 1;
-    return (size_t)n * n + n + 8 * (size_t)N + 7 * (size_t)R;
+    return (size_t)n * n + 2 * (size_t)n + 9 * (size_t)N + 9 * (size_t)R;
 }
 __host__ __device__ inline size_t slice_bytes(int N, int R) {
     size_t b = slice_doubles(N, R) * sizeof(double) + (size_t)(N + 1) * sizeof(int);
@@ -64,44 +66,46 @@ __device__ Slice make_slice(char *base, int N, int R) {
     double *d = reinterpret_cast<double *>(base);
     s.G = d; d += (size_t)n * n;
     s.bsw = d; d += n;
-    s.C = d; d += N; s.HRT = d; d += N; s.SR = d; d += N; s.cpR = d; d += N;
-    s.dcpR = d; d += N; s.wdot = d; d += N; s.wT = d; d += N; s.JCC = d; d += N;
-    s.rF = d; d += R; s.rkf = d; d += R; s.rkr = d; d += R; s.rrop = d; d += R;
-    s.rdFdC = d; d += R; s.rq = d; d += R; s.rdqT = d; d += R;
+    s.invd = d; d += n;
+    s.C = d; d += N; s.HRT = d; d += N; s.SR = d; d += N; s.cpR = d; d += N; s.wdot = d; d += N;
+    s.wT = d; d += N; s.JCC = d; d += N; s.U = d; d += N; s.V = d; d += N;
+    s.rq = d; d += R; s.rdqT = d; d += R; s.rc3 = d; d += R;
+    s.rdq = d; d += 6 * (size_t)R;
     s.piv = reinterpret_cast<int *>(d);
     return s;
 }
 
 // values of the last right-hand-side evaluation needed by the Jacobian
 struct EvalInfo {
-    double T, rho, cp, dcpdT, Wbar, Q;
+    double T, invT, rho, invrho, cp, dcpdT, Wbar, Q;
 };
 
 __device__ __forceinline__ double sel(const double v[2], int slot) { return slot ? v[1] : v[0]; }
 
-// Troe blending function with the derivatives used by the Jacobian
-__device__ void troe_F(const double *tp, double T, double Prd, double &F, double &glg, double &dFdT_atPr) {
-    double a = tp[0], T3 = tp[1], T1 = tp[2], T2 = tp[3];
-    double e3 = exp(-T / T3), e1 = exp(-T / T1), e2 = exp(-T2 / T);
-    double Fc = (1.0 - a) * e3 + a * e1 + e2;
-    double dFc = -(1.0 - a) / T3 * e3 - a / T1 * e1 + T2 / (T * T) * e2;
-    double phi = log10(Fc);
-    double c = -0.4 - 0.67 * phi, nn = 0.75 - 1.27 * phi, d = 0.14;
-    double L = log10(Prd) + c;
-    double den = nn - d * L;
-    double f1 = L / den;
-    double q = 1.0 + f1 * f1;
-    double lgF = phi / q;
-    F = exp10(lgF);
-    double df1_dL = nn / (den * den);
-    glg = -phi * 2.0 * f1 / (q * q) * df1_dL;
-    double df1_dphi = (-0.67 * den - L * (-1.27 - d * -0.67)) / (den * den);
-    double dlgF_dphi = 1.0 / q - phi * 2.0 * f1 / (q * q) * df1_dphi;
-    double dphi_dT = dFc / (Fc * 2.302585092994046);
+// Troe blending function F(T, Pr) (Gilbert, Luther and Troe 1983), with
+// glg = d log10 F / d log10 Pr and dF/dT at fixed Pr. tp = (a, 1/T***, 1/T*, T**).
+__device__ void troe_F(const double *tp, double T, double invT, double Prd, double &F, double &glg,
+                       double &dFdT_atPr) {
+    const double a = __ldg(tp), r3 = __ldg(tp + 1), r1 = __ldg(tp + 2), T2 = __ldg(tp + 3);
+    const double e3 = exp(-T * r3), e1 = exp(-T * r1), e2 = exp(-T2 * invT);
+    const double Fc = (1.0 - a) * e3 + a * e1 + e2;
+    const double dFc = -(1.0 - a) * r3 * e3 - a * r1 * e1 + T2 * invT * invT * e2;
+    const double phi = log10(Fc);
+    const double c = -0.4 - 0.67 * phi, nn = 0.75 - 1.27 * phi, d = 0.14;
+    const double L = log10(Prd) + c;
+    const double rden = 1.0 / (nn - d * L);
+    const double f1 = L * rden;
+    const double rq = 1.0 / (1.0 + f1 * f1);
+    F = exp10(phi * rq);
+    const double df1_dL = nn * rden * rden;
+    glg = -phi * 2.0 * f1 * rq * rq * df1_dL;
+    const double df1_dphi = (-0.67 * (nn - d * L) - L * (-1.27 + d * 0.67)) * rden * rden;
+    const double dlgF_dphi = rq - phi * 2.0 * f1 * rq * rq * df1_dphi;
+    const double dphi_dT = dFc / (Fc * 2.302585092994046);
     dFdT_atPr = F * 2.302585092994046 * dlgF_dphi * dphi_dT;
 }
 
-// f = f(y) for the warp's cell; with jac, also stores what the Jacobian needs.
+// f = f(y) for the warp's cell. With jac, also stores what build_matrix needs.
 __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double p, const double y[2], double f[2],
                              bool jac) {
     const int N = m.N, R = m.R, n = N + 1;
@@ -109,70 +113,74 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
     f[0] = 0.0;
     f[1] = 0.0;
     const double T = __shfl_sync(kFull, y[0], 0);
-    info.T = T;
-    const int rng = (T >= m.T_mid) ? 1 : 0;
+    const double invT = 1.0 / T;
     const double lnT = log(T);
+    info.T = T;
+    info.invT = invT;
+    const int rng = (T >= m.T_mid) ? 1 : 0;
     __syncwarp();
-    // species pass: thermo, mixture sums
+    // species pass: thermo and mixture sums (lane per species)
     double S = 0.0, cp = 0.0, dcp = 0.0;
+    double yw_s[2] = {0.0, 0.0};
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
+        const int c = lane + 32 * s;
         if (c >= 1 && c < n) {
-            int k = c - 1;
-            const double *a = m.nasa + (size_t)(rng * N + k) * 7;
-            double a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3), a4 = __ldg(a + 4),
-                   a5 = __ldg(a + 5), a6 = __ldg(a + 6);
-            double T2 = T * T, T3 = T2 * T, T4 = T3 * T;
-            double cpR = a0 + a1 * T + a2 * T2 + a3 * T3 + a4 * T4;
-            double HRT = a0 + a1 * T / 2.0 + a2 * T2 / 3.0 + a3 * T3 / 4.0 + a4 * T4 / 5.0 + a5 / T;
-            double SR = a0 * lnT + a1 * T + a2 * T2 / 2.0 + a3 * T3 / 3.0 + a4 * T4 / 4.0 + a6;
-            double Yk = y[s];
-            double W = __ldg(m.W + k);
-            S += Yk / W;
-            cp += Yk * cpR * kR / W;
+            const int k = c - 1;
+            const double *a = m.f64.nasa_cp + (size_t)(rng * N + k) * 5;
+            const double *b = m.f64.nasa_h + (size_t)(rng * N + k) * 6;
+            const double *e = m.nasa_s + (size_t)(rng * N + k) * 6;
+            const double a0 = __ldg(a), a1 = __ldg(a + 1), a2 = __ldg(a + 2), a3 = __ldg(a + 3), a4 = __ldg(a + 4);
+            const double cpR = a0 + T * (a1 + T * (a2 + T * (a3 + T * a4)));
+            const double HRT = __ldg(b) + T * (__ldg(b + 1) + T * (__ldg(b + 2) + T * (__ldg(b + 3) + T * __ldg(b + 4))))
+                               + __ldg(b + 5) * invT;
+            const double SR = __ldg(e) * lnT + T * (__ldg(e + 1) + T * (__ldg(e + 2) + T * (__ldg(e + 3) + T * __ldg(e + 4))))
+                              + __ldg(e + 5);
+            const double yw = y[s] * __ldg(m.f64.invW + k);
+            yw_s[s] = yw;
+            S += yw;
+            cp += yw * cpR;
             sh.HRT[k] = HRT;
             sh.SR[k] = SR;
             sh.cpR[k] = cpR;
-            if (jac) {
-                double dcpR = a1 + 2.0 * a2 * T + 3.0 * a3 * T2 + 4.0 * a4 * T3;
-                sh.dcpR[k] = dcpR;
-                dcp += Yk * dcpR * kR / W;
-            }
+            if (jac) dcp += yw * (a1 + T * (2.0 * a2 + T * (3.0 * a3 + T * 4.0 * a4)));
         }
     }
     S = warp_sum(S);
-    cp = warp_sum(cp);
-    if (jac) dcp = warp_sum(dcp);
-    const double rho = p / (kR * T * S);
+    cp = warp_sum(cp) * kR;
+    if (jac) dcp = warp_sum(dcp) * kR;
+    const double Wbar = 1.0 / S;
+    const double rho = p * invT * Wbar * (1.0 / kR);
+    const double invrho = 1.0 / rho;
     info.rho = rho;
+    info.invrho = invrho;
     info.cp = cp;
     info.dcpdT = dcp;
-    info.Wbar = 1.0 / S;
+    info.Wbar = Wbar;
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
-        if (c >= 1 && c < n) sh.C[c - 1] = rho * y[s] / __ldg(m.W + c - 1);
+        const int c = lane + 32 * s;
+        if (c >= 1 && c < n) sh.C[c - 1] = rho * yw_s[s];
     }
     __syncwarp();
-    // reaction pass: lane per reaction
-    const double RT = kR * T;
-    const double PRT = m.P_std / RT;
+    // reaction pass (lane per reaction)
+    const double lnPRT = m.lnPR - lnT;
     for (int j = lane; j < R; j += 32) {
         const int *re = m.reac + 3 * j;
         const int *pr = m.prod + 3 * j;
-        int r0 = __ldg(re), r1 = __ldg(re + 1), r2 = __ldg(re + 2);
-        int p0 = __ldg(pr), p1 = __ldg(pr + 1), p2 = __ldg(pr + 2);
-        double kf = exp(__ldg(m.lnA + j) + __ldg(m.beta + j) * lnT - __ldg(m.EaR + j) / T);
+        const int r0 = __ldg(re), r1 = __ldg(re + 1), r2 = __ldg(re + 2);
+        const int p0 = __ldg(pr), p1 = __ldg(pr + 1), p2 = __ldg(pr + 2);
+        const double beta = __ldg(m.beta + j), EaR = __ldg(m.EaR + j);
+        const double lnkf = __ldg(m.lnA + j) + beta * lnT - EaR * invT;
+        const double kf = exp(lnkf);
         double lnKp = 0.0, dH = 0.0;
-        int dnu = 0;
-        if (p0 >= 0) { lnKp += sh.SR[p0] - sh.HRT[p0]; dH += sh.HRT[p0] / T; ++dnu; }
-        if (r0 >= 0) { lnKp -= sh.SR[r0] - sh.HRT[r0]; dH -= sh.HRT[r0] / T; --dnu; }
-        if (p1 >= 0) { lnKp += sh.SR[p1] - sh.HRT[p1]; dH += sh.HRT[p1] / T; ++dnu; }
-        if (r1 >= 0) { lnKp -= sh.SR[r1] - sh.HRT[r1]; dH -= sh.HRT[r1] / T; --dnu; }
-        if (p2 >= 0) { lnKp += sh.SR[p2] - sh.HRT[p2]; dH += sh.HRT[p2] / T; ++dnu; }
-        if (r2 >= 0) { lnKp -= sh.SR[r2] - sh.HRT[r2]; dH -= sh.HRT[r2] / T; --dnu; }
-        double pw = (dnu == 0) ? 1.0 : (dnu == 1 ? PRT : (dnu == -1 ? 1.0 / PRT : pow(PRT, (double)dnu)));
-        double Kc = exp(lnKp) * pw;
-        double kr = kf / Kc;
+        if (p0 >= 0) { lnKp += sh.SR[p0] - sh.HRT[p0]; dH += sh.HRT[p0]; }
+        if (r0 >= 0) { lnKp -= sh.SR[r0] - sh.HRT[r0]; dH -= sh.HRT[r0]; }
+        if (p1 >= 0) { lnKp += sh.SR[p1] - sh.HRT[p1]; dH += sh.HRT[p1]; }
+        if (r1 >= 0) { lnKp -= sh.SR[r1] - sh.HRT[r1]; dH -= sh.HRT[r1]; }
+        if (p2 >= 0) { lnKp += sh.SR[p2] - sh.HRT[p2]; dH += sh.HRT[p2]; }
+        if (r2 >= 0) { lnKp -= sh.SR[r2] - sh.HRT[r2]; dH -= sh.HRT[r2]; }
+        const double dnu = (double)__ldg(m.dnu + j);
+        // k_r = k_f / K_c, ln K_c = ln K_p + dnu ln(P_std / RT)
+        const double kr = exp(lnkf - lnKp - dnu * lnPRT);
         double Pf = 1.0, Pr = 1.0;
         if (r0 >= 0) Pf *= sh.C[r0];
         if (r1 >= 0) Pf *= sh.C[r1];
@@ -181,59 +189,77 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
         if (p1 >= 0) Pr *= sh.C[p1];
         if (p2 >= 0) Pr *= sh.C[p2];
         const int type = __ldg(m.rtype + j);
+        const double dlnkf = (beta + EaR * invT) * invT;
         double F = 1.0, dFdC = 0.0, dFdT = 0.0;
-        double dlnkf = __ldg(m.beta + j) / T + __ldg(m.EaR + j) / (T * T);
         if (type != 0) {
             const double *e = m.eff + (size_t)__ldg(m.tb_row + j) * N;
             double M = 0.0;
             for (int k = 0; k < N; ++k) M += __ldg(e + k) * sh.C[k];
             if (type == 1) {
-                F = M; dFdC = 1.0;
+                F = M;
+                dFdC = 1.0;
             } else {
-                double k0 = exp(__ldg(m.lnA0 + j) + __ldg(m.beta0 + j) * lnT - __ldg(m.Ea0R + j) / T);
-                double dlnk0 = __ldg(m.beta0 + j) / T + __ldg(m.Ea0R + j) / (T * T);
-                double Prd = k0 * M / kf;
+                const double beta0 = __ldg(m.beta0 + j), Ea0R = __ldg(m.Ea0R + j);
+                const double ratio = exp(__ldg(m.lnA0 + j) + beta0 * lnT - Ea0R * invT - lnkf);   // k0 / k_inf
+                double Prd = M * ratio;
                 if (Prd < 1e-300) Prd = 1e-300;
                 double Ft, glg, dFtdT;
-                troe_F(m.troe + 4 * j, T, Prd, Ft, glg, dFtdT);
-                double blend = Prd / (1.0 + Prd);
-                double dF_dPrd = Ft / ((1.0 + Prd) * (1.0 + Prd)) + blend * Ft * glg / Prd;
+                troe_F(m.troe_r + 4 * j, T, invT, Prd, Ft, glg, dFtdT);
+                const double ip = 1.0 / (1.0 + Prd);
+                const double blend = Prd * ip;
+                const double dF_dPrd = Ft * ip * (ip + glg);
                 F = blend * Ft;
-                dFdC = dF_dPrd * k0 / kf;
+                dFdC = dF_dPrd * ratio;
+                const double dlnk0 = (beta0 + Ea0R * invT) * invT;
                 dFdT = dF_dPrd * Prd * (dlnk0 - dlnkf) + blend * dFtdT;
             }
         }
-        double rop = kf * Pf - kr * Pr;
+        const double rop = kf * Pf - kr * Pr;
         sh.rq[j] = F * rop;
         if (jac) {
-            double dlnKc = dH - (double)dnu / T;
-            double dkfdT = kf * dlnkf;
-            double dkrdT = kr * (dlnkf - dlnKc);
-            sh.rF[j] = F;
-            sh.rkf[j] = kf;
-            sh.rkr[j] = kr;
-            sh.rrop[j] = rop;
-            sh.rdFdC[j] = dFdC;
+            const double dlnKc = (dH - dnu) * invT;
+            const double dkfdT = kf * dlnkf;
+            const double dkrdT = kr * (dlnkf - dlnKc);
             sh.rdqT[j] = F * (dkfdT * Pf - dkrdT * Pr) + rop * dFdT;
+            sh.rc3[j] = (type != 0) ? rop * dFdC : 0.0;
+            // d q / d C_l through the mass-action products, for the distinct species l
+            for (int u = 0; u < 6; ++u) {
+                const int l = __ldg(m.rsp + 6 * j + u);
+                if (l < 0) break;
+                double dPf = 0.0, dPr = 0.0;
+                if (r0 == l) dPf += (r1 >= 0 ? sh.C[r1] : 1.0) * (r2 >= 0 ? sh.C[r2] : 1.0);
+                if (r1 == l) dPf += (r0 >= 0 ? sh.C[r0] : 1.0) * (r2 >= 0 ? sh.C[r2] : 1.0);
+                if (r2 == l) dPf += (r0 >= 0 ? sh.C[r0] : 1.0) * (r1 >= 0 ? sh.C[r1] : 1.0);
+                if (p0 == l) dPr += (p1 >= 0 ? sh.C[p1] : 1.0) * (p2 >= 0 ? sh.C[p2] : 1.0);
+                if (p1 == l) dPr += (p0 >= 0 ? sh.C[p0] : 1.0) * (p2 >= 0 ? sh.C[p2] : 1.0);
+                if (p2 == l) dPr += (p0 >= 0 ? sh.C[p0] : 1.0) * (p1 >= 0 ? sh.C[p1] : 1.0);
+                sh.rdq[6 * j + u] = F * (kf * dPf - kr * dPr);
+            }
         }
     }
     __syncwarp();
     // species gather: wdot_k = sum_j nu_kj q_j (reactions ascending)
     double Q = 0.0;
+    const double RT = kR * T;
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
+        const int c = lane + 32 * s;
         if (c >= 1 && c < n) {
-            int k = c - 1;
+            const int k = c - 1;
             double w = 0.0, wt = 0.0;
-            int b = __ldg(m.inc_ptr + k), e = __ldg(m.inc_ptr + k + 1);
+            const int b = __ldg(m.inc_ptr + k), e = __ldg(m.inc_ptr + k + 1);
             for (int t = b; t < e; ++t) {
-                int2 ent = __ldg(m.inc + t);
+                const int2 ent = __ldg(m.inc + t);
                 w += (double)ent.y * sh.rq[ent.x];
                 if (jac) wt += (double)ent.y * sh.rdqT[ent.x];
             }
-            if (jac) { sh.wdot[k] = w; sh.wT[k] = wt; }
-            double W = __ldg(m.W + k);
-            f[s] = W * w / rho;
+            const double Wk = __ldg(m.W + k);
+            if (jac) {
+                sh.wdot[k] = w;
+                sh.wT[k] = wt;
+                sh.U[k] = Wk * invrho;
+                sh.V[k] = Wk * w * Wbar * invrho;
+            }
+            f[s] = Wk * w * invrho;
             Q += sh.HRT[k] * RT * w;
         }
     }
@@ -243,58 +269,56 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
     return info;
 }
 
-// Builds G = I/(h g) - J in the slice from the data of eval_rhs(..., jac = true).
+// G = I/(h g) - J from the data of eval_rhs(..., jac = true).
 __device__ void build_matrix(const DevMech &m, const Slice &sh, int lane, const EvalInfo &in, double h) {
-    const int N = m.N, R = m.R, n = N + 1;
+    const int N = m.N, n = N + 1;
     double *G = sh.G;
-    // zero the species block (lane owns the columns c = lane + 32 s throughout)
-    for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
+    for (int s = 0; s < 2; ++s) {            // zero the species block (column owners)
+        const int c = lane + 32 * s;
         if (c >= 1 && c < n)
             for (int r = 1; r < n; ++r) G[r * n + c] = 0.0;
     }
     __syncwarp();
-    // JC[k][l] = d wdot_k / d C_l, reaction by reaction (ascending), column-parallel
-    for (int j = 0; j < R; ++j) {
-        const int type = __ldg(m.rtype + j);
-        int rs[3], ps[3];
-        for (int i = 0; i < 3; ++i) { rs[i] = __ldg(m.reac + 3 * j + i); ps[i] = __ldg(m.prod + 3 * j + i); }
-        const double F = sh.rF[j], kf = sh.rkf[j], kr = sh.rkr[j], rop = sh.rrop[j], dFdC = sh.rdFdC[j];
-        const double *e = (type != 0) ? m.eff + (size_t)__ldg(m.tb_row + j) * N : nullptr;
-        for (int s = 0; s < 2; ++s) {
-            const int c = lane + 32 * s;   // matrix column c = species l + 1
-            if (c < 1 || c >= n) continue;
-            const int l = c - 1;
-            bool part = (type != 0);
-            for (int i = 0; i < 3; ++i) part |= (rs[i] == l) || (ps[i] == l);
-            if (!part) continue;
-            double dPf = 0.0, dPr = 0.0;
-            for (int i = 0; i < 3; ++i) {
-                if (rs[i] == l) {
-                    double t = 1.0;
-                    for (int i2 = 0; i2 < 3; ++i2)
-                        if (i2 != i && rs[i2] >= 0) t *= sh.C[rs[i2]];
-                    dPf += t;
+    // sparse part of JC = d wdot / d C: row owners gather their reactions (ascending)
+    for (int s = 0; s < 2; ++s) {
+        const int c = lane + 32 * s;
+        if (c >= 1 && c < n) {
+            const int k = c - 1;
+            double *row = G + (size_t)c * n + 1;
+            const int b = __ldg(m.inc_ptr + k), e = __ldg(m.inc_ptr + k + 1);
+            for (int t = b; t < e; ++t) {
+                const int2 ent = __ldg(m.inc + t);
+                const double nu = (double)ent.y;
+                for (int u = 0; u < 6; ++u) {
+                    const int l = __ldg(m.rsp + 6 * ent.x + u);
+                    if (l < 0) break;
+                    row[l] += nu * sh.rdq[6 * ent.x + u];
                 }
-                if (ps[i] == l) {
-                    double t = 1.0;
-                    for (int i2 = 0; i2 < 3; ++i2)
-                        if (i2 != i && ps[i2] >= 0) t *= sh.C[ps[i2]];
-                    dPr += t;
-                }
-            }
-            double dFl = (type == 0) ? 0.0 : dFdC * __ldg(e + l);
-            double dq = F * (kf * dPf - kr * dPr) + rop * dFl;
-            for (int i = 0; i < 3; ++i) {
-                if (rs[i] >= 0) G[(1 + rs[i]) * n + 1 + l] -= dq;
-                if (ps[i] >= 0) G[(1 + ps[i]) * n + 1 + l] += dq;
             }
         }
     }
     __syncwarp();
-    // JCC[k] = sum_l JC[k][l] C_l (lane per row)
+    // dense third-body part: rank-1 terms nu_j (rop dF/dM) eff_j (column owners)
+    for (int t = 0; t < m.n_tb; ++t) {
+        const int j = __ldg(m.tb_list + t);
+        const double c3 = sh.rc3[j];
+        const double *e = m.eff + (size_t)__ldg(m.tb_row + j) * N;
+        for (int s = 0; s < 2; ++s) {
+            const int c = lane + 32 * s;
+            if (c >= 1 && c < n) {
+                const double v = c3 * __ldg(e + c - 1);
+                for (int u = 0; u < 6; ++u) {
+                    const int k = __ldg(m.rsp + 6 * j + u);
+                    if (k < 0) break;
+                    G[(1 + k) * n + c] += (double)__ldg(m.rnu + 6 * j + u) * v;
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // JCC[k] = sum_l JC[k][l] C_l (row owners)
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
+        const int c = lane + 32 * s;
         if (c >= 1 && c < n) {
             double acc = 0.0;
             for (int l = 0; l < N; ++l) acc += G[c * n + 1 + l] * sh.C[l];
@@ -302,82 +326,80 @@ __device__ void build_matrix(const DevMech &m, const Slice &sh, int lane, const 
         }
     }
     __syncwarp();
-    const double T = in.T, rho = in.rho, cp = in.cp, Wbar = in.Wbar, Q = in.Q;
-    const double rcp = rho * cp;
+    // chain rule through C(T, Y) and rho(T, Y); then G = I/(h g) - J
+    const double T = in.T, invT = in.invT, cp = in.cp, Wbar = in.Wbar, Q = in.Q;
+    const double invrcp = 1.0 / (in.rho * cp);
+    const double qq = Q * invrcp / cp;              // Q / (rho cp^2)
+    const double RT = kR * T;
     const double ghinv = 1.0 / (h * kGam);
+    double sT = 0.0;
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
-        if (c >= n) continue;
-        if (c == 0) {
-            // temperature column and J[0][0]
-            double sT = 0.0;
-            for (int k = 0; k < N; ++k) {
-                double Wk = __ldg(m.W + k);
-                double dwdT = sh.wT[k] - sh.JCC[k] / T;
-                sT += sh.cpR[k] * kR * sh.wdot[k] + sh.HRT[k] * kR * T * dwdT;
-                double J = Wk / rho * dwdT + Wk * sh.wdot[k] / (rho * T);
-                G[(1 + k) * n] = -J;
-            }
-            double J00 = -sT / rcp - Q * (cp / T - in.dcpdT) / (rho * cp * cp);
-            G[0] = ghinv - J00;
-        } else {
-            int mm = c - 1;
-            double Wm = __ldg(m.W + mm);
-            double sTr = 0.0;
-            for (int k = 0; k < N; ++k) {
-                double Wk = __ldg(m.W + k);
-                double dw = G[(1 + k) * n + c] * rho / Wm - Wbar / Wm * sh.JCC[k];
-                sTr += sh.HRT[k] * kR * T * dw;
-                double J = Wk / rho * dw + Wk * sh.wdot[k] * Wbar / (rho * Wm);
-                G[(1 + k) * n + c] = (1 + k == c) ? ghinv - J : -J;
-            }
-            double J0 = -sTr / rcp - Q * (cp * Wbar - sh.cpR[mm] * kR) / (rho * cp * cp * Wm);
-            G[c] = -J0;
+        const int c = lane + 32 * s;
+        if (c < 1 || c >= n) continue;
+        // species column c (column owner)
+        const int mm = c - 1;
+        const double iWm = __ldg(m.f64.invW + mm);
+        const double a = in.rho * iWm, b = Wbar * iWm;
+        double sTr = 0.0;
+        for (int k = 0; k < N; ++k) {
+            double *g = G + (size_t)(1 + k) * n + c;
+            const double dw = *g * a - b * sh.JCC[k];
+            sTr += sh.HRT[k] * RT * dw;
+            const double J = sh.U[k] * dw + sh.V[k] * iWm;
+            *g = (1 + k == c) ? ghinv - J : -J;
         }
+        G[c] = sTr * invrcp + qq * (cp * Wbar - sh.cpR[mm] * kR) * iWm;   // -J[0][c]
+        // temperature column entry of row c (row owner)
+        const double dwdT = sh.wT[mm] - sh.JCC[mm] * invT;
+        G[(size_t)c * n] = -(sh.U[mm] * dwdT + sh.U[mm] * sh.wdot[mm] * invT);
+        sT += sh.cpR[mm] * kR * sh.wdot[mm] + sh.HRT[mm] * RT * dwdT;
     }
+    sT = warp_sum(sT);
+    if (lane == 0) G[0] = ghinv + sT * invrcp + qq * (cp * invT - in.dcpdT);
     __syncwarp();
 }
 
-// In-place LU with partial pivoting; returns false for an exactly singular matrix.
+// In-place LU with partial pivoting; false for a zero or non-finite pivot column.
 __device__ bool lu_factor(const Slice &sh, int lane, int n) {
     double *G = sh.G;
     for (int k = 0; k < n; ++k) {
         double best = -1.0;
         int bi = n;
         for (int s = 0; s < 2; ++s) {
-            int i = lane + 32 * s;
+            const int i = lane + 32 * s;
             if (i >= k && i < n) {
-                double v = fabs(G[i * n + k]);
+                const double v = fabs(G[i * n + k]);
                 if (v > best || (v == best && i < bi)) { best = v; bi = i; }
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(kFull, best, o);
-            int oi = __shfl_xor_sync(kFull, bi, o);
+            const double ob = __shfl_xor_sync(kFull, best, o);
+            const int oi = __shfl_xor_sync(kFull, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (!(best > 0.0) || bi >= n) return false;   // zero or non-finite column
+        if (!(best > 0.0) || bi >= n) return false;
         if (lane == 0) sh.piv[k] = bi;
         if (bi != k) {
             for (int s = 0; s < 2; ++s) {
-                int c = lane + 32 * s;
+                const int c = lane + 32 * s;
                 if (c < n) {
-                    double t = G[k * n + c];
+                    const double t = G[k * n + c];
                     G[k * n + c] = G[bi * n + c];
                     G[bi * n + c] = t;
                 }
             }
         }
         __syncwarp();
-        const double pivot = G[k * n + k];
+        const double rp = 1.0 / G[k * n + k];
+        if (lane == 0) sh.invd[k] = rp;
         for (int s = 0; s < 2; ++s) {
-            int i = lane + 32 * s;
-            if (i > k && i < n) G[i * n + k] = G[i * n + k] / pivot;
+            const int i = lane + 32 * s;
+            if (i > k && i < n) G[i * n + k] *= rp;
         }
         __syncwarp();
         for (int s = 0; s < 2; ++s) {
-            int c = lane + 32 * s;
+            const int c = lane + 32 * s;
             if (c > k && c < n) {
                 const double akc = G[k * n + c];
                 for (int i = k + 1; i < n; ++i) G[i * n + c] -= G[i * n + k] * akc;
@@ -392,36 +414,36 @@ __device__ bool lu_factor(const Slice &sh, int lane, int n) {
 __device__ void lu_solve(const Slice &sh, int lane, int n, double b[2]) {
     const double *G = sh.G;
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
+        const int c = lane + 32 * s;
         if (c < n) sh.bsw[c] = b[s];
     }
     __syncwarp();
     if (lane == 0) {
         for (int k = 0; k < n; ++k) {
-            int p = sh.piv[k];
-            if (p != k) { double t = sh.bsw[k]; sh.bsw[k] = sh.bsw[p]; sh.bsw[p] = t; }
+            const int p = sh.piv[k];
+            if (p != k) { const double t = sh.bsw[k]; sh.bsw[k] = sh.bsw[p]; sh.bsw[p] = t; }
         }
     }
     __syncwarp();
     for (int s = 0; s < 2; ++s) {
-        int c = lane + 32 * s;
+        const int c = lane + 32 * s;
         b[s] = (c < n) ? sh.bsw[c] : 0.0;
     }
     for (int k = 0; k < n - 1; ++k) {
-        double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
+        const double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
         for (int s = 0; s < 2; ++s) {
-            int i = lane + 32 * s;
+            const int i = lane + 32 * s;
             if (i > k && i < n) b[s] -= G[i * n + k] * bk;
         }
     }
     for (int k = n - 1; k >= 0; --k) {
         if ((k & 31) == lane) {
-            if (k >> 5) b[1] = b[1] / G[k * n + k];
-            else b[0] = b[0] / G[k * n + k];
+            if (k >> 5) b[1] *= sh.invd[k];
+            else b[0] *= sh.invd[k];
         }
-        double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
+        const double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
         for (int s = 0; s < 2; ++s) {
-            int i = lane + 32 * s;
+            const int i = lane + 32 * s;
             if (i < k) b[s] -= G[i * n + k] * bk;
         }
     }
