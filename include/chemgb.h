@@ -156,6 +156,33 @@ int chem_step_stiff(const chem_mech *mech, int64_t ncells, int64_t ld, double dt
                     double *T, const double *p, double *Y, int32_t *status, int32_t *nsteps,
                     chem_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * chem_step_stiff_noalloc -- chem_step_stiff without any device allocation
+ * ---------------------------------------------------------------------------
+ * The paper has no counterpart: this entry point exists for callers that must
+ * not allocate device memory, or write into library-owned memory, while they
+ * step. Examples are a host code that hands out its whole device budget from
+ * its own pool and forbids other allocations, and a caller that runs the step
+ * in a region where cudaMalloc is not allowed or would synchronise the device.
+ * It computes exactly what chem_step_stiff computes, with the same arguments
+ * and results. Its only scratch, the work-queue counter, lives in a static
+ * 256-byte device array inside the library instead of the mechanism handle;
+ * every GPU that loads the library holds that array until the process exits.
+ *  - The call allocates nothing and leaves the mechanism handle untouched
+ *    (its tables are only read).
+ *  - ncells is limited to 2^30 by the 32-bit counter; larger values return
+ *    CHEM_EINVAL.
+ *  - All calls share the array. Each call clears the counter on its own stream
+ *    first, so calls that overlap on the GPU (different streams, or different
+ *    host threads on one device) race and must be ordered by the caller.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture on the device.
+ */
+int chem_step_stiff_noalloc(const chem_mech *mech, int64_t ncells, int64_t ld, double dt, const chem_ode_opts *opts,
+                            double *T, const double *p, double *Y, int32_t *status, int32_t *nsteps,
+                            chem_stream_t stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *chem_last_error(void);
 

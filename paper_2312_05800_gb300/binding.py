@@ -55,6 +55,7 @@ def lib() -> ctypes.CDLL:
     L.chem_ode_opts_default.argtypes = [ctypes.POINTER(chem_ode_opts)]
     L.chem_ode_opts_default.restype = None
     L.chem_step_stiff.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
+    L.chem_step_stiff_noalloc.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
     L.chem_last_error.restype = ctypes.c_char_p
     L.chem_version.restype = ctypes.c_char_p
     _lib = L
@@ -147,6 +148,13 @@ def chem_step_stiff(mech: Mech, ncells: int, ld: int, dt: float, opts: Optional[
                     nsteps=None, stream=None):
     _check(lib().chem_step_stiff(mech.handle, ncells, ld, float(dt), ctypes.byref(opts) if opts is not None else None,
                                  _ptr(T), _ptr(p), _ptr(Y), _ptr(status), _ptr(nsteps), _stream(stream)))
+
+
+def chem_step_stiff_noalloc(mech: Mech, ncells: int, ld: int, dt: float, opts: Optional[chem_ode_opts], T, p, Y,
+                            status, nsteps=None, stream=None):
+    _check(lib().chem_step_stiff_noalloc(mech.handle, ncells, ld, float(dt),
+                                         ctypes.byref(opts) if opts is not None else None, _ptr(T), _ptr(p), _ptr(Y),
+                                         _ptr(status), _ptr(nsteps), _stream(stream)))
 
 
 def chem_last_error() -> str:

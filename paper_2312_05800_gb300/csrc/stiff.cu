@@ -19,6 +19,7 @@
 //    y_new = y + sum_i m_i K_i, error estimate sum_i e_i K_i, with the
 //    step-size controller of chem_ode_opts. Everything is FP64.
 #include <cmath>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -621,4 +622,96 @@ extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, d
     if (rc) return rc;
     stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue);
     return check_cuda(cudaGetLastError(), "chem_step_stiff launch");
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of chem_step_stiff.
+//
+// The regular entry point keeps its only global scratch (the work-queue
+// counter) inside the mechanism handle. This variant keeps it in the
+// file-scope array below instead, so a call neither allocates device memory
+// nor writes into the handle. The array is 256 bytes (64 32-bit words) and
+// every GPU that loads the library holds it until the process exits. A call
+// uses word 0 as its queue counter and clears it first on its stream; calls
+// that overlap on the GPU share that word and race.
+// ---------------------------------------------------------------------------
+namespace chemgb {
+namespace {
+
+constexpr int kNoAllocWords = 64;
+// Largest ncells one call accepts: every resident warp takes one ticket past
+// the last cell, so the 32-bit counter needs headroom below 2^32.
+constexpr int64_t kNoAllocMaxCells = (int64_t)1 << 30;
+
+static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocWords];
+
+// Device address of g_noalloc_scratch for the current device, looked up once
+// per device (with that device current). In host code the array's name is only
+// a host-side stand-in, so kernels must be given this address.
+int noalloc_scratch(unsigned int **out) {
+    static std::mutex mu;
+    static unsigned int *addr[64] = {nullptr};
+    int dev = -1;
+    int rc = check_cuda(cudaGetDevice(&dev), "chem_step_stiff_noalloc: cudaGetDevice");
+    if (rc) return rc;
+    if (dev < 0 || dev >= 64) return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff_noalloc: device index above 63");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        rc = check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "chem_step_stiff_noalloc: cudaGetSymbolAddress");
+        if (rc) return rc;
+        addr[dev] = static_cast<unsigned int *>(p);
+    }
+    *out = addr[dev];
+    return CHEM_OK;
+}
+
+}  // namespace
+}  // namespace chemgb
+
+extern "C" int chem_step_stiff_noalloc(const chem_mech *m, int64_t ncells, int64_t ld, double dt,
+                                       const chem_ode_opts *opts, double *T, const double *p, double *Y,
+                                       int32_t *status, int32_t *nsteps, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: null mechanism");
+    if (ncells < 0 || ld < ncells || (ld & 3) != 0)
+        return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: need 0 <= ncells <= ld, ld a multiple of 4");
+    if (ncells > kNoAllocMaxCells)
+        return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: ncells exceeds the 2^30-cell limit of its static "
+                                      "work-queue scratch");
+    if (!(dt > 0.0)) return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: dt must be positive");
+    if (m->N > 63) return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff_noalloc: at most 63 species");
+    if (ncells == 0) return CHEM_OK;
+    if (!T || !p || !Y || !status) return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: null array");
+    const void *ptrs[] = {T, p, Y, status, nsteps};
+    for (const void *q : ptrs)
+        if (q && !aligned16(q))
+            return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: arrays must be 16-byte aligned");
+    chem_ode_opts o;
+    chem_ode_opts_default(&o);
+    if (opts) o = *opts;
+    if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || o.max_steps < 1)
+        return set_error(CHEM_EINVAL, "chem_step_stiff_noalloc: tolerances, h0 and max_steps must be positive");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff_noalloc: " + why);
+    unsigned int *queue = nullptr;
+    int rc = noalloc_scratch(&queue);
+    if (rc) return rc;
+    size_t smem = slice_bytes(m->N, m->R) * kWarps;
+    if (smem > 227 * 1024)
+        return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff_noalloc: mechanism too large for shared memory");
+    rc = check_cuda(cudaFuncSetAttribute(stiff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                    "chem_step_stiff_noalloc: smem attribute");
+    if (rc) return rc;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stiff_kernel, kWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t need = (ncells + kWarps - 1) / kWarps;
+    int blocks = (int)((int64_t)sms * per_sm < need ? (int64_t)sms * per_sm : need);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "chem_step_stiff_noalloc: clear queue");
+    if (rc) return rc;
+    stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue);
+    return check_cuda(cudaGetLastError(), "chem_step_stiff_noalloc launch");
 }
