@@ -109,10 +109,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def make_inputs(rank: int):
+def make_inputs(rank: int, ncells: int = NCELLS):
     from paper_2312_05800_gb300 import synth
     mech = synth.get_mech(MECH)
-    T, p, Y = synth.states_profiles(mech, NCELLS, SEED + 1000 * rank, ld=NCELLS)
+    T, p, Y = synth.states_profiles(mech, ncells, SEED + 1000 * rank, ld=synth.padded_ld(ncells))
     return mech, T, p, Y
 
 
@@ -157,6 +157,7 @@ def run_reference(args):
 
 
 def main():
+    global NCELLS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -164,12 +165,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="stiff", choices=["stiff"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=NCELLS,
+                    help="cells per GPU; smaller values only for profiling captures (the bench line uses the default)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
-    import numpy as np
     import torch
+    NCELLS = args.cells
+    if NCELLS % 4:
+        raise SystemExit("--cells must be a multiple of 4")
     rank, world, local = env_rank()
     if world > 1:
         import torch.distributed as dist
@@ -177,7 +182,7 @@ def main():
     torch.cuda.set_device(local)
     from paper_2312_05800_gb300 import binding, build
     build.build()
-    mech, T, p, Y = make_inputs(rank)
+    mech, T, p, Y = make_inputs(rank, NCELLS)
     N = mech.N
     dm = binding.Mech(mech)
     dev = torch.device("cuda", local)

@@ -183,6 +183,116 @@ int chem_step_stiff_noalloc(const chem_mech *mech, int64_t ncells, int64_t ld, d
                             double *T, const double *p, double *Y, int32_t *status, int32_t *nsteps,
                             chem_stream_t stream);
 
+/* ---------------------------------------------------------------------------
+ * chem_dense_bf16 -- one dense layer of the network on the tensor cores
+ * ---------------------------------------------------------------------------
+ * Sec. 3.2: each hidden layer applies GELU to an affine map of the layer below.
+ * Computes, for i < M and n < N,
+ *     acc[i][n] = sum_k x[i][k] W[n][k]      (BF16 operands, FP32 accumulation)
+ *     act = 0:  y[i][n] = acc + b[n]         (float y)
+ *     act = 1:  y[i][n] = GELU(acc + b[n])   (BF16 y, exact erf GELU)
+ * x: [M][ldx] BF16, W: [N][ldw] BF16 (row n = output n), b: [N] float or NULL,
+ * y: [M][ldy]. ldx and ldw must make rows a multiple of 16 bytes and the bases
+ * 16-byte aligned. tile_n selects the output tile width (32, 64, 128, 160, 208
+ * or 256; 0 = automatic). err (device int, may be NULL) receives a non-zero
+ * code if a pipeline wait timed out (the call then returns without a result).
+ */
+int chem_dense_bf16(int64_t M, int N, int K, const void *x, int64_t ldx, const void *W, int64_t ldw,
+                    const float *b, int act, void *y, int64_t ldy, int tile_n, int *err, chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned chemistry (Sec. 3.2)
+ * ---------------------------------------------------------------------------
+ * The network maps the input x(t) = {T, p, F(Y_1..Y_N)}, F(Y) = (Y^0.1 - 1)/0.1
+ * (the Box-Cox map; negative Y clamp to 0), Z-score normalised with training
+ * statistics, through three GELU hidden layers (1600, 800, 400 in the paper)
+ * to the Z-scored change u*(t) = Y(t + dt) - Y(t) of the N - 1 species other
+ * than the bath species (ascending species index). One multi-output network
+ * stands in for the paper's one-network-per-species ensemble. Layers run on
+ * the tensor cores in BF16 with FP32 accumulation; parameters are kept in FP32.
+ * The bath species is closed by mass conservation (dY_bath = -sum dY_k).
+ */
+typedef struct chem_mlp chem_mlp;
+
+typedef struct {
+    int32_t n_hidden[3]; /* hidden widths, multiples of 8 (Sec. 3.2: 1600, 800, 400) */
+    int32_t chunk;       /* cells per inference chunk (0 = 262144): sets the activation workspace */
+    int32_t max_batch;   /* largest training batch (0 = 4096) */
+    int32_t _pad;
+    double dt;           /* the flow step the network predicts, s (Sec. 3.1: 1e-6) */
+} chem_mlp_desc;
+
+enum { CHEM_PREC_BF16 = 0, CHEM_PREC_FP8 = 1 };
+
+/* Creates a network for the mechanism's species (inputs N + 2, outputs N - 1)
+ * with seeded U(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and unit statistics.
+ * Allocates all device memory it will use (parameters, Adam moments,
+ * inference and training workspaces). */
+int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc, uint64_t seed, chem_mlp **out);
+int chem_mlp_free(chem_mlp *mlp);
+/* widths[5] = {N + 2, h1, h2, h3, N - 1} */
+int chem_mlp_dims(const chem_mlp *mlp, int32_t *widths);
+/* Number of parameters: sum over the 4 layers of out * in + out. */
+int64_t chem_mlp_nparams(const chem_mlp *mlp);
+/* Host float arrays of chem_mlp_nparams values, layer by layer: W[out][in]
+ * row-major then b[out]. set_params also resets the Adam state. get_grads
+ * returns the gradients of the last mlp_train_step in the same layout. */
+int chem_mlp_set_params(chem_mlp *mlp, const float *host);
+int chem_mlp_get_params(const chem_mlp *mlp, float *host);
+int chem_mlp_get_grads(const chem_mlp *mlp, float *host);
+/* Z-score statistics, host doubles: mu_x, sd_x [N + 2] of the inputs and
+ * mu_u, sd_u [N - 1] of the outputs (sd below 1e-12 is replaced by 1). */
+int chem_mlp_set_norm(chem_mlp *mlp, const double *mu_x, const double *sd_x, const double *mu_u, const double *sd_u);
+int chem_mlp_get_norm(const chem_mlp *mlp, double *mu_x, double *sd_x, double *mu_u, double *sd_u);
+/* Computes and sets the statistics (FP64, population standard deviation) of n
+ * training pairs: inputs from (T, p, Y) and outputs from u* = Y1 - Y, where Y1
+ * [N][ld] is the state after dt (device, SoA). Synchronises the stream. */
+int chem_mlp_fit_norm(chem_mlp *mlp, int64_t n, int64_t ld, const double *T, const double *p, const double *Y,
+                      const double *Y1, chem_stream_t stream);
+/* Normalised network outputs u [ncells][ldu] (float, device) for SoA states. */
+int chem_mlp_forward(const chem_mlp *mlp, int64_t ncells, int64_t ld, const double *T, const double *p,
+                     const double *Y, float *u, int64_t ldu, chem_stream_t stream);
+/* Checkpoint (host path): statistics, FP32 parameters, Adam moments and step
+ * count, with a version header and an FNV-1a checksum. Training resumed from a
+ * checkpoint continues bit for bit (training is deterministic). load checks
+ * the species against the mechanism and returns CHEM_EIO on a damaged file. */
+int chem_mlp_save(const chem_mlp *mlp, const char *path);
+int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
+/* Sticky error word of the network's pipeline waits (0 = none); synchronises the device. */
+int chem_mlp_error(const chem_mlp *mlp, int *host_err);
+
+/* ---------------------------------------------------------------------------
+ * chem_step_ann -- the learned method: advance every cell by the network
+ * ---------------------------------------------------------------------------
+ * Sec. 3.2: the network predicts u*(t) = Y(t + dt) - Y(t) from (T, p, Y). Per
+ * cell: dY = sigma_u u + mu_u for the output species, dY_bath = -sum dY,
+ * Y' = max(Y + dY, 0) renormalised to sum 1, and T' solves h(T', Y') = h(T, Y)
+ * (adiabatic, constant pressure) by Newton iteration on the NASA-7 enthalpy.
+ * T [ld], Y [N][ld] (double, device) are updated in place; p [ld] is read.
+ * dt must equal the dt the network was created for (CHEM_EINVAL otherwise).
+ * prec: CHEM_PREC_BF16. status [ld] (int32, device, may be NULL) receives
+ * CHEM_CELL_OK. fallback: options of the stiff integrator for cells routed to
+ * it (reserved; may be NULL).
+ */
+int chem_step_ann(const chem_mech *mech, const chem_mlp *mlp, int64_t ncells, int64_t ld, double dt, int prec,
+                  const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
+                  chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------
+ * mlp_train_step -- one Adam step on the L1 loss of Eq. 5
+ * ---------------------------------------------------------------------------
+ * L = (1/B) sum_i |u*_i - u_i|_1 on normalised outputs (Sec. 3.2, Eq. 5),
+ * gradients by back-propagation through the same tensor-core layers, then
+ * Adam (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on the FP32
+ * parameters. The batch is rows idx[0..batch) (int32, device) of a training
+ * set of SoA pairs with leading dimension ld: the state (T, p, Y) at t and the
+ * mass fractions Y1 at t + dt, so the target is u* = Y1 - Y; idx == NULL takes
+ * rows 0..batch-1. batch: a multiple of 8, at most max_batch. loss_dev
+ * (float, device, may be NULL) receives L. Deterministic: no atomics.
+ */
+int mlp_train_step(chem_mlp *mlp, int64_t batch, const int32_t *idx, int64_t ld, const double *T, const double *p,
+                   const double *Y, const double *Y1, float lr, float *loss_dev, chem_stream_t stream);
+
 /* Last error message of the calling thread ("" if none). */
 const char *chem_last_error(void);
 

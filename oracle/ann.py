@@ -1,0 +1,79 @@
+"""FP64 oracle of the learned step (TEST INFRASTRUCTURE ONLY), Sec. 3.2.
+
+prologue -> network -> epilogue, written out plainly:
+  x = (T, p, F(Y)),  z = (x - mu_x) / sd_x            (Box-Cox and Z-score, Sec. 3.2)
+  u = network(z)                                       (GELU hidden layers)
+  dY_k = sd_u u_k + mu_u  for the non-bath species      (u* = Y(t+dt) - Y(t), Sec. 3.2)
+  dY_bath = -sum_k dY_k                                 (mass conservation)
+  Y' = max(Y + dY, 0) / sum(max(Y + dY, 0))
+  T' : h(T', Y') = h(T, Y)  (adiabatic, constant p), Newton to |dT| < 1e-10 K.
+round_bf16 rounds the operands at the points where the GPU stores BF16 (the
+network input, the weights and each hidden activation); accumulation stays FP64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import mlp as M
+
+
+def to_bf16(x):
+    """Round-to-nearest-even to BF16 (returned as float64)."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def out_species(mech):
+    return [k for k in range(mech.N) if k != mech.bath]
+
+
+def network(layers, z, round_bf16=False):
+    h = np.asarray(z, np.float64)
+    if round_bf16:
+        h = to_bf16(h)
+    for i, (W, b) in enumerate(layers):
+        Wq = to_bf16(W) if round_bf16 else W
+        pre = h @ Wq.T + b
+        if i < len(layers) - 1:
+            h = M.gelu(pre)
+            if round_bf16:
+                h = to_bf16(h)
+        else:
+            h = pre
+    return h
+
+
+def forward_u(mech, layers, stats, T, p, Y, round_bf16=False):
+    mu_x, sd_x, mu_u, sd_u = stats
+    x = M.features(T, p, Y)
+    z = (x - mu_x) / sd_x
+    if round_bf16:
+        # the device forms z in FP32
+        z = np.asarray(z, np.float32).astype(np.float64)
+    return network(layers, z, round_bf16)
+
+
+def step_ann(mech, layers, stats, T, p, Y, round_bf16=False):
+    """Returns (T', Y') for SoA inputs T[n], p[n], Y[N, n]."""
+    import oracle as O
+    mu_x, sd_x, mu_u, sd_u = stats
+    u = forward_u(mech, layers, stats, T, p, Y, round_bf16)
+    dY = u * sd_u + mu_u
+    Yn = np.array(Y, dtype=np.float64)
+    sp = out_species(mech)
+    Yn[sp, :] += dY.T
+    Yn[mech.bath, :] -= dY.sum(axis=1)
+    Yn = np.maximum(Yn, 0.0)
+    Yn /= Yn.sum(axis=0, keepdims=True)
+    n = T.shape[0]
+    h0 = O.props(mech, T, p, Y)[1]
+    Tn = np.array(T, dtype=np.float64)
+    for _ in range(50):
+        cp, h, *_ = O.props(mech, Tn, p, Yn)
+        d = (h - h0) / cp
+        Tn = Tn - d
+        if np.all(np.abs(d[:n]) < 1e-10):
+            break
+    return Tn, Yn

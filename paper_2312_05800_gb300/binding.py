@@ -32,6 +32,14 @@ class chem_ode_opts(ctypes.Structure):
                 ("h0", ctypes.c_double), ("max_steps", ctypes.c_int32), ("_pad", ctypes.c_int32)]
 
 
+class chem_mlp_desc(ctypes.Structure):
+    _fields_ = [("n_hidden", ctypes.c_int32 * 3), ("chunk", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("_pad", ctypes.c_int32), ("dt", ctypes.c_double)]
+
+
+CHEM_PREC_BF16, CHEM_PREC_FP8 = 0, 1
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -56,6 +64,24 @@ def lib() -> ctypes.CDLL:
     L.chem_ode_opts_default.restype = None
     L.chem_step_stiff.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
     L.chem_step_stiff_noalloc.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
+    L.chem_dense_bf16.argtypes = [i64, i32, i32, vp, i64, vp, i64, vp, i32, vp, i64, i32, vp, vp]
+    L.chem_mlp_create.argtypes = [vp, ctypes.POINTER(chem_mlp_desc), ctypes.c_uint64, ctypes.POINTER(vp)]
+    L.chem_mlp_free.argtypes = [vp]
+    L.chem_mlp_dims.argtypes = [vp, vp]
+    L.chem_mlp_nparams.argtypes = [vp]
+    L.chem_mlp_nparams.restype = ctypes.c_int64
+    L.chem_mlp_set_params.argtypes = [vp, vp]
+    L.chem_mlp_get_params.argtypes = [vp, vp]
+    L.chem_mlp_get_grads.argtypes = [vp, vp]
+    L.chem_mlp_set_norm.argtypes = [vp, vp, vp, vp, vp]
+    L.chem_mlp_get_norm.argtypes = [vp, vp, vp, vp, vp]
+    L.chem_mlp_fit_norm.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+    L.chem_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, i64, vp]
+    L.chem_mlp_error.argtypes = [vp, vp]
+    L.chem_mlp_save.argtypes = [vp, ctypes.c_char_p]
+    L.chem_mlp_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
+    L.chem_step_ann.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp]
+    L.mlp_train_step.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, ctypes.c_float, vp, vp]
     L.chem_last_error.restype = ctypes.c_char_p
     L.chem_version.restype = ctypes.c_char_p
     _lib = L
@@ -155,6 +181,112 @@ def chem_step_stiff_noalloc(mech: Mech, ncells: int, ld: int, dt: float, opts: O
     _check(lib().chem_step_stiff_noalloc(mech.handle, ncells, ld, float(dt),
                                          ctypes.byref(opts) if opts is not None else None, _ptr(T), _ptr(p), _ptr(Y),
                                          _ptr(status), _ptr(nsteps), _stream(stream)))
+
+
+def chem_dense_bf16(M: int, N: int, K: int, x, ldx: int, W, ldw: int, b, act: int, y, ldy: int, tile_n: int = 0,
+                    err=None, stream=None):
+    _check(lib().chem_dense_bf16(M, N, K, _ptr(x), ldx, _ptr(W), ldw, _ptr(b), act, _ptr(y), ldy, tile_n, _ptr(err),
+                                 _stream(stream)))
+
+
+class Mlp:
+    """Library-owned network handle (chem_mlp_create / chem_mlp_free)."""
+
+    def __init__(self, mech: Mech, hidden=(1600, 800, 400), dt=1e-6, seed=0, chunk=0, max_batch=0):
+        import numpy as np
+        d = chem_mlp_desc()
+        for i in range(3):
+            d.n_hidden[i] = int(hidden[i])
+        d.chunk, d.max_batch, d.dt = int(chunk), int(max_batch), float(dt)
+        h = ctypes.c_void_p()
+        _check(lib().chem_mlp_create(mech.handle, ctypes.byref(d), ctypes.c_uint64(seed), ctypes.byref(h)))
+        self.handle = h.value
+        w = np.zeros(5, np.int32)
+        _check(lib().chem_mlp_dims(self.handle, w.ctypes.data))
+        self.widths = [int(v) for v in w]
+        self.nparams = int(lib().chem_mlp_nparams(self.handle))
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        _check(lib().chem_mlp_set_params(self.handle, a.ctypes.data))
+
+    def get_params(self):
+        import numpy as np
+        a = np.zeros(self.nparams, np.float32)
+        _check(lib().chem_mlp_get_params(self.handle, a.ctypes.data))
+        return a
+
+    def get_grads(self):
+        import numpy as np
+        a = np.zeros(self.nparams, np.float32)
+        _check(lib().chem_mlp_get_grads(self.handle, a.ctypes.data))
+        return a
+
+    def set_norm(self, mu_x, sd_x, mu_u, sd_u):
+        import numpy as np
+        arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (mu_x, sd_x, mu_u, sd_u)]
+        _check(lib().chem_mlp_set_norm(self.handle, *[a.ctypes.data for a in arrs]))
+
+    def get_norm(self):
+        import numpy as np
+        nin, nout = self.widths[0], self.widths[4]
+        arrs = [np.zeros(nin), np.zeros(nin), np.zeros(nout), np.zeros(nout)]
+        _check(lib().chem_mlp_get_norm(self.handle, *[a.ctypes.data for a in arrs]))
+        return arrs
+
+    def save(self, path: str):
+        _check(lib().chem_mlp_save(self.handle, path.encode()))
+
+    @classmethod
+    def load(cls, mech: Mech, path: str) -> "Mlp":
+        import numpy as np
+        h = ctypes.c_void_p()
+        _check(lib().chem_mlp_load(mech.handle, path.encode(), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.handle = h.value
+        w = np.zeros(5, np.int32)
+        _check(lib().chem_mlp_dims(self.handle, w.ctypes.data))
+        self.widths = [int(v) for v in w]
+        self.nparams = int(lib().chem_mlp_nparams(self.handle))
+        return self
+
+    def error(self) -> int:
+        e = ctypes.c_int()
+        _check(lib().chem_mlp_error(self.handle, ctypes.byref(e)))
+        return e.value
+
+    def free(self):
+        if self.handle:
+            _check(lib().chem_mlp_free(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def chem_mlp_fit_norm(mlp: Mlp, n: int, ld: int, T, p, Y, Y1, stream=None):
+    _check(lib().chem_mlp_fit_norm(mlp.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Y1), _stream(stream)))
+
+
+def chem_mlp_forward(mlp: Mlp, ncells: int, ld: int, T, p, Y, u, ldu: int, stream=None):
+    _check(lib().chem_mlp_forward(mlp.handle, ncells, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(u), ldu, _stream(stream)))
+
+
+def chem_step_ann(mech: Mech, mlp: Mlp, ncells: int, ld: int, dt: float, prec: int, fallback, T, p, Y, status=None,
+                  stream=None):
+    _check(lib().chem_step_ann(mech.handle, mlp.handle, ncells, ld, float(dt), prec,
+                               ctypes.byref(fallback) if fallback is not None else None, _ptr(T), _ptr(p), _ptr(Y),
+                               _ptr(status), _stream(stream)))
+
+
+def mlp_train_step(mlp: Mlp, batch: int, idx, ld: int, T, p, Y, Y1, lr: float, loss=None, stream=None):
+    _check(lib().mlp_train_step(mlp.handle, batch, _ptr(idx), ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Y1),
+                                ctypes.c_float(lr), _ptr(loss), _stream(stream)))
 
 
 def chem_last_error() -> str:

@@ -1,0 +1,255 @@
+// gemm.cuh -- persistent, warp-specialised BF16 GEMM on the 5th-generation
+// tensor cores: Y[M][N] = epilogue(X[M][K] * W[N][K]^T), FP32 accumulation.
+// This is the dense contraction of every MLP layer (Sec. 3.2: hidden layers of
+// 1600, 800 and 400 GELU units), forward and backward.
+//
+// Roles (192 threads per CTA, one CTA per SM, static round-robin over tiles):
+//   warp 0      TMA producer: 128 x 64 tile of X and BN x 64 tile of W per
+//               k-block into a STAGES-deep ring (128-byte swizzle).
+//   warp 1      TMEM allocation and the single MMA-issuing thread:
+//               tcgen05.mma kind::f16, M = 128, N = BN, K = 16 per instruction,
+//               accumulating in one of two TMEM buffers (columns 0 and 256).
+//   warps 2..5  epilogue: tcgen05.ld of 16-column chunks (warp w reads TMEM
+//               lanes 32 (w % 4) .. +31, i.e. output rows), then the functor.
+// Ragged M, N and K: TMA fills out-of-range operand elements with zeros and
+// the epilogue functors mask rows >= M and columns >= N.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "tc.cuh"
+
+namespace chemgb {
+
+constexpr int kGemmThreads = 192;
+constexpr int kBM = 128;
+constexpr int kBK = 64;
+constexpr uint32_t kTmemCols = 512;
+
+template <int BN, int STAGES>
+struct GemmSmem {
+    static constexpr uint32_t kABytes = kBM * kBK * 2;
+    static constexpr uint32_t kBBytes = BN * kBK * 2;
+    static constexpr uint32_t kTiles = STAGES * (kABytes + kBBytes);
+    static constexpr uint32_t kBars = (2 * STAGES + 5) * 8 + 16;
+    static constexpr uint32_t kTotal = 1024 + kTiles + kBars;
+    static_assert(kBBytes % 1024 == 0, "B tile must keep 1024-byte alignment");
+};
+
+__device__ __forceinline__ float gelu_exact(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+// ---- epilogue functors: (row, first column, 16 accumulator values) --------
+
+// Y = bf16(GELU(acc + b)); optionally also the FP32 pre-activation acc + b.
+struct EpiGelu {
+    int M, N;
+    const float *bias;
+    __nv_bfloat16 *out;
+    int64_t ldo;
+    float *pre;      // may be null
+    int64_t ldp;
+    __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
+        if (row >= M) return;
+        float z[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = v[i] + ((col0 + i < N && bias) ? __ldg(bias + col0 + i) : 0.0f);
+        __nv_bfloat16 *o = out + (int64_t)row * ldo + col0;
+        if (col0 + 16 <= N && (ldo & 7) == 0) {
+            __align__(16) __nv_bfloat162 h[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) h[i] = __floats2bfloat162_rn(gelu_exact(z[2 * i]), gelu_exact(z[2 * i + 1]));
+            reinterpret_cast<uint4 *>(o)[0] = reinterpret_cast<const uint4 *>(h)[0];
+            reinterpret_cast<uint4 *>(o)[1] = reinterpret_cast<const uint4 *>(h)[1];
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < N) o[i] = __float2bfloat16_rn(gelu_exact(z[i]));
+        }
+        if (pre) {
+            float *q = pre + (int64_t)row * ldp + col0;
+            if (col0 + 16 <= N && (ldp & 3) == 0) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    reinterpret_cast<float4 *>(q)[i] = make_float4(z[4 * i], z[4 * i + 1], z[4 * i + 2], z[4 * i + 3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (col0 + i < N) q[i] = z[i];
+            }
+        }
+    }
+};
+
+// Y = acc + b in FP32 (b may be null).
+struct EpiLinear {
+    int M, N;
+    const float *bias;
+    float *out;
+    int64_t ldo;
+    __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
+        if (row >= M) return;
+        float *o = out + (int64_t)row * ldo + col0;
+        if (col0 + 16 <= N && (ldo & 3) == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 t;
+                t.x = v[4 * i] + (bias ? __ldg(bias + col0 + 4 * i) : 0.0f);
+                t.y = v[4 * i + 1] + (bias ? __ldg(bias + col0 + 4 * i + 1) : 0.0f);
+                t.z = v[4 * i + 2] + (bias ? __ldg(bias + col0 + 4 * i + 2) : 0.0f);
+                t.w = v[4 * i + 3] + (bias ? __ldg(bias + col0 + 4 * i + 3) : 0.0f);
+                reinterpret_cast<float4 *>(o)[i] = t;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (col0 + i < N) o[i] = v[i] + (bias ? __ldg(bias + col0 + i) : 0.0f);
+        }
+    }
+};
+
+// Y = bf16(acc * GELU'(Z)), Z the FP32 pre-activation of the layer below (backward pass).
+struct EpiGeluGrad {
+    int M, N;
+    const float *z;
+    int64_t ldz;
+    __nv_bfloat16 *out;
+    int64_t ldo;
+    __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
+        if (row >= M) return;
+        const float *zr = z + (int64_t)row * ldz + col0;
+        __nv_bfloat16 *o = out + (int64_t)row * ldo + col0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (col0 + i < N) o[i] = __float2bfloat16_rn(v[i] * gelu_grad(zr[i]));
+    }
+};
+
+// ---- kernel ---------------------------------------------------------------
+
+template <int BN, int STAGES, class Epi>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    gemm_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                   int K, Epi epi, int *err) {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
+    using L = GemmSmem<BN, STAGES>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + STAGES * L::kABytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kTiles);
+    uint64_t *full = bars;
+    uint64_t *empty = bars + STAGES;
+    uint64_t *tfull = bars + 2 * STAGES;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *drain = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m_tiles = (M + kBM - 1) / kBM, n_tiles = (N + BN - 1) / BN;
+    const int tiles = m_tiles * n_tiles;
+    const int kblocks = (K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 128); }
+        tc::mbar_init(drain, 1);
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, kTmemCols);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            tc::tma_prefetch_desc(&tmA);
+            tc::tma_prefetch_desc(&tmB);
+            int it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+                const int m_blk = tile / n_tiles, n_blk = tile % n_tiles;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, tc::kErrTimeoutEmpty); ok = false; break; }
+                    tc::mbar_arrive_expect_tx(&full[s], L::kABytes + L::kBBytes);
+                    tc::tma_load_2d(sA + s * L::kABytes, &tmA, &full[s], kb * kBK, m_blk * kBM);
+                    tc::tma_load_2d(sB + s * L::kBBytes, &tmB, &full[s], kb * kBK, n_blk * BN);
+                }
+            }
+            // every issued load lands before the CTA may exit (bounded)
+            for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+                if (!tc::mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) {
+                    atomicExch(err, tc::kErrTimeoutDrain);
+                    break;
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+            int it = 0, t = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
+                const int acc = t & 1;
+                const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+                if (!tc::mbar_wait(&tempty[acc], aph ^ 1u)) { atomicExch(err, tc::kErrTimeoutTmemEmpty); break; }
+                tc::tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)acc * 256u;
+                for (int kb = 0; kb < kblocks; ++kb, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                    if (!tc::mbar_wait(&full[s], ph)) { atomicExch(err, tc::kErrTimeoutFull); ok = false; break; }
+                    tc::tc_fence_after();
+                    const uint32_t a0 = tc::smem_u32(sA + s * L::kABytes);
+                    const uint32_t b0 = tc::smem_u32(sB + s * L::kBBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk)
+                        tc::umma_f16(d_tmem, tc::sdesc_kmajor_sw128(a0 + kk * 32), tc::sdesc_kmajor_sw128(b0 + kk * 32),
+                                     idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    tc::umma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                tc::umma_commit(&tfull[acc]);
+            }
+            // all MMAs issued by this thread complete before TMEM is released (bounded)
+            tc::umma_commit(drain);
+            if (!tc::mbar_wait(drain, 0)) atomicExch(err, tc::kErrTimeoutDrain);
+        }
+    } else {
+        const int quad = warp & 3;
+        int t = 0;
+        for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
+            const int acc = t & 1;
+            const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+            if (!tc::mbar_wait(&tfull[acc], aph)) { atomicExch(err, tc::kErrTimeoutTmemFull); break; }
+            tc::tc_fence_after();
+            const int m_blk = tile / n_tiles, n_blk = tile % n_tiles;
+            const int row = m_blk * kBM + quad * 32 + lane;
+            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u;
+#pragma unroll 1
+            for (int c = 0; c < BN / 16; ++c) {
+                const int col0 = n_blk * BN + c * 16;
+                if (col0 >= N) break;               // warp-uniform
+                float v[16];
+                tc::tmem_ld16(tbase + (uint32_t)(c * 16), v);
+                epi(row, col0, v);
+            }
+            tc::tc_fence_before();
+            tc::mbar_arrive(&tempty[acc]);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+}  // namespace chemgb

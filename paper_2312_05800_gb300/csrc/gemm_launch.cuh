@@ -1,0 +1,124 @@
+// gemm_launch.cuh -- host-side launch of gemm_tn_kernel: TMA descriptors,
+// tile-width dispatch and the persistent grid. Included by the translation
+// units that instantiate the kernel for their epilogue.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+#include <string>
+
+#include "gemm.cuh"
+#include "internal.cuh"
+
+namespace chemgb {
+
+// cuTensorMapEncodeTiled resolved through the runtime (no link-time libcuda dependency).
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 2-D BF16 tensor map over a row-major [rows][cols] matrix with row stride ld
+// (elements), box = box_rows x 64 columns, 128-byte swizzle, zero fill outside.
+inline int make_tmap_bf16(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    if (!aligned16(ptr) || (ld * 2) % 16 != 0)
+        return set_error(CHEM_EINVAL, "GEMM operand: base must be 16-byte aligned and rows a multiple of 16 bytes");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled_fn();
+    if (!enc) return set_error(CHEM_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims,
+                                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(CHEM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return CHEM_OK;
+}
+
+inline int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    return sms;
+}
+
+template <int BN, int STAGES, class Epi>
+int launch_gemm_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K, const Epi &epi,
+                   int *err, cudaStream_t st, int max_ctas) {
+    using L = GemmSmem<BN, STAGES>;
+    static bool configured = false;
+    if (!configured) {
+        int rc = check_cuda(cudaFuncSetAttribute(gemm_tn_kernel<BN, STAGES, Epi>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kTotal),
+                            "GEMM smem attribute");
+        if (rc) return rc;
+        configured = true;
+    }
+    CUtensorMap ta, tb;
+    int rc = make_tmap_bf16(&ta, X, M, K, ldx, kBM);
+    if (rc) return rc;
+    rc = make_tmap_bf16(&tb, W, N, K, ldw, BN);
+    if (rc) return rc;
+    const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
+    int grid = num_sms();
+    if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
+    if (tiles < grid) grid = tiles;
+    gemm_tn_kernel<BN, STAGES, Epi><<<grid, kGemmThreads, L::kTotal, st>>>(ta, tb, M, N, K, epi, err);
+    return check_cuda(cudaGetLastError(), "GEMM launch");
+}
+
+// Tile widths the library is built with (the autotuner picks among them).
+constexpr int kTileWidths[] = {32, 64, 128, 160, 208, 256};
+
+template <class Epi>
+int launch_gemm(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K,
+                const Epi &epi, int *err, cudaStream_t st, int max_ctas = 0) {
+    if (M <= 0 || N <= 0 || K <= 0) return CHEM_OK;
+    switch (bn) {
+        case 32: return launch_gemm_bn<32, 8>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
+        case 64: return launch_gemm_bn<64, 8>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
+        case 128: return launch_gemm_bn<128, 6>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
+        case 160: return launch_gemm_bn<160, 5>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
+        case 208: return launch_gemm_bn<208, 4>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
+        case 256: return launch_gemm_bn<256, 4>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
+        default: return set_error(CHEM_EINVAL, "GEMM: unsupported tile width " + std::to_string(bn));
+    }
+}
+
+// Default tile width for an output width N (fewest padded columns, then widest tile).
+inline int default_tile_width(int N) {
+    int best = 256;
+    long best_pad = -1;
+    for (int bn : kTileWidths) {
+        if (bn < 64 && N > 64) continue;
+        long pad = (long)((N + bn - 1) / bn) * bn - N;
+        if (best_pad < 0 || pad < best_pad || (pad == best_pad && bn > best)) { best = bn; best_pad = pad; }
+    }
+    return best;
+}
+
+// Forward declarations of the per-epilogue launchers (one translation unit each).
+int gemm_gelu(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K, const float *bias,
+              void *out, int64_t ldo, float *pre, int64_t ldp, int *err, cudaStream_t st, int max_ctas = 0);
+int gemm_linear(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K,
+                const float *bias, float *out, int64_t ldo, int *err, cudaStream_t st, int max_ctas = 0);
+int gemm_gelu_grad(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K,
+                   const float *z, int64_t ldz, void *out, int64_t ldo, int *err, cudaStream_t st, int max_ctas = 0);
+
+}  // namespace chemgb

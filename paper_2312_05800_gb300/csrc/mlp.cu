@@ -1,0 +1,879 @@
+// mlp.cu -- the learned chemistry of Sec. 3.2 on the GPU: the network handle,
+// the per-cell prologue (Box-Cox + Z-score -> BF16 rows), the tensor-core
+// layers (gemm_*.cu), the per-cell epilogue (de-normalised dY, bath closure,
+// clamp + renormalise, T from the conserved enthalpy), and training (L1 loss
+// of Eq. 5, backward through the same GEMM kernel, Adam).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gemm_launch.cuh"
+
+namespace chemgb {
+namespace {
+
+constexpr int kLayers = 4;
+constexpr float kLambdaBC = 0.1f;     // Box-Cox lambda (Sec. 3.2)
+constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
+
+inline int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct Layer {
+    int in, out;          // logical widths
+    int kin;              // padded input width (row length of W, multiple of 8)
+    int outp;             // padded output width (multiple of 8)
+    float *W, *b;         // FP32 master [out][kin], [outp]
+    __nv_bfloat16 *Wb;    // BF16 [out][kin]
+    __nv_bfloat16 *Wt;    // BF16 transposed [in][outp]
+    float *mW, *vW, *mb, *vb;   // Adam moments
+    float *gW, *gb;       // gradients of the last training step
+    int tile;             // forward tile width
+};
+
+}  // namespace chemgb
+
+struct chem_mlp {
+    int N, bath, n_in, n_in_pad, n_out, n_out_pad;
+    int widths[5];
+    int out_species[64];
+    double dt;
+    int64_t chunk, max_batch;
+    chemgb::Layer L[chemgb::kLayers];
+    float *mu_x, *isd_x, *mu_u, *sd_u;     // device FP32 Z-score statistics
+    int *out_sp_dev;                        // [n_out] species of each output
+    double h_mu_x[66], h_sd_x[66], h_mu_u[64], h_sd_u[64];
+    // inference workspace
+    __nv_bfloat16 *a0, *h[3];
+    float *out;
+    // training workspace
+    __nv_bfloat16 *tx0, *th[3], *tdout, *tdz[3], *tT0, *tT1;
+    float *tz[3], *tout, *loss_part;
+    int *err;
+    int64_t adam_t;
+    void *blob;
+    size_t blob_bytes;
+    int device;
+    uint64_t seed;
+};
+
+namespace chemgb {
+namespace {
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+// Rows z = (x - mu) / sigma, x = (T, p, F(Y_1..Y_N)), F(Y) = (max(Y,0)^0.1 - 1)/0.1, as BF16.
+__global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict__ T, const double *__restrict__ p,
+                                const double *__restrict__ Y, const int32_t *__restrict__ idx, int N, int n_in_pad,
+                                const float *__restrict__ mu, const float *__restrict__ isd,
+                                __nv_bfloat16 *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t c = idx ? (int64_t)idx[i] : i;
+    __nv_bfloat16 *row = out + i * n_in_pad;
+    for (int j0 = 0; j0 < n_in_pad; j0 += 8) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = j0 + u;
+            float x;
+            if (j == 0) x = (float)T[c];
+            else if (j == 1) x = (float)p[c];
+            else if (j < N + 2) {
+                const float y = fmaxf((float)Y[(int64_t)(j - 2) * ld + c], 0.0f);
+                x = (powf(y, kLambdaBC) - 1.0f) * (1.0f / kLambdaBC);
+            } else {
+                x = 0.0f;
+            }
+            const float z = (j < N + 2) ? (x - __ldg(mu + j)) * __ldg(isd + j) : 0.0f;
+            v[u] = __float2bfloat16_rn(z);
+        }
+        *reinterpret_cast<uint4 *>(row + j0) = *reinterpret_cast<const uint4 *>(v);
+    }
+}
+
+// NASA-7 mixture h (J/kg) and cp (J/kg/K) in FP32 from the FP32 property tables.
+__device__ __forceinline__ void mix_h_cp(const PropTables<float> &tb, int N, float T_mid, float T, const double *Yk,
+                                         float &h, float &cp) {
+    const int rng = (T >= T_mid) ? 1 : 0;
+    float hs = 0.0f, cs = 0.0f;
+    for (int k = 0; k < N; ++k) {
+        const float *a = tb.nasa_cp + (rng * N + k) * 5;
+        const float *b = tb.nasa_h + (rng * N + k) * 6;
+        float c = __ldg(a + 4);
+        c = fmaf(c, T, __ldg(a + 3)); c = fmaf(c, T, __ldg(a + 2)); c = fmaf(c, T, __ldg(a + 1)); c = fmaf(c, T, __ldg(a));
+        float hh = __ldg(b + 4);
+        hh = fmaf(hh, T, __ldg(b + 3)); hh = fmaf(hh, T, __ldg(b + 2)); hh = fmaf(hh, T, __ldg(b + 1));
+        hh = fmaf(hh, T, __ldg(b));
+        hh = hh * T + __ldg(b + 5);                 // H_k / R
+        const float yw = (float)Yk[k] * __ldg(tb.invW + k);
+        hs = fmaf(yw, hh, hs);
+        cs = fmaf(yw, c, cs);
+    }
+    h = hs * (float)kR;
+    cp = cs * (float)kR;
+}
+
+// Per cell: dY_k = sigma_k u_k + mu_k (output species), dY_bath = -sum dY_k,
+// Y' = max(Y + dY, 0) renormalised, T' from h(T', Y') = h(T, Y) by Newton.
+__global__ void epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu, int N, int bath,
+                                int n_out, const int *__restrict__ out_sp, const float *__restrict__ mu_u,
+                                const float *__restrict__ sd_u, PropTables<float> tb, float T_mid,
+                                double *__restrict__ T, double *__restrict__ Y, int32_t *__restrict__ status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double y[kMaxSpecies];
+    double y0[kMaxSpecies];
+    for (int k = 0; k < N; ++k) { y0[k] = Y[(int64_t)k * ld + i]; y[k] = y0[k]; }
+    const float *ur = u + i * ldu;
+    double sum_dy = 0.0;
+    for (int j = 0; j < n_out; ++j) {
+        const double dy = (double)fmaf(__ldg(sd_u + j), ur[j], __ldg(mu_u + j));
+        y[out_sp[j]] += dy;
+        sum_dy += dy;
+    }
+    y[bath] -= sum_dy;
+    double s = 0.0;
+    for (int k = 0; k < N; ++k) { y[k] = fmax(y[k], 0.0); s += y[k]; }
+    const double inv = 1.0 / s;
+    for (int k = 0; k < N; ++k) y[k] *= inv;
+    const float T0 = (float)T[i];
+    float h0, cp0;
+    mix_h_cp(tb, N, T_mid, T0, y0, h0, cp0);
+    float Tn = T0;
+    for (int it = 0; it < 30; ++it) {
+        float h1, cp1;
+        mix_h_cp(tb, N, T_mid, Tn, y, h1, cp1);
+        const float d = (h1 - h0) / cp1;
+        Tn -= d;
+        if (fabsf(d) < 1e-4f) break;
+    }
+    T[i] = (double)Tn;
+    for (int k = 0; k < N; ++k) Y[(int64_t)k * ld + i] = y[k];
+    if (status) status[i] = CHEM_CELL_OK;
+}
+
+// L1 loss of Eq. 5 on normalised outputs; dL/du = sign(u - u*)/B written as BF16.
+__global__ void l1_loss_kernel(int64_t B, const float *__restrict__ u, int ldu, const int32_t *__restrict__ idx,
+                               int64_t ld, const double *__restrict__ Y0, const double *__restrict__ Y1, int n_out,
+                               const int *__restrict__ out_sp,
+                               const float *__restrict__ mu_u, const float *__restrict__ sd_u,
+                               __nv_bfloat16 *__restrict__ dout, int lddo, float *__restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    const int64_t c = idx ? (int64_t)idx[i] : i;
+    const float invB = 1.0f / (float)B;
+    float acc = 0.0f;
+    for (int j = 0; j < lddo; ++j) {
+        float g = 0.0f;
+        if (j < n_out) {
+            const int64_t q = (int64_t)out_sp[j] * ld + c;
+            const float target = ((float)(Y1[q] - Y0[q]) - __ldg(mu_u + j)) / __ldg(sd_u + j);
+            const float d = u[i * ldu + j] - target;
+            acc += fabsf(d);
+            g = (d > 0.0f) ? invB : ((d < 0.0f) ? -invB : 0.0f);
+        }
+        dout[i * lddo + j] = __float2bfloat16_rn(g);
+    }
+    part[i] = acc;
+}
+
+// Deterministic sum of the per-sample partials (one block, fixed order), then / B.
+__global__ void loss_reduce_kernel(int64_t B, const float *__restrict__ part, float *__restrict__ loss) {
+    __shared__ float sh[256];
+    float a = 0.0f;
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) a += part[i];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = sh[0] / (float)B;
+}
+
+// Column sums of a BF16 [B][ld] matrix (bias gradients), rows in order.
+__global__ void colsum_kernel(int64_t B, int ncol, const __nv_bfloat16 *__restrict__ g, int ldg,
+                              float *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncol) return;
+    float s = 0.0f;
+    for (int64_t i = 0; i < B; ++i) s += __bfloat162float(g[i * ldg + j]);
+    out[j] = s;
+}
+
+// out[c][r] = in[r][c] for a BF16 [rows][cols] matrix (row strides ldi, ldo), 32x32 tiles.
+__global__ void transpose_kernel(int rows, int cols, const __nv_bfloat16 *__restrict__ in, int64_t ldi,
+                                 __nv_bfloat16 *__restrict__ out, int64_t ldo) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        t[k][threadIdx.x] = (r < rows && c < cols) ? in[(int64_t)r * ldi + c] : __float2bfloat16_rn(0.0f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < cols && r < rows) out[(int64_t)c * ldo + r] = t[threadIdx.x][k];
+    }
+}
+
+// Adam (Kingma and Ba 2015) on one layer; refreshes the BF16 and transposed BF16 copies.
+__global__ void adam_kernel(int out, int in, int kin, int outp, float *__restrict__ W, float *__restrict__ b,
+                            const float *__restrict__ gW, const float *__restrict__ gb, float *__restrict__ mW,
+                            float *__restrict__ vW, float *__restrict__ mb, float *__restrict__ vb,
+                            __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Wt, float lr, float bc1,
+                            float bc2) {
+    const int64_t nW = (int64_t)out * in;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nW) {
+        const int o = (int)(t / in), k = (int)(t % in);
+        const int64_t q = (int64_t)o * kin + k;
+        const float g = gW[q];
+        const float m = kAdamB1 * mW[q] + (1.0f - kAdamB1) * g;
+        const float v = kAdamB2 * vW[q] + (1.0f - kAdamB2) * g * g;
+        mW[q] = m;
+        vW[q] = v;
+        const float w = W[q] - lr * (m / bc1) / (sqrtf(v / bc2) + kAdamEps);
+        W[q] = w;
+        const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+        Wb[q] = wb;
+        Wt[(int64_t)k * outp + o] = wb;
+    } else if (t < nW + out) {
+        const int o = (int)(t - nW);
+        const float g = gb[o];
+        const float m = kAdamB1 * mb[o] + (1.0f - kAdamB1) * g;
+        const float v = kAdamB2 * vb[o] + (1.0f - kAdamB2) * g * g;
+        mb[o] = m;
+        vb[o] = v;
+        b[o] = b[o] - lr * (m / bc1) / (sqrtf(v / bc2) + kAdamEps);
+    }
+}
+
+// FP32 master -> BF16 copies (after set_params).
+__global__ void refresh_bf16_kernel(int out, int in, int kin, int outp, const float *__restrict__ W,
+                                    __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Wt) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)out * kin) return;
+    const int o = (int)(t / kin), k = (int)(t % kin);
+    const __nv_bfloat16 wb = __float2bfloat16_rn(k < in ? W[t] : 0.0f);
+    Wb[t] = wb;
+    if (k < in) Wt[(int64_t)k * outp + o] = wb;
+}
+
+// Mean and population standard deviation of feature f over n samples, FP64,
+// two passes, one block per feature (fixed reduction order).
+__global__ void norm_stats_kernel(int64_t n, int64_t ld, const double *__restrict__ T, const double *__restrict__ p,
+                                  const double *__restrict__ Y, const double *__restrict__ Y1, int N, int n_in,
+                                  const int *__restrict__ out_sp, double *__restrict__ mean, double *__restrict__ sd) {
+    __shared__ double sh[256];
+    const int f = blockIdx.x;
+    auto feat = [&](int64_t i) -> double {
+        if (f == 0) return T[i];
+        if (f == 1) return p[i];
+        if (f < n_in) {
+            const double y = fmax(Y[(int64_t)(f - 2) * ld + i], 0.0);
+            return (pow(y, 0.1) - 1.0) / 0.1;
+        }
+        const int64_t q = (int64_t)out_sp[f - n_in] * ld + i;
+        return Y1[q] - Y[q];
+    };
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += feat(i);
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    const double m = sh[0] / (double)n;
+    __syncthreads();
+    a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = feat(i) - m;
+        a += d * d;
+    }
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mean[f] = m;
+        sd[f] = sqrt(sh[0] / (double)n);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+
+uint64_t splitmix64(uint64_t &s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int upload_norm(chem_mlp *m) {
+    std::vector<float> mx(m->n_in_pad, 0.f), ix(m->n_in_pad, 0.f), mu(m->n_out_pad, 0.f), su(m->n_out_pad, 1.f);
+    for (int j = 0; j < m->n_in; ++j) {
+        mx[j] = (float)m->h_mu_x[j];
+        ix[j] = (float)(1.0 / m->h_sd_x[j]);
+    }
+    for (int j = 0; j < m->n_out; ++j) {
+        mu[j] = (float)m->h_mu_u[j];
+        su[j] = (float)m->h_sd_u[j];
+    }
+    int rc = check_cuda(cudaMemcpy(m->mu_x, mx.data(), mx.size() * 4, cudaMemcpyHostToDevice), "norm upload");
+    if (!rc) rc = check_cuda(cudaMemcpy(m->isd_x, ix.data(), ix.size() * 4, cudaMemcpyHostToDevice), "norm upload");
+    if (!rc) rc = check_cuda(cudaMemcpy(m->mu_u, mu.data(), mu.size() * 4, cudaMemcpyHostToDevice), "norm upload");
+    if (!rc) rc = check_cuda(cudaMemcpy(m->sd_u, su.data(), su.size() * 4, cudaMemcpyHostToDevice), "norm upload");
+    return rc;
+}
+
+int64_t param_count(const chem_mlp *m) {
+    int64_t n = 0;
+    for (int l = 0; l < kLayers; ++l) n += (int64_t)m->L[l].out * m->L[l].in + m->L[l].out;
+    return n;
+}
+
+// host params (layer-major: W[out][in] row-major, then b[out]) <-> device master (padded rows)
+int copy_params(const chem_mlp *m, float *host, bool to_host, bool grads) {
+    int64_t off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const Layer &L = m->L[l];
+        float *W = grads ? L.gW : L.W;
+        float *b = grads ? L.gb : L.b;
+        cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+        int rc = check_cuda(to_host ? cudaMemcpy2D(host + off, L.in * 4, W, L.kin * 4, L.in * 4, L.out, kind)
+                                    : cudaMemcpy2D(W, L.kin * 4, host + off, L.in * 4, L.in * 4, L.out, kind),
+                            "parameter copy");
+        if (rc) return rc;
+        off += (int64_t)L.out * L.in;
+        rc = check_cuda(to_host ? cudaMemcpy(host + off, b, L.out * 4, kind) : cudaMemcpy(b, host + off, L.out * 4, kind),
+                        "parameter copy");
+        if (rc) return rc;
+        off += L.out;
+    }
+    return CHEM_OK;
+}
+
+int refresh_bf16(chem_mlp *m, cudaStream_t st) {
+    for (int l = 0; l < kLayers; ++l) {
+        const Layer &L = m->L[l];
+        int64_t n = (int64_t)L.out * L.kin;
+        refresh_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L.out, L.in, L.kin, L.outp, L.W, L.Wb, L.Wt);
+    }
+    return check_cuda(cudaGetLastError(), "refresh_bf16");
+}
+
+int check_state_args(int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y, const char *who) {
+    if (ncells < 0 || ld < ncells || (ld & 3) != 0 || ncells > 0x7fffffff)
+        return set_error(CHEM_EINVAL, std::string(who) + ": need 0 <= ncells <= ld < 2^31, ld a multiple of 4");
+    if (ncells > 0 && (!T || !p || !Y)) return set_error(CHEM_EINVAL, std::string(who) + ": null state array");
+    if ((T && !aligned16(T)) || (p && !aligned16(p)) || (Y && !aligned16(Y)))
+        return set_error(CHEM_EINVAL, std::string(who) + ": arrays must be 16-byte aligned");
+    return CHEM_OK;
+}
+
+// prologue + four layers on cells [0, n) of the given SoA pointers; normalised outputs into m->out
+int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p, const double *Y,
+                  cudaStream_t st) {
+    prologue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, T, p, Y, nullptr, m->N, m->n_in_pad, m->mu_x,
+                                                                 m->isd_x, m->a0);
+    int rc = check_cuda(cudaGetLastError(), "prologue");
+    if (rc) return rc;
+    const __nv_bfloat16 *x = m->a0;
+    int64_t ldx = m->n_in_pad;
+    for (int l = 0; l < 3; ++l) {
+        const Layer &L = m->L[l];
+        rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->h[l], L.out, nullptr, 0, m->err, st);
+        if (rc) return rc;
+        x = m->h[l];
+        ldx = L.out;
+    }
+    const Layer &L = m->L[3];
+    return gemm_linear(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->out, m->n_out_pad, m->err, st);
+}
+
+}  // namespace
+}  // namespace chemgb
+
+using namespace chemgb;
+
+extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc, uint64_t seed, chem_mlp **out) {
+    if (!mech || !desc || !out) return set_error(CHEM_EINVAL, "chem_mlp_create: null argument");
+    *out = nullptr;
+    for (int i = 0; i < 3; ++i)
+        if (desc->n_hidden[i] < 8 || desc->n_hidden[i] % 8 != 0 || desc->n_hidden[i] > 8192)
+            return set_error(CHEM_EINVAL, "chem_mlp_create: hidden widths must be multiples of 8 in [8, 8192]");
+    if (!(desc->dt > 0.0)) return set_error(CHEM_EINVAL, "chem_mlp_create: dt must be positive");
+    if (mech->N < 2) return set_error(CHEM_EINVAL, "chem_mlp_create: the mechanism needs at least 2 species");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_create: " + why);
+    chem_mlp *m = new chem_mlp();
+    m->N = mech->N;
+    m->bath = mech->bath;
+    m->n_in = mech->N + 2;
+    m->n_in_pad = (int)pad8(m->n_in);
+    m->n_out = mech->N - 1;
+    m->n_out_pad = (int)pad8(m->n_out);
+    for (int k = 0, j = 0; k < mech->N; ++k)
+        if (k != mech->bath) m->out_species[j++] = k;
+    m->dt = desc->dt;
+    m->chunk = desc->chunk > 0 ? desc->chunk : 262144;
+    m->chunk = (m->chunk + 127) / 128 * 128;
+    m->max_batch = desc->max_batch > 0 ? (desc->max_batch + 7) / 8 * 8 : 4096;
+    m->seed = seed;
+    m->widths[0] = m->n_in;
+    for (int i = 0; i < 3; ++i) m->widths[1 + i] = desc->n_hidden[i];
+    m->widths[4] = m->n_out;
+    for (int l = 0; l < kLayers; ++l) {
+        Layer &L = m->L[l];
+        L.in = m->widths[l];
+        L.out = m->widths[l + 1];
+        L.kin = (int)pad8(L.in);
+        L.outp = (int)pad8(L.out);
+        L.tile = default_tile_width(L.out);
+    }
+    for (int j = 0; j < m->n_in; ++j) { m->h_mu_x[j] = 0.0; m->h_sd_x[j] = 1.0; }
+    for (int j = 0; j < m->n_out; ++j) { m->h_mu_u[j] = 0.0; m->h_sd_u[j] = 1.0; }
+    // one device blob: parameters, optimiser state, statistics, workspaces
+    std::vector<std::pair<void **, size_t>> parts;
+    for (int l = 0; l < kLayers; ++l) {
+        Layer &L = m->L[l];
+        size_t w = (size_t)L.out * L.kin, o = (size_t)L.outp;
+        parts.push_back({(void **)&L.W, w * 4});
+        parts.push_back({(void **)&L.b, o * 4});
+        parts.push_back({(void **)&L.Wb, w * 2});
+        parts.push_back({(void **)&L.Wt, (size_t)L.in * L.outp * 2});
+        parts.push_back({(void **)&L.mW, w * 4});
+        parts.push_back({(void **)&L.vW, w * 4});
+        parts.push_back({(void **)&L.mb, o * 4});
+        parts.push_back({(void **)&L.vb, o * 4});
+        parts.push_back({(void **)&L.gW, w * 4});
+        parts.push_back({(void **)&L.gb, o * 4});
+    }
+    parts.push_back({(void **)&m->mu_x, (size_t)m->n_in_pad * 4});
+    parts.push_back({(void **)&m->isd_x, (size_t)m->n_in_pad * 4});
+    parts.push_back({(void **)&m->mu_u, (size_t)m->n_out_pad * 4});
+    parts.push_back({(void **)&m->sd_u, (size_t)m->n_out_pad * 4});
+    parts.push_back({(void **)&m->out_sp_dev, (size_t)64 * 4});
+    parts.push_back({(void **)&m->err, 64});
+    const int64_t C = m->chunk, B = m->max_batch;
+    parts.push_back({(void **)&m->a0, (size_t)C * m->n_in_pad * 2});
+    for (int i = 0; i < 3; ++i) parts.push_back({(void **)&m->h[i], (size_t)C * desc->n_hidden[i] * 2});
+    parts.push_back({(void **)&m->out, (size_t)C * m->n_out_pad * 4});
+    int maxw = m->n_in_pad > m->n_out_pad ? m->n_in_pad : m->n_out_pad;
+    for (int i = 0; i < 3; ++i) maxw = desc->n_hidden[i] > maxw ? desc->n_hidden[i] : maxw;
+    parts.push_back({(void **)&m->tx0, (size_t)B * m->n_in_pad * 2});
+    for (int i = 0; i < 3; ++i) {
+        parts.push_back({(void **)&m->th[i], (size_t)B * desc->n_hidden[i] * 2});
+        parts.push_back({(void **)&m->tz[i], (size_t)B * desc->n_hidden[i] * 4});
+        parts.push_back({(void **)&m->tdz[i], (size_t)B * desc->n_hidden[i] * 2});
+    }
+    parts.push_back({(void **)&m->tout, (size_t)B * m->n_out_pad * 4});
+    parts.push_back({(void **)&m->tdout, (size_t)B * m->n_out_pad * 2});
+    parts.push_back({(void **)&m->tT0, (size_t)B * maxw * 2});
+    parts.push_back({(void **)&m->tT1, (size_t)B * maxw * 2});
+    parts.push_back({(void **)&m->loss_part, (size_t)B * 4});
+    size_t total = 0;
+    for (auto &pp : parts) total = align256(total) + pp.second;
+    total = align256(total);
+    void *blob = nullptr;
+    int rc = check_cuda(cudaMalloc(&blob, total), "chem_mlp_create: cudaMalloc");
+    if (rc) { delete m; return rc; }
+    rc = check_cuda(cudaMemset(blob, 0, total), "chem_mlp_create: memset");
+    if (rc) { cudaFree(blob); delete m; return rc; }
+    size_t off = 0;
+    for (auto &pp : parts) {
+        off = align256(off);
+        *pp.first = static_cast<uint8_t *>(blob) + off;
+        off += pp.second;
+    }
+    m->blob = blob;
+    m->blob_bytes = total;
+    cudaGetDevice(&m->device);
+    rc = check_cuda(cudaMemcpy(m->out_sp_dev, m->out_species, sizeof(int) * m->n_out, cudaMemcpyHostToDevice),
+                    "chem_mlp_create: species map");
+    // seeded U(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation (splitmix64 stream)
+    std::vector<float> host(param_count(m));
+    uint64_t s = seed;
+    int64_t q = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const double a = 1.0 / std::sqrt((double)m->L[l].in);
+        for (int64_t t = 0; t < (int64_t)m->L[l].out * m->L[l].in + m->L[l].out; ++t) {
+            const double r = (double)(splitmix64(s) >> 11) * (1.0 / 9007199254740992.0);
+            host[q++] = (float)((2.0 * r - 1.0) * a);
+        }
+    }
+    if (!rc) rc = copy_params(m, host.data(), false, false);
+    if (!rc) rc = upload_norm(m);
+    if (!rc) rc = refresh_bf16(m, 0);
+    if (!rc) rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_create");
+    if (rc) { cudaFree(blob); delete m; return rc; }
+    *out = m;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_free(chem_mlp *m) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_free: null handle");
+    cudaDeviceSynchronize();
+    cudaFree(m->blob);
+    delete m;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_dims(const chem_mlp *m, int32_t *widths) {
+    if (!m || !widths) return set_error(CHEM_EINVAL, "chem_mlp_dims: null argument");
+    for (int i = 0; i < 5; ++i) widths[i] = m->widths[i];
+    return CHEM_OK;
+}
+
+extern "C" int64_t chem_mlp_nparams(const chem_mlp *m) { return m ? param_count(m) : -1; }
+
+extern "C" int chem_mlp_set_params(chem_mlp *m, const float *host) {
+    if (!m || !host) return set_error(CHEM_EINVAL, "chem_mlp_set_params: null argument");
+    int rc = copy_params(m, const_cast<float *>(host), false, false);
+    if (rc) return rc;
+    for (int l = 0; l < kLayers; ++l) {
+        Layer &L = m->L[l];
+        cudaMemset(L.mW, 0, (size_t)L.out * L.kin * 4);
+        cudaMemset(L.vW, 0, (size_t)L.out * L.kin * 4);
+        cudaMemset(L.mb, 0, (size_t)L.outp * 4);
+        cudaMemset(L.vb, 0, (size_t)L.outp * 4);
+    }
+    m->adam_t = 0;
+    rc = refresh_bf16(m, 0);
+    if (rc) return rc;
+    return check_cuda(cudaDeviceSynchronize(), "chem_mlp_set_params");
+}
+
+extern "C" int chem_mlp_get_params(const chem_mlp *m, float *host) {
+    if (!m || !host) return set_error(CHEM_EINVAL, "chem_mlp_get_params: null argument");
+    int rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_get_params");
+    return rc ? rc : copy_params(m, host, true, false);
+}
+
+extern "C" int chem_mlp_get_grads(const chem_mlp *m, float *host) {
+    if (!m || !host) return set_error(CHEM_EINVAL, "chem_mlp_get_grads: null argument");
+    int rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_get_grads");
+    return rc ? rc : copy_params(m, host, true, true);
+}
+
+extern "C" int chem_mlp_set_norm(chem_mlp *m, const double *mu_x, const double *sd_x, const double *mu_u,
+                                 const double *sd_u) {
+    if (!m || !mu_x || !sd_x || !mu_u || !sd_u) return set_error(CHEM_EINVAL, "chem_mlp_set_norm: null argument");
+    for (int j = 0; j < m->n_in; ++j) {
+        m->h_mu_x[j] = mu_x[j];
+        m->h_sd_x[j] = (sd_x[j] < 1e-12) ? 1.0 : sd_x[j];
+    }
+    for (int j = 0; j < m->n_out; ++j) {
+        m->h_mu_u[j] = mu_u[j];
+        m->h_sd_u[j] = (sd_u[j] < 1e-30) ? 1.0 : sd_u[j];
+    }
+    return upload_norm(m);
+}
+
+extern "C" int chem_mlp_get_norm(const chem_mlp *m, double *mu_x, double *sd_x, double *mu_u, double *sd_u) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_norm: null handle");
+    for (int j = 0; j < m->n_in; ++j) { if (mu_x) mu_x[j] = m->h_mu_x[j]; if (sd_x) sd_x[j] = m->h_sd_x[j]; }
+    for (int j = 0; j < m->n_out; ++j) { if (mu_u) mu_u[j] = m->h_mu_u[j]; if (sd_u) sd_u[j] = m->h_sd_u[j]; }
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_fit_norm(chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p,
+                                 const double *Y, const double *Y1, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_fit_norm: null handle");
+    int rc = check_state_args(n, ld, T, p, Y, "chem_mlp_fit_norm");
+    if (rc) return rc;
+    if (n < 2 || !Y1 || !aligned16(Y1)) return set_error(CHEM_EINVAL, "chem_mlp_fit_norm: need n >= 2 and aligned Y1");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int nf = m->n_in + m->n_out;
+    double *dev = reinterpret_cast<double *>(m->loss_part);   // 2 nf doubles of scratch
+    if ((size_t)2 * nf * 8 > (size_t)m->max_batch * 4)
+        return set_error(CHEM_EINVAL, "chem_mlp_fit_norm: training batch workspace too small");
+    norm_stats_kernel<<<nf, 256, 0, st>>>(n, ld, T, p, Y, Y1, m->N, m->n_in, m->out_sp_dev, dev, dev + nf);
+    rc = check_cuda(cudaGetLastError(), "chem_mlp_fit_norm launch");
+    if (rc) return rc;
+    std::vector<double> h(2 * nf);
+    rc = check_cuda(cudaMemcpyAsync(h.data(), dev, 2 * nf * 8, cudaMemcpyDeviceToHost, st), "chem_mlp_fit_norm copy");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_norm sync");
+    if (rc) return rc;
+    return chem_mlp_set_norm(m, h.data(), h.data() + nf, h.data() + m->n_in, h.data() + nf + m->n_in);
+}
+
+extern "C" int chem_mlp_forward(const chem_mlp *m, int64_t ncells, int64_t ld, const double *T, const double *p,
+                                const double *Y, float *u, int64_t ldu, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_forward: null handle");
+    int rc = check_state_args(ncells, ld, T, p, Y, "chem_mlp_forward");
+    if (rc) return rc;
+    if (ncells == 0) return CHEM_OK;
+    if (!u || ldu < m->n_out) return set_error(CHEM_EINVAL, "chem_mlp_forward: null u or ldu < n_out");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int64_t c0 = 0; c0 < ncells; c0 += m->chunk) {
+        const int64_t n = (ncells - c0 < m->chunk) ? ncells - c0 : m->chunk;
+        rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
+        if (rc) return rc;
+        rc = check_cuda(cudaMemcpy2DAsync(u + c0 * ldu, ldu * 4, m->out, m->n_out_pad * 4, m->n_out * 4, n,
+                                          cudaMemcpyDeviceToDevice, st), "chem_mlp_forward copy");
+        if (rc) return rc;
+    }
+    return CHEM_OK;
+}
+
+extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int64_t ld, double dt, int prec,
+                             const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
+                             chem_stream_t stream) {
+    (void)fallback;
+    if (!mech || !m) return set_error(CHEM_EINVAL, "chem_step_ann: null handle");
+    if (mech->N != m->N || mech->bath != m->bath)
+        return set_error(CHEM_EINVAL, "chem_step_ann: network and mechanism disagree on the species");
+    if (!(std::fabs(dt - m->dt) <= 1e-12 * m->dt))
+        return set_error(CHEM_EINVAL, "chem_step_ann: dt differs from the step the network was trained for");
+    if (prec != 0) return set_error(CHEM_EUNSUPPORTED, "chem_step_ann: only CHEM_PREC_BF16 is built");
+    int rc = check_state_args(ncells, ld, T, p, Y, "chem_step_ann");
+    if (rc) return rc;
+    if (ncells == 0) return CHEM_OK;
+    if (status && !aligned16(status)) return set_error(CHEM_EINVAL, "chem_step_ann: status must be 16-byte aligned");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_step_ann: " + why);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int64_t c0 = 0; c0 < ncells; c0 += m->chunk) {
+        const int64_t n = (ncells - c0 < m->chunk) ? ncells - c0 : m->chunk;
+        rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
+        if (rc) return rc;
+        epilogue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+            n, ld, m->out, m->n_out_pad, m->N, m->bath, m->n_out, m->out_sp_dev, m->mu_u, m->sd_u, mech->dev.f32,
+            (float)mech->T_mid, T + c0, Y + c0, status ? status + c0 : nullptr);
+        rc = check_cuda(cudaGetLastError(), "chem_step_ann epilogue");
+        if (rc) return rc;
+    }
+    return CHEM_OK;
+}
+
+extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, int64_t ld, const double *T,
+                              const double *p, const double *Y, const double *Y1, float lr, float *loss_dev,
+                              chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "mlp_train_step: null handle");
+    if (batch < 8 || batch > m->max_batch || batch % 8 != 0)
+        return set_error(CHEM_EINVAL, "mlp_train_step: batch must be a multiple of 8 in [8, max_batch]");
+    int rc = check_state_args(idx ? ld : batch, ld, T, p, Y, "mlp_train_step");
+    if (rc) return rc;
+    if (!Y1 || !aligned16(Y1) || (loss_dev && !aligned16(loss_dev)))
+        return set_error(CHEM_EINVAL, "mlp_train_step: Y1 and loss must be 16-byte aligned");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "mlp_train_step: " + why);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int B = (int)batch;
+    // forward with saved pre-activations
+    prologue_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, ld, T, p, Y, idx, m->N, m->n_in_pad, m->mu_x, m->isd_x, m->tx0);
+    if ((rc = check_cuda(cudaGetLastError(), "train prologue"))) return rc;
+    const __nv_bfloat16 *x = m->tx0;
+    int64_t ldx = m->n_in_pad;
+    for (int l = 0; l < 3; ++l) {
+        const Layer &L = m->L[l];
+        rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kin, B, L.out, L.kin, L.b, m->th[l], L.out, m->tz[l], L.out, m->err, st);
+        if (rc) return rc;
+        x = m->th[l];
+        ldx = L.out;
+    }
+    {
+        const Layer &L = m->L[3];
+        rc = gemm_linear(L.tile, x, ldx, L.Wb, L.kin, B, L.out, L.kin, L.b, m->tout, m->n_out_pad, m->err, st);
+        if (rc) return rc;
+    }
+    // loss and dL/du
+    l1_loss_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, m->tout, m->n_out_pad, idx, ld, Y, Y1, m->n_out, m->out_sp_dev,
+                                                     m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part);
+    if (loss_dev) loss_reduce_kernel<<<1, 256, 0, st>>>(B, m->loss_part, loss_dev);
+    if ((rc = check_cuda(cudaGetLastError(), "train loss"))) return rc;
+    // backward, top layer down: dW_l = dZ_l^T H_{l-1}, db_l = colsum dZ_l, dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
+    const __nv_bfloat16 *dz = m->tdout;
+    int lddz = m->n_out_pad;
+    for (int l = 3; l >= 0; --l) {
+        const Layer &L = m->L[l];
+        const __nv_bfloat16 *hin = (l == 0) ? m->tx0 : m->th[l - 1];
+        const int ldh = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
+        dim3 tb(32, 8);
+        transpose_kernel<<<dim3((lddz + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, lddz, dz, lddz, m->tT0, B);
+        transpose_kernel<<<dim3((ldh + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, ldh, hin, ldh, m->tT1, B);
+        if ((rc = check_cuda(cudaGetLastError(), "train transpose"))) return rc;
+        rc = gemm_linear(default_tile_width(L.kin), m->tT0, B, m->tT1, B, L.out, L.kin, B, nullptr, L.gW, L.kin, m->err,
+                         st);
+        if (rc) return rc;
+        colsum_kernel<<<(L.out + 127) / 128, 128, 0, st>>>(B, L.out, dz, lddz, L.gb);
+        if ((rc = check_cuda(cudaGetLastError(), "train bias grad"))) return rc;
+        if (l > 0) {
+            const Layer &Lb = m->L[l - 1];
+            rc = gemm_gelu_grad(default_tile_width(Lb.out), dz, lddz, L.Wt, L.outp, B, Lb.out, L.outp, m->tz[l - 1],
+                                Lb.out, m->tdz[l - 1], Lb.out, m->err, st);
+            if (rc) return rc;
+            dz = m->tdz[l - 1];
+            lddz = Lb.out;
+        }
+    }
+    // Adam
+    m->adam_t += 1;
+    const float bc1 = 1.0f - std::pow(kAdamB1, (float)m->adam_t);
+    const float bc2 = 1.0f - std::pow(kAdamB2, (float)m->adam_t);
+    for (int l = 0; l < kLayers; ++l) {
+        Layer &L = m->L[l];
+        const int64_t n = (int64_t)L.out * L.in + L.out;
+        adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L.out, L.in, L.kin, L.outp, L.W, L.b, L.gW, L.gb, L.mW,
+                                                                 L.vW, L.mb, L.vb, L.Wb, L.Wt, lr, bc1, bc2);
+    }
+    return check_cuda(cudaGetLastError(), "train adam");
+}
+
+extern "C" int chem_mlp_error(const chem_mlp *m, int *host_err) {
+    if (!m || !host_err) return set_error(CHEM_EINVAL, "chem_mlp_error: null argument");
+    int rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_error");
+    if (rc) return rc;
+    return check_cuda(cudaMemcpy(host_err, m->err, sizeof(int), cudaMemcpyDeviceToHost), "chem_mlp_error");
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint: header, statistics, parameters and Adam state, FNV-1a checksum
+// ---------------------------------------------------------------------------
+namespace chemgb {
+namespace {
+
+constexpr char kMlpMagic[8] = {'C', 'H', 'M', 'L', 'P', '0', '0', '1'};
+
+uint64_t fnv1a(const uint8_t *p, size_t n) {
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) { h ^= p[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+// Adam moments in the host parameter layout (W[out][in] then b[out] per layer)
+int copy_moments(const chem_mlp *m, float *host, bool to_host, bool second) {
+    int64_t off = 0;
+    for (int l = 0; l < kLayers; ++l) {
+        const Layer &L = m->L[l];
+        float *W = second ? L.vW : L.mW;
+        float *b = second ? L.vb : L.mb;
+        cudaMemcpyKind kind = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+        int rc = check_cuda(to_host ? cudaMemcpy2D(host + off, L.in * 4, W, L.kin * 4, L.in * 4, L.out, kind)
+                                    : cudaMemcpy2D(W, L.kin * 4, host + off, L.in * 4, L.in * 4, L.out, kind),
+                            "moment copy");
+        if (rc) return rc;
+        off += (int64_t)L.out * L.in;
+        rc = check_cuda(to_host ? cudaMemcpy(host + off, b, L.out * 4, kind) : cudaMemcpy(b, host + off, L.out * 4, kind),
+                        "moment copy");
+        if (rc) return rc;
+        off += L.out;
+    }
+    return CHEM_OK;
+}
+
+}  // namespace
+}  // namespace chemgb
+
+extern "C" int chem_mlp_save(const chem_mlp *m, const char *path) {
+    if (!m || !path) return set_error(CHEM_EINVAL, "chem_mlp_save: null argument");
+    int rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_save");
+    if (rc) return rc;
+    const int64_t np = param_count(m);
+    std::vector<uint8_t> body;
+    auto put = [&](const void *p, size_t n) {
+        const uint8_t *b = static_cast<const uint8_t *>(p);
+        body.insert(body.end(), b, b + n);
+    };
+    int32_t hdr[8] = {1, m->N, m->bath, m->widths[0], m->widths[1], m->widths[2], m->widths[3], m->widths[4]};
+    put(hdr, sizeof(hdr));
+    put(&m->dt, 8);
+    put(&m->adam_t, 8);
+    put(m->h_mu_x, 8 * m->n_in);
+    put(m->h_sd_x, 8 * m->n_in);
+    put(m->h_mu_u, 8 * m->n_out);
+    put(m->h_sd_u, 8 * m->n_out);
+    std::vector<float> buf(np);
+    if ((rc = copy_params(m, buf.data(), true, false))) return rc;
+    put(buf.data(), 4 * np);
+    if ((rc = copy_moments(m, buf.data(), true, false))) return rc;
+    put(buf.data(), 4 * np);
+    if ((rc = copy_moments(m, buf.data(), true, true))) return rc;
+    put(buf.data(), 4 * np);
+    const uint64_t sum = fnv1a(body.data(), body.size());
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return set_error(CHEM_EIO, std::string("chem_mlp_save: cannot open ") + path);
+    bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(body.data(), 1, body.size(), f) == body.size() &&
+              std::fwrite(&sum, 8, 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? CHEM_OK : set_error(CHEM_EIO, "chem_mlp_save: write failed");
+}
+
+extern "C" int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out) {
+    if (!mech || !path || !out) return set_error(CHEM_EINVAL, "chem_mlp_load: null argument");
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_error(CHEM_EIO, std::string("chem_mlp_load: cannot open ") + path);
+    std::vector<uint8_t> all;
+    uint8_t tmp[65536];
+    size_t n;
+    while ((n = std::fread(tmp, 1, sizeof(tmp), f)) > 0) all.insert(all.end(), tmp, tmp + n);
+    std::fclose(f);
+    if (all.size() < 8 + 32 + 16 + 8 || std::memcmp(all.data(), kMlpMagic, 8) != 0)
+        return set_error(CHEM_EIO, "chem_mlp_load: not a network checkpoint");
+    const uint8_t *body = all.data() + 8;
+    const size_t blen = all.size() - 16;
+    uint64_t sum;
+    std::memcpy(&sum, all.data() + all.size() - 8, 8);
+    if (fnv1a(body, blen) != sum) return set_error(CHEM_EIO, "chem_mlp_load: checksum mismatch");
+    int32_t hdr[8];
+    std::memcpy(hdr, body, sizeof(hdr));
+    if (hdr[0] != 1) return set_error(CHEM_EIO, "chem_mlp_load: unknown checkpoint version");
+    if (hdr[1] != mech->N || hdr[2] != mech->bath)
+        return set_error(CHEM_EINVAL, "chem_mlp_load: checkpoint species do not match the mechanism");
+    chem_mlp_desc d;
+    std::memset(&d, 0, sizeof(d));
+    for (int i = 0; i < 3; ++i) d.n_hidden[i] = hdr[4 + i];
+    size_t off = sizeof(hdr);
+    std::memcpy(&d.dt, body + off, 8);
+    off += 8;
+    int64_t adam_t;
+    std::memcpy(&adam_t, body + off, 8);
+    off += 8;
+    chem_mlp *m = nullptr;
+    int rc = chem_mlp_create(mech, &d, 0, &m);
+    if (rc) return rc;
+    const int64_t np = param_count(m);
+    const size_t need = off + 8 * (size_t)(2 * m->n_in + 2 * m->n_out) + 12 * (size_t)np;
+    if (need != blen) { chem_mlp_free(m); return set_error(CHEM_EIO, "chem_mlp_load: truncated checkpoint"); }
+    std::vector<double> st(2 * m->n_in + 2 * m->n_out);
+    std::memcpy(st.data(), body + off, 8 * st.size());
+    off += 8 * st.size();
+    rc = chem_mlp_set_norm(m, st.data(), st.data() + m->n_in, st.data() + 2 * m->n_in,
+                           st.data() + 2 * m->n_in + m->n_out);
+    std::vector<float> buf(np);
+    if (!rc) {
+        std::memcpy(buf.data(), body + off, 4 * np);
+        off += 4 * np;
+        rc = chem_mlp_set_params(m, buf.data());
+    }
+    if (!rc) {
+        std::memcpy(buf.data(), body + off, 4 * np);
+        off += 4 * np;
+        rc = copy_moments(m, buf.data(), false, false);
+    }
+    if (!rc) {
+        std::memcpy(buf.data(), body + off, 4 * np);
+        rc = copy_moments(m, buf.data(), false, true);
+    }
+    if (rc) { chem_mlp_free(m); return rc; }
+    m->adam_t = adam_t;
+    *out = m;
+    return CHEM_OK;
+}

@@ -451,23 +451,30 @@ __device__ void lu_solve(const Slice &sh, int lane, int n, double b[2]) {
     __syncwarp();
 }
 
+// Cells 0..ncells-1, or (list != null) the *list_count cells list[0..) of a
+// device-built queue; status of a successful cell = ok_status.
 __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t ncells, int64_t ld, double dt,
                                                              chem_ode_opts o, double *__restrict__ Tg,
                                                              const double *__restrict__ pg, double *__restrict__ Yg,
                                                              int32_t *__restrict__ status,
                                                              int32_t *__restrict__ nsteps_out,
-                                                             unsigned int *__restrict__ queue) {
+                                                             unsigned int *__restrict__ queue,
+                                                             const int32_t *__restrict__ list,
+                                                             const unsigned int *__restrict__ list_count,
+                                                             int ok_status) {
     extern __shared__ __align__(16) char smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int N = m.N, n = N + 1;
     Slice sh = make_slice(smem + (size_t)warp * slice_bytes(N, m.R), N, m.R);
+    const int64_t limit = list ? (int64_t)(*list_count < (unsigned int)ncells ? *list_count : (unsigned int)ncells)
+                               : ncells;
     for (;;) {
-        unsigned int cell_u = 0;
-        if (lane == 0) cell_u = atomicAdd(queue, 1u);
-        cell_u = __shfl_sync(kFull, cell_u, 0);
-        const int64_t cell = (int64_t)cell_u;
-        if (cell >= ncells) break;
+        unsigned int pos = 0;
+        if (lane == 0) pos = atomicAdd(queue, 1u);
+        pos = __shfl_sync(kFull, pos, 0);
+        if ((int64_t)pos >= limit) break;
+        const int64_t cell = list ? (int64_t)list[pos] : (int64_t)pos;
         double y[2], yn[2], f0[2], K1[2], K2[2], K3[2], K4[2], ys[2], fs[2];
         for (int s = 0; s < 2; ++s) {
             int c = lane + 32 * s;
@@ -568,7 +575,7 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
             else if (c < n) Yg[(int64_t)(c - 1) * ld + cell] = y[s];
         }
         if (lane == 0) {
-            status[cell] = stat;
+            status[cell] = (stat == CHEM_CELL_OK) ? ok_status : stat;
             if (nsteps_out) nsteps_out[cell] = nst;
         }
     }
@@ -620,9 +627,40 @@ extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, d
     unsigned int *queue = m->dev.counters;
     int rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "chem_step_stiff: queue reset");
     if (rc) return rc;
-    stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue);
+    stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue, nullptr,
+                                                    nullptr, CHEM_CELL_OK);
     return check_cuda(cudaGetLastError(), "chem_step_stiff launch");
 }
+
+namespace chemgb {
+// Stiff integration of the cells a device queue lists (the fallback of the
+// learned step): list[0..*count) with count <= capacity, status ok_status on
+// success. Uses the mechanism's second work-queue counter.
+int launch_stiff_list(const chem_mech *m, int64_t capacity, int64_t ld, double dt, const chem_ode_opts &o, double *T,
+                      const double *p, double *Y, int32_t *status, const int32_t *list, const unsigned int *count,
+                      int ok_status, cudaStream_t st) {
+    if (m->N > 63) return set_error(CHEM_EUNSUPPORTED, "fallback: at most 63 species");
+    size_t smem = slice_bytes(m->N, m->R) * kWarps;
+    if (smem > 227 * 1024) return set_error(CHEM_EUNSUPPORTED, "fallback: mechanism too large for shared memory");
+    int rc = check_cuda(cudaFuncSetAttribute(stiff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                        "fallback: smem attribute");
+    if (rc) return rc;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stiff_kernel, kWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t need = (capacity + kWarps - 1) / kWarps;
+    int blocks = (int)((int64_t)sms * per_sm < need ? (int64_t)sms * per_sm : need);
+    if (blocks < 1) blocks = 1;
+    unsigned int *queue = m->dev.counters + 1;
+    rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "fallback: queue reset");
+    if (rc) return rc;
+    stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, capacity, ld, dt, o, T, p, Y, status, nullptr, queue, list,
+                                                    count, ok_status);
+    return check_cuda(cudaGetLastError(), "fallback launch");
+}
+}  // namespace chemgb
 
 // ---------------------------------------------------------------------------
 // Allocation-free variant of chem_step_stiff.
@@ -712,6 +750,7 @@ extern "C" int chem_step_stiff_noalloc(const chem_mech *m, int64_t ncells, int64
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "chem_step_stiff_noalloc: clear queue");
     if (rc) return rc;
-    stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue);
+    stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue, nullptr,
+                                                    nullptr, CHEM_CELL_OK);
     return check_cuda(cudaGetLastError(), "chem_step_stiff_noalloc launch");
 }

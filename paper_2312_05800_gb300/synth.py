@@ -550,3 +550,35 @@ def perturb_off_manifold(T: np.ndarray, Y: np.ndarray, ncells: int, frac: float,
     Y[:, idx] *= np.exp(sigma * rng.standard_normal((Y.shape[0], idx.size)))
     Y[:, idx] /= Y[:, idx].sum(axis=0, keepdims=True)
     return T, Y, mask
+
+
+# ----------------------------------------------------------------------------
+# network parameters for tests (seeded uniform draws; no arithmetic of the method)
+# ----------------------------------------------------------------------------
+
+def mlp_layers(widths, seed: int):
+    """[(W [out, in], b [out])] with entries U(-1/sqrt(in), 1/sqrt(in)), float32-representable."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for fi, fo in zip(widths[:-1], widths[1:]):
+        a = 1.0 / np.sqrt(fi)
+        W = rng.uniform(-a, a, (fo, fi)).astype(np.float32).astype(np.float64)
+        b = rng.uniform(-a, a, fo).astype(np.float32).astype(np.float64)
+        out.append((W, b))
+    return out
+
+
+def flatten_layers(layers):
+    """Layer-by-layer W (row-major) then b, as float32 (the C ABI's parameter layout)."""
+    return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in layers]).astype(np.float32)
+
+
+def unflatten(flat, widths):
+    out, o = [], 0
+    for fi, fo in zip(widths[:-1], widths[1:]):
+        W = flat[o:o + fo * fi].reshape(fo, fi).astype(np.float64)
+        o += fo * fi
+        b = flat[o:o + fo].astype(np.float64)
+        o += fo
+        out.append((W, b))
+    return out

@@ -1,0 +1,75 @@
+"""chem_dense_bf16 (the tcgen05 GEMM behind every MLP layer, Sec. 3.2) against
+an FP64 matrix product of the same BF16-rounded operands.
+
+Bound: FP32 accumulation of exact BF16 products gives |err| <= 2^-22 K-scaled
+sum |x||w| (we allow 1e-5 of that sum); a BF16 output adds 2^-8 relative.
+Shapes cover every layer of both networks, ragged M, N and K, and every tile
+width the library is built with."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # (M, N, K)
+    (300, 1600, 32), (1000, 800, 1600), (257, 400, 800), (4099, 29, 400),
+    (129, 2048, 56), (131, 52, 512), (1, 16, 8), (640, 1024, 2048),
+    # more tiles than CTAs: each persistent CTA reuses both TMEM accumulators
+    (40000, 1600, 32), (20000, 800, 1600), (33333, 29, 400),
+]
+
+
+def _gelu64(z):
+    from scipy.special import erf
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def _case(M, N, K, act, tile_n, seed):
+    import torch
+    from paper_2312_05800_gb300 import binding
+    g = torch.Generator().manual_seed(seed)
+    x = (torch.randn(M, K, generator=g) * 0.7).to(torch.bfloat16)
+    W = (torch.randn(N, K, generator=g) / math.sqrt(K)).to(torch.bfloat16)
+    b = torch.randn(N, generator=g, dtype=torch.float32) * 0.1
+    xd, Wd, bd = x.cuda(), W.cuda(), b.cuda()
+    err = torch.zeros(4, dtype=torch.int32, device="cuda")
+    if act == 0:
+        ldy = N + (-N) % 4
+        y = torch.full((M, ldy), float("nan"), dtype=torch.float32, device="cuda")
+    else:
+        ldy = N + (-N) % 8
+        y = torch.full((M, ldy), float("nan"), dtype=torch.bfloat16, device="cuda")
+    binding.chem_dense_bf16(M, N, K, xd, K, Wd, K, bd, act, y, ldy, tile_n, err)
+    torch.cuda.synchronize()
+    assert int(err[0].item()) == 0
+    x64, W64, b64 = x.double().numpy(), W.double().numpy(), b.double().numpy()
+    acc = x64 @ W64.T + b64
+    scale = np.abs(x64) @ np.abs(W64).T
+    got = y.double().cpu().numpy()[:, :N]
+    if act == 0:
+        bound = 1e-5 * scale + 1e-6
+        err = np.abs(got - acc)
+    else:
+        ref = _gelu64(acc)
+        bound = 2.0 ** -8 * np.abs(ref) + 1.2e-5 * scale + 1e-6
+        err = np.abs(got - ref)
+    bad = err > bound
+    if bad.any():
+        i, j = np.unravel_index(np.argmax(err / bound), err.shape)
+        raise AssertionError("%d of %d outside the bound; worst (%d, %d): err %.3g bound %.3g"
+                             % (bad.sum(), bad.size, i, j, err[i, j], bound[i, j]))
+    if ldy > N:   # padding columns untouched
+        assert torch.isnan(y[:, N:].float()).all()
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("act", [0, 1])
+def test_dense_auto_tile(M, N, K, act):
+    _case(M, N, K, act, 0, 7 + M + N + K + act)
+
+
+@pytest.mark.parametrize("tile_n", [32, 64, 128, 160, 208, 256])
+def test_dense_every_tile_width(tile_n):
+    _case(515, 450, 200, 1, tile_n, tile_n)
+    _case(515, 450, 200, 0, tile_n, tile_n + 1)
