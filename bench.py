@@ -9,9 +9,16 @@ mechanism, 2,097,152 cells sampled along algebraic stratified premixed
 profiles (phi 0.5-1.2, 5 % log-normal Y noise), 1 atm. Inputs (about 0.5 GB
 of FP64 state) are larger than L2, so no flush is needed between steps.
 
-Paths (see --path): "stiff" = chem_step_stiff (FP64 Rodas3 at rtol 1e-3, the
-loosest setting tried; its error against a tight integration is far inside the
-ANN bars) followed by props_eval (FP32 arithmetic on the FP64 state).
+Paths (see --path):
+  "ann" (default): chem_step_ann (the Box-Cox / Z-score MLP 32-1600-800-400-29 on
+      the tensor cores, BF16 with FP32 accumulation) then props_eval, on
+      4,194,304 cells. The network is trained first (untimed) on pairs the GPU
+      stiff integrator generates; its error against a tight stiff integration
+      is measured on held-out cells and printed with the throughput, beside the
+      plain method (stiff + props) timed on a sample of the same cells.
+  "stiff": chem_step_stiff (FP64 Rodas3 at rtol 1e-3, the loosest setting
+      tried; its error against a tight integration is far inside the ANN bars)
+      followed by props_eval (FP32 arithmetic on the FP64 state), 2,097,152 cells.
 
 Contract: python bench.py --gpus N --steps K --warmup W [--impl reference]
 prints one JSON line. Under torchrun each rank runs its own shard (the cells
@@ -28,11 +35,15 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NCELLS = 2097152
+NCELLS_ANN = 4194304
 DT = 1.0e-6
+TIGHT_OPTS = dict(rtol=1e-6, atol_Y=1e-13, atol_T=1e-6, h0=1e-9, max_steps=20000)
 STIFF_OPTS = dict(rtol=1e-3, atol_Y=1e-9, atol_T=1e-3, h0=1e-9, max_steps=10000)
 MECH = "c2"
 SEED = 2002
@@ -134,54 +145,48 @@ def omp_threads() -> int:
 
 
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: the same path and metric as
+    our arm, each step a bounded sample of the workload."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
     import oracle as O
     O.build()
-    mech, T, p, Y = make_inputs(0)
-    sample = 4096
-    for _ in range(args.warmup):
-        run_cpu_oracle(mech, T, p, Y, sample)
-    times = [run_cpu_oracle(mech, T, p, Y, sample) for _ in range(args.steps)]
-    v = sample / statistics.median(times)
+    from paper_2312_05800_gb300 import synth
+    if args.path == "ann":
+        smech = synth.get_mech(MECH)
+        T, p, Y = synth.states_profiles(smech, 8192, 2003, ld=8192)
+        sample = 4096
+        for _ in range(args.warmup):
+            cpu_baseline_ann(smech, T, p, Y, sample)
+        vals = [cpu_baseline_ann(smech, T, p, Y, sample)["value"] for _ in range(args.steps)]
+        v = statistics.median(vals)
+        cfg = {"workload": "ANN chemistry + props: c2 stratified-profile cells, 30 species / 180 reactions, "
+                           "MLP 32-1600-800-400-29, dt 1 us", "path": "oracle ANN step (FP64) + props",
+               "cells_per_step": sample}
+        desc = "first %d cells per step: oracle ANN step (FP64) + props" % sample
+    else:
+        mech, T, p, Y = make_inputs(0, 8192)
+        sample = 4096
+        for _ in range(args.warmup):
+            run_cpu_oracle(mech, T, p, Y, sample)
+        v = sample / statistics.median([run_cpu_oracle(mech, T, p, Y, sample) for _ in range(args.steps)])
+        cfg = {"workload": "c2 stratified-profile cells, 30 species / 180 reactions, dt 1 us",
+               "path": "oracle stiff+props", "cells_per_step": sample, "rtol": STIFF_OPTS["rtol"]}
+        desc = "first %d cells per step: oracle stiff + props at rtol %g" % (sample, STIFF_OPTS["rtol"])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "c2 stratified-profile cells, 30 species / 180 reactions, dt 1 us",
-                       "path": "stiff+props", "cells_per_step": sample, "rtol": STIFF_OPTS["rtol"]},
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": "cells/s", "cores": omp_threads(), "kind": "oracle",
-                             "sample": "first %d of the %d cells per step" % (sample, NCELLS)},
+                             "sample": desc},
             "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def main():
-    global NCELLS
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--path", default="stiff", choices=["stiff"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cells", type=int, default=NCELLS,
-                    help="cells per GPU; smaller values only for profiling captures (the bench line uses the default)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        run_reference(args)
-        return
+def bench_stiff(args, rank, world, local):
     import torch
-    NCELLS = args.cells
-    if NCELLS % 4:
-        raise SystemExit("--cells must be a multiple of 4")
-    rank, world, local = env_rank()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2312_05800_gb300 import binding, build
-    build.build()
+    from paper_2312_05800_gb300 import binding
     mech, T, p, Y = make_inputs(rank, NCELLS)
     N = mech.N
     dm = binding.Mech(mech)
@@ -298,6 +303,243 @@ def main():
         el = run_cpu_oracle(mech, T, p, Y, sample)
         line["cpu_baseline"] = {"value": sample / el, "unit": "cells/s", "cores": omp_threads(), "kind": "oracle",
                                 "sample": "first %d of the %d cells, stiff + props at the same rtol" % (sample, NCELLS)}
+    return line
+
+
+
+
+def measured_peak(key: str, fallback: float):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)[key]), "measured"
+    except Exception:
+        return fallback, "fallback"
+
+
+def accuracy(mech, T0, Y0, Ta, Ya, Tr, Yr, n):
+    """Per major species relative L2 of dY, and |T error| max / p99.9, against a reference."""
+    import numpy as np
+    major = [k for k in range(mech.N) if k != mech.bath and Y0[k, :n].mean() >= 1e-2]
+    rel = {}
+    for k in major:
+        dr = Yr[k, :n] - Y0[k, :n]
+        da = Ya[k, :n] - Y0[k, :n]
+        rel[str(k)] = float(np.linalg.norm(da - dr) / max(np.linalg.norm(dr), 1e-300))
+    terr = np.abs(Ta[:n] - Tr[:n])
+    return {"dY_rel_l2_major": rel, "dY_rel_l2_major_max": max(rel.values()) if rel else None,
+            "T_err_max_K": float(terr.max()), "T_err_p999_K": float(np.percentile(terr, 99.9)), "cells": int(n)}
+
+
+def bench_ann(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_2312_05800_gb300 import binding, synth, train
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    smech = synth.get_mech(MECH)
+    dm = binding.Mech(smech)
+    N = smech.N
+    # ---- training (untimed): GPU stiff pairs, statistics, Adam on Eq. 5
+    t0 = time.perf_counter()
+    data = train.make_training_set(dm, smech, args.train_pairs, seed=2103 + 1000 * rank)
+    t_data = time.perf_counter() - t0
+    net = binding.Mlp(dm, hidden=(1600, 800, 400), dt=DT, seed=3003, chunk=262144, max_batch=4096)
+    train.fit_norm(net, data)
+    t0 = time.perf_counter()
+    hist = train.train(net, data, epochs=args.epochs, batch=4096, lr0=args.lr)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del data
+    # ---- inference workload
+    ncells = args.cells
+    T, p, Y = synth.states_profiles(smech, ncells, 2003 + 1000 * rank, ld=synth.padded_ld(ncells))
+    ld = T.shape[0]
+    T0 = torch.from_numpy(T).to(dev)
+    p0 = torch.from_numpy(p).to(dev)
+    Y0 = torch.from_numpy(Y).to(dev)
+    Tw, Yw = T0.clone(), Y0.clone()
+    status = torch.zeros(ld, dtype=torch.int32, device=dev)
+    cp = torch.empty(ld, dtype=torch.float32, device=dev)
+    hh, mu, lam = torch.empty_like(cp), torch.empty_like(cp), torch.empty_like(cp)
+    Dk = torch.empty(N, ld, dtype=torch.float32, device=dev)
+    # ---- accuracy on held-out cells against a tight stiff integration
+    ne = min(args.eval_cells, ncells)
+    Ta, Ya = T0.clone(), Y0.clone()
+    binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_BF16, None, Ta, p0, Ya, status)
+    Tr, Yr = T0.clone(), Y0.clone()
+    binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**TIGHT_OPTS), Tr, p0, Yr, status)
+    Ts, Ys = T0.clone(), Y0.clone()
+    binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**STIFF_OPTS), Ts, p0, Ys, status)
+    torch.cuda.synchronize()
+    Ta, Ya, Tr, Yr, Ts, Ys = [x.cpu().numpy() for x in (Ta, Ya, Tr, Yr, Ts, Ys)]
+    acc_ann = accuracy(smech, T, Y, Ta, Ya, Tr, Yr, ne)
+    acc_stiff = accuracy(smech, T, Y, Ts, Ys, Tr, Yr, ne)
+    del Ta, Ya, Tr, Yr, Ts, Ys
+
+    def step():
+        Tw.copy_(T0)
+        Yw.copy_(Y0)
+        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, None, Tw, p0, Yw, status, stream)
+        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert net.error() == 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    binding.chem_prof_enable(True)
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for _ in range(args.steps):
+            step()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    prof = binding.chem_prof_read()
+    binding.chem_prof_enable(False)
+    if world > 1:
+        torch.distributed.barrier()
+    total_s = ev[0].elapsed_time(ev[1]) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * ncells * args.steps / total_s
+    gemm = {k: v for k, v in prof.items() if k.startswith("gemm_tn_kernel")}
+    g_ms = sum(v[1] for v in gemm.values())
+    g_fl = sum(v[2] for v in gemm.values())
+    peak, src = measured_peak("bf16_tflops", 1900.0)
+    achieved = g_fl / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
+    # ---- the plain method on a sample of the same cells (stiff at rtol 1e-3 + props)
+    ns = min(args.stiff_sample, ncells)
+    torch.cuda.synchronize()
+    Tw.copy_(T0)
+    Yw.copy_(Y0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    binding.chem_step_stiff(dm, ns, ld, DT, binding.make_opts(**STIFF_OPTS), Tw, p0, Yw, status, None, stream)
+    binding.props_eval(dm, ns, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    stiff_value = ns / (e0.elapsed_time(e1) / 1e3)
+    # ---- end to end through the C ABI with pinned host buffers
+    Th, ph, Yh = torch.from_numpy(T).pin_memory(), torch.from_numpy(p).pin_memory(), torch.from_numpy(Y).pin_memory()
+    Tout, Yout = torch.empty_like(Th).pin_memory(), torch.empty_like(Yh).pin_memory()
+    sout = torch.empty(ld, dtype=torch.int32).pin_memory()
+    pout = [torch.empty(ld, dtype=torch.float32).pin_memory() for _ in range(4)]
+    Dout = torch.empty(N, ld, dtype=torch.float32).pin_memory()
+    h2d = (Th.numel() + ph.numel() + Yh.numel()) * 8
+    d2h = (Tout.numel() + Yout.numel()) * 8 + sout.numel() * 4 + 4 * ld * 4 + Dout.numel() * 4
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Tw.copy_(Th, non_blocking=True)
+        p0.copy_(ph, non_blocking=True)
+        Yw.copy_(Yh, non_blocking=True)
+        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, None, Tw, p0, Yw, status, stream)
+        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+        Tout.copy_(Tw, non_blocking=True)
+        Yout.copy_(Yw, non_blocking=True)
+        sout.copy_(status, non_blocking=True)
+        for o, d in zip(pout, (cp, hh, mu, lam)):
+            o.copy_(d, non_blocking=True)
+        Dout.copy_(Dk, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_value = world * ncells * e2e_steps / (e0.elapsed_time(e1) / 1e3)
+    chunks = (ncells + 262143) // 262144
+    line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "ANN chemistry + props: c2 stratified-profile cells, 30 species / 180 reactions, "
+                                   "MLP 32-1600-800-400-29, dt 1 us",
+                       "path": "chem_step_ann (BF16 tcgen05 GEMMs, FP32 accumulation) + props_eval (FP32)",
+                       "cells_per_gpu": ncells, "l2": "inputs larger than L2 (1 GB FP64 state)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_rtol1e-3_vs_tight_stiff": acc_stiff,
+                         "reference": "chem_step_stiff rtol 1e-6 on the first %d cells" % ne},
+            "stiff": {"value": stiff_value, "unit": "cells/s", "path": "chem_step_stiff rtol 1e-3 + props_eval",
+                      "sample": "first %d of the %d cells, one step" % (ns, ncells),
+                      "ann_speedup": value / stiff_value},
+            "training": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": 4096,
+                         "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "data_s": t_data,
+                         "train_s": t_train},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "kernel": "gemm_tn_kernel (all four layers; logical 2MNK flops)", "peak_source": src,
+                         "per_shape": {k: {"launches": v[0], "ms": v[1],
+                                           "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
+                                       for k, v in gemm.items()}},
+            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (chunks * 6 + 1),
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_ann(smech, T, p, Y)
+    return line
+
+
+def cpu_baseline_ann(smech, T, p, Y, sample=4096):
+    """The oracle's learned step + props (FP64, numpy matmul and the C oracle) on a sample."""
+    import oracle as O
+    from oracle import ann as A
+    from oracle import mlp as M
+    from paper_2312_05800_gb300 import synth
+    O.build()
+    widths = [smech.N + 2, 1600, 800, 400, smech.N - 1]
+    layers = synth.mlp_layers(widths, 3003)
+    x = M.features(T[:sample], p[:sample], Y[:, :sample])
+    mu_x, sd_x = M.zscore_stats(x)
+    stats = (mu_x, sd_x, np.zeros(smech.N - 1), np.full(smech.N - 1, 1e-5))
+    t0 = time.perf_counter()
+    T1, Y1 = A.step_ann(smech, layers, stats, T[:sample].copy(), p[:sample].copy(), Y[:, :sample].copy())
+    O.props(smech, T1, p[:sample].copy(), Y1)
+    el = time.perf_counter() - t0
+    return {"value": sample / el, "unit": "cells/s", "cores": omp_threads(), "kind": "oracle",
+            "sample": "first %d of the cells: oracle ANN step (FP64) + props" % sample}
+
+
+def main():
+    global NCELLS
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="ann", choices=["ann", "stiff"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="cells per GPU (default 4,194,304 for ann, 2,097,152 for stiff); smaller values only for "
+                         "profiling captures")
+    ap.add_argument("--train-pairs", type=int, default=524288)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval-cells", type=int, default=32768)
+    ap.add_argument("--stiff-sample", type=int, default=262144)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    if args.cells is None:
+        args.cells = NCELLS_ANN if args.path == "ann" else NCELLS
+    NCELLS = args.cells
+    if NCELLS % 4:
+        raise SystemExit("--cells must be a multiple of 4")
+    rank, world, local = env_rank()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2312_05800_gb300 import build
+    build.build()
+    if args.path == "ann":
+        line = bench_ann(args, rank, world, local)
+    else:
+        line = bench_stiff(args, rank, world, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -293,6 +293,17 @@ int chem_step_ann(const chem_mech *mech, const chem_mlp *mlp, int64_t ncells, in
 int mlp_train_step(chem_mlp *mlp, int64_t batch, const int32_t *idx, int64_t ld, const double *T, const double *p,
                    const double *Y, const double *Y1, float lr, float *loss_dev, chem_stream_t stream);
 
+/* Opt-in kernel timing (no counterpart in the paper; a measurement aid).
+ * chem_prof_enable(1) clears the counters and starts recording CUDA events on
+ * the launch stream around the library's kernels (tensor-core GEMMs, the
+ * network's prologue and epilogue, props and the stiff integrator);
+ * chem_prof_read writes one line per kernel tag:
+ * "tag\tlaunches\tmilliseconds\tflops\tbytes\n" (algorithmic flops and bytes
+ * where defined: 2 M N K for a GEMM), synchronising on the recorded events.
+ * Off by default; timing adds two event records per launch. */
+int chem_prof_enable(int on);
+int chem_prof_read(char *buf, int64_t buflen);
+
 /* Last error message of the calling thread ("" if none). */
 const char *chem_last_error(void);
 

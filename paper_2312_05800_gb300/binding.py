@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
     L.chem_step_ann.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp]
     L.mlp_train_step.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, ctypes.c_float, vp, vp]
+    L.chem_prof_enable.argtypes = [i32]
+    L.chem_prof_read.argtypes = [ctypes.c_char_p, i64]
     L.chem_last_error.restype = ctypes.c_char_p
     L.chem_version.restype = ctypes.c_char_p
     _lib = L
@@ -287,6 +289,21 @@ def chem_step_ann(mech: Mech, mlp: Mlp, ncells: int, ld: int, dt: float, prec: i
 def mlp_train_step(mlp: Mlp, batch: int, idx, ld: int, T, p, Y, Y1, lr: float, loss=None, stream=None):
     _check(lib().mlp_train_step(mlp.handle, batch, _ptr(idx), ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Y1),
                                 ctypes.c_float(lr), _ptr(loss), _stream(stream)))
+
+
+def chem_prof_enable(on: bool):
+    _check(lib().chem_prof_enable(1 if on else 0))
+
+
+def chem_prof_read():
+    """{tag: (launches, ms, flops, bytes)} accumulated since chem_prof_enable."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().chem_prof_read(buf, len(buf)))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        tag, n, ms, fl, by = line.split("\t")
+        out[tag] = (int(n), float(ms), float(fl), float(by))
+    return out
 
 
 def chem_last_error() -> str:

@@ -3,16 +3,20 @@
 // This is the dense contraction of every MLP layer (Sec. 3.2: hidden layers of
 // 1600, 800 and 400 GELU units), forward and backward.
 //
-// Roles (192 threads per CTA, one CTA per SM, static round-robin over tiles):
+// Roles (320 threads per CTA, one CTA per SM, static round-robin over tiles):
 //   warp 0      TMA producer: 128 x 64 tile of X and BN x 64 tile of W per
 //               k-block into a STAGES-deep ring (128-byte swizzle).
 //   warp 1      TMEM allocation and the single MMA-issuing thread:
 //               tcgen05.mma kind::f16, M = 128, N = BN, K = 16 per instruction,
 //               accumulating in one of two TMEM buffers (columns 0 and 256).
-//   warps 2..5  epilogue: tcgen05.ld of 16-column chunks (warp w reads TMEM
-//               lanes 32 (w % 4) .. +31, i.e. output rows), then the functor.
-// Ragged M, N and K: TMA fills out-of-range operand elements with zeros and
-// the epilogue functors mask rows >= M and columns >= N.
+//   warps 2..9  epilogue: two warps per TMEM lane quadrant (warp w reads TMEM
+//               lanes 32 (w % 4) .. +31, i.e. output rows) split the 16-column
+//               chunks between them; tcgen05.ld, then the functor. BF16 GELU
+//               outputs are staged per warp in shared memory (double buffered)
+//               and written by TMA tensor stores.
+// Ragged M, N and K: TMA fills out-of-range operand elements with zeros, TMA
+// stores clip at the tensor bounds, and direct stores mask rows >= M and
+// columns >= N.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -21,7 +25,9 @@
 
 namespace chemgb {
 
-constexpr int kGemmThreads = 192;
+constexpr int kGemmThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kStageBytesPerWarp = 32 * 16 * 2;   // one 32 x 16 BF16 chunk
 constexpr int kBM = 128;
 constexpr int kBK = 64;
 constexpr uint32_t kTmemCols = 512;
@@ -31,19 +37,36 @@ struct GemmSmem {
     static constexpr uint32_t kABytes = kBM * kBK * 2;
     static constexpr uint32_t kBBytes = BN * kBK * 2;
     static constexpr uint32_t kTiles = STAGES * (kABytes + kBBytes);
+    static constexpr uint32_t kStaging = kEpiWarps * 2 * kStageBytesPerWarp;
     static constexpr uint32_t kBars = (2 * STAGES + 5) * 8 + 16;
-    static constexpr uint32_t kTotal = 1024 + kTiles + kBars;
+    static constexpr uint32_t kTotal = 1024 + kTiles + kStaging + kBars;
     static_assert(kBBytes % 1024 == 0, "B tile must keep 1024-byte alignment");
 };
 
-__device__ __forceinline__ float gelu_exact(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// erf by Abramowitz and Stegun (1964) formula 7.1.26: for x >= 0,
+// erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x),
+// absolute error <= 1.5e-7 (far below the BF16 rounding of the activations);
+// odd in x.
+__device__ __forceinline__ float erf_as(float x) {
+    const float ax = fabsf(x);
+    const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
+    float y = fmaf(1.061405429f, t, -1.453152027f);
+    y = fmaf(y, t, 1.421413741f);
+    y = fmaf(y, t, -0.284496736f);
+    y = fmaf(y, t, 0.254829592f);
+    const float r = 1.0f - y * t * __expf(-ax * ax);
+    return copysignf(r, x);
+}
+// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ float gelu_exact(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
 // ---- epilogue functors: (row, first column, 16 accumulator values) --------
 
 // Y = bf16(GELU(acc + b)); optionally also the FP32 pre-activation acc + b.
+// Without a pre-activation the kernel stages the BF16 chunk and stores it by TMA.
 struct EpiGelu {
     int M, N;
     const float *bias;
@@ -51,6 +74,19 @@ struct EpiGelu {
     int64_t ldo;
     float *pre;      // may be null
     int64_t ldp;
+    // TMA stores clip at 16-byte granularity in the row, so they are used only
+    // when every row of the output ends on a 16-byte boundary (N % 8 == 0)
+    __host__ __device__ __forceinline__ bool tma_store() const { return pre == nullptr && (N & 7) == 0; }
+    // the 16 BF16 values of (row, col0..col0+15), two per 32-bit word
+    __device__ __forceinline__ void compute(int col0, const float (&v)[16], uint32_t (&w)[8]) const {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float b0 = (col0 + 2 * i < N) ? __ldg(bias + col0 + 2 * i) : 0.0f;
+            const float b1 = (col0 + 2 * i + 1 < N) ? __ldg(bias + col0 + 2 * i + 1) : 0.0f;
+            __nv_bfloat162 h = __floats2bfloat162_rn(gelu_exact(v[2 * i] + b0), gelu_exact(v[2 * i + 1] + b1));
+            w[i] = *reinterpret_cast<uint32_t *>(&h);
+        }
+    }
     __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
         if (row >= M) return;
         float z[16];
@@ -89,6 +125,8 @@ struct EpiLinear {
     const float *bias;
     float *out;
     int64_t ldo;
+    __device__ __forceinline__ bool tma_store() const { return false; }
+    __device__ __forceinline__ void compute(int, const float (&)[16], uint32_t (&)[8]) const {}
     __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
         if (row >= M) return;
         float *o = out + (int64_t)row * ldo + col0;
@@ -117,6 +155,8 @@ struct EpiGeluGrad {
     int64_t ldz;
     __nv_bfloat16 *out;
     int64_t ldo;
+    __device__ __forceinline__ bool tma_store() const { return false; }
+    __device__ __forceinline__ void compute(int, const float (&)[16], uint32_t (&)[8]) const {}
     __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
         if (row >= M) return;
         const float *zr = z + (int64_t)row * ldz + col0;
@@ -131,15 +171,16 @@ struct EpiGeluGrad {
 
 template <int BN, int STAGES, class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    gemm_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                   int K, Epi epi, int *err) {
+    gemm_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, int M, int N, int K, Epi epi, int *err) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
     using L = GemmSmem<BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t *sA = smem;
     uint8_t *sB = smem + STAGES * L::kABytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kTiles);
+    uint8_t *staging = smem + L::kTiles;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kTiles + L::kStaging);
     uint64_t *full = bars;
     uint64_t *empty = bars + STAGES;
     uint64_t *tfull = bars + 2 * STAGES;
@@ -154,7 +195,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 128); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 32 * kEpiWarps); }
         tc::mbar_init(drain, 1);
         tc::fence_barrier_init();
     }
@@ -224,6 +265,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
     } else {
         const int quad = warp & 3;
+        const int group = (warp - 2) >> 2;          // 0 or 1: which half of the column chunks
+        const bool tma = epi.tma_store();
+        uint8_t *my_stage = staging + (size_t)(warp - 2) * 2 * kStageBytesPerWarp;
+        int nstore = 0;
+        if (tma && lane == 0) tc::tma_prefetch_desc(&tmC);
         int t = 0;
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
             const int acc = t & 1;
@@ -231,19 +277,40 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (!tc::mbar_wait(&tfull[acc], aph)) { atomicExch(err, tc::kErrTimeoutTmemFull); break; }
             tc::tc_fence_after();
             const int m_blk = tile / n_tiles, n_blk = tile % n_tiles;
-            const int row = m_blk * kBM + quad * 32 + lane;
+            const int row0 = m_blk * kBM + quad * 32;
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u;
 #pragma unroll 1
-            for (int c = 0; c < BN / 16; ++c) {
+            for (int c = group; c < BN / 16; c += 2) {
                 const int col0 = n_blk * BN + c * 16;
                 if (col0 >= N) break;               // warp-uniform
                 float v[16];
                 tc::tmem_ld16(tbase + (uint32_t)(c * 16), v);
-                epi(row, col0, v);
+                if (tma) {
+                    if (row0 >= M) continue;            // warp-uniform: nothing of this slice is in range
+                    uint32_t w[8];
+                    epi.compute(col0, v, w);
+                    uint8_t *buf = my_stage + (nstore & 1) * kStageBytesPerWarp;
+                    if (nstore >= 2 && lane == 0) tc::bulk_wait_read<1>();   // this buffer's previous store has read it
+                    __syncwarp();
+                    uint4 *dst = reinterpret_cast<uint4 *>(buf + lane * 32);
+                    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    tc::fence_proxy_async_smem();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::tma_store_2d(&tmC, buf, col0, row0);
+                        tc::bulk_commit();
+                    }
+                    ++nstore;
+                } else {
+                    epi(row0 + lane, col0, v);
+                }
             }
             tc::tc_fence_before();
             tc::mbar_arrive(&tempty[acc]);
         }
+        if (tma && lane == 0) tc::bulk_wait<0>();    // stores complete before the CTA exits
+        __syncwarp();
     }
     __syncthreads();
     if (warp == 1) {

@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -58,6 +59,29 @@ inline int num_sms() {
     return sms;
 }
 
+// Output tensor map for the TMA-store epilogue: BF16 [rows][cols], box 32 rows x 16 columns, no swizzle.
+inline int make_tmap_out_bf16(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld) {
+    if (!aligned16(ptr) || (ld * 2) % 16 != 0)
+        return set_error(CHEM_EINVAL, "GEMM output: base must be 16-byte aligned and rows a multiple of 16 bytes");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint32_t box[2] = {16, 32};
+    cuuint32_t estr[2] = {1, 1};
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled_fn();
+    if (!enc) return set_error(CHEM_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(CHEM_ECUDA, "cuTensorMapEncodeTiled (output) failed (" + std::to_string((int)r) + ")");
+    return CHEM_OK;
+}
+
+template <class Epi> struct EpiOut { static const void *ptr(const Epi &) { return nullptr; } static int64_t ld(const Epi &) { return 0; } };
+template <> struct EpiOut<EpiGelu> {
+    static const void *ptr(const EpiGelu &e) { return e.tma_store() ? e.out : nullptr; }
+    static int64_t ld(const EpiGelu &e) { return e.ldo; }
+};
+
 template <int BN, int STAGES, class Epi>
 int launch_gemm_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K, const Epi &epi,
                    int *err, cudaStream_t st, int max_ctas) {
@@ -75,11 +99,21 @@ int launch_gemm_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M
     if (rc) return rc;
     rc = make_tmap_bf16(&tb, W, N, K, ldw, BN);
     if (rc) return rc;
+    CUtensorMap tc;
+    std::memset(&tc, 0, sizeof(tc));
+    if (const void *op = EpiOut<Epi>::ptr(epi)) {
+        rc = make_tmap_out_bf16(&tc, op, M, N, EpiOut<Epi>::ld(epi));
+        if (rc) return rc;
+    }
     const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
     int grid = num_sms();
     if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
     if (tiles < grid) grid = tiles;
-    gemm_tn_kernel<BN, STAGES, Epi><<<grid, kGemmThreads, L::kTotal, st>>>(ta, tb, M, N, K, epi, err);
+    void *pb = prof_begin(st);
+    gemm_tn_kernel<BN, STAGES, Epi><<<grid, kGemmThreads, L::kTotal, st>>>(ta, tb, tc, M, N, K, epi, err);
+    if (pb)
+        prof_end(pb, st, "gemm_tn_kernel<" + std::to_string(BN) + "> " + std::to_string(N) + "x" + std::to_string(K),
+                 2.0 * M * N * K, 2.0 * ((double)M * K + (double)N * K));
     return check_cuda(cudaGetLastError(), "GEMM launch");
 }
 

@@ -79,6 +79,10 @@ struct chem_mech {
 
 namespace chemgb {
 int set_error(int code, const std::string &msg);
+// opt-in per-kernel timing (chem_prof_enable): events around tagged launches
+bool prof_on();
+void *prof_begin(cudaStream_t st);
+void prof_end(void *begin, cudaStream_t st, const std::string &tag, double flops, double bytes);
 int check_cuda(cudaError_t e, const char *what);
 bool device_ok(std::string *why);
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -100,64 +100,91 @@ __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict_
     }
 }
 
-// NASA-7 mixture h (J/kg) and cp (J/kg/K) in FP32 from the FP32 property tables.
-__device__ __forceinline__ void mix_h_cp(const PropTables<float> &tb, int N, float T_mid, float T, const double *Yk,
-                                         float &h, float &cp) {
-    const int rng = (T >= T_mid) ? 1 : 0;
-    float hs = 0.0f, cs = 0.0f;
-    for (int k = 0; k < N; ++k) {
-        const float *a = tb.nasa_cp + (rng * N + k) * 5;
-        const float *b = tb.nasa_h + (rng * N + k) * 6;
-        float c = __ldg(a + 4);
-        c = fmaf(c, T, __ldg(a + 3)); c = fmaf(c, T, __ldg(a + 2)); c = fmaf(c, T, __ldg(a + 1)); c = fmaf(c, T, __ldg(a));
-        float hh = __ldg(b + 4);
-        hh = fmaf(hh, T, __ldg(b + 3)); hh = fmaf(hh, T, __ldg(b + 2)); hh = fmaf(hh, T, __ldg(b + 1));
-        hh = fmaf(hh, T, __ldg(b));
-        hh = hh * T + __ldg(b + 5);                 // H_k / R
-        const float yw = (float)Yk[k] * __ldg(tb.invW + k);
-        hs = fmaf(yw, hh, hs);
-        cs = fmaf(yw, c, cs);
-    }
-    h = hs * (float)kR;
-    cp = cs * (float)kR;
-}
-
 // Per cell: dY_k = sigma_k u_k + mu_k (output species), dY_bath = -sum dY_k,
 // Y' = max(Y + dY, 0) renormalised, T' from h(T', Y') = h(T, Y) by Newton.
-__global__ void epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu, int N, int bath,
-                                int n_out, const int *__restrict__ out_sp, const float *__restrict__ mu_u,
-                                const float *__restrict__ sd_u, PropTables<float> tb, float T_mid,
-                                double *__restrict__ T, double *__restrict__ Y, int32_t *__restrict__ status) {
+// dY and the provisional Y' live in FP32 registers (species loops unrolled to
+// the compile-time bound NMAX) for the enthalpy Newton iteration; the final
+// clamp and renormalisation are FP64 so that sum Y' = 1 to FP64 round-off.
+template <int NMAX>
+__global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu,
+                                                       int N, int bath, const float *__restrict__ mu_u,
+                                                       const float *__restrict__ sd_u, PropTables<float> tb,
+                                                       float T_mid, double *__restrict__ T, double *__restrict__ Y,
+                                                       int32_t *__restrict__ status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double y[kMaxSpecies];
-    double y0[kMaxSpecies];
-    for (int k = 0; k < N; ++k) { y0[k] = Y[(int64_t)k * ld + i]; y[k] = y0[k]; }
     const float *ur = u + i * ldu;
-    double sum_dy = 0.0;
-    for (int j = 0; j < n_out; ++j) {
-        const double dy = (double)fmaf(__ldg(sd_u + j), ur[j], __ldg(mu_u + j));
-        y[out_sp[j]] += dy;
-        sum_dy += dy;
-    }
-    y[bath] -= sum_dy;
-    double s = 0.0;
-    for (int k = 0; k < N; ++k) { y[k] = fmax(y[k], 0.0); s += y[k]; }
-    const double inv = 1.0 / s;
-    for (int k = 0; k < N; ++k) y[k] *= inv;
     const float T0 = (float)T[i];
-    float h0, cp0;
-    mix_h_cp(tb, N, T_mid, T0, y0, h0, cp0);
+    const int r0 = (T0 >= T_mid) ? 1 : 0;
+    float dy[NMAX], yf[NMAX];
+    float sum = 0.0f, h0 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+        dy[k] = 0.0f;
+        yf[k] = 0.0f;
+        if (k < N) {
+            const float y = (float)Y[(int64_t)k * ld + i];
+            yf[k] = y;
+            if (k != bath) {
+                const int j = (k < bath) ? k : k - 1;   // outputs: the non-bath species, ascending
+                dy[k] = fmaf(__ldg(sd_u + j), ur[j], __ldg(mu_u + j));
+                sum += dy[k];
+            }
+            const float *b = tb.nasa_h + (r0 * N + k) * 6;
+            float hh = __ldg(b + 4);
+            hh = fmaf(hh, T0, __ldg(b + 3)); hh = fmaf(hh, T0, __ldg(b + 2)); hh = fmaf(hh, T0, __ldg(b + 1));
+            hh = fmaf(hh, T0, __ldg(b));
+            hh = hh * T0 + __ldg(b + 5);               // H_k / R
+            h0 = fmaf(y * __ldg(tb.invW + k), hh, h0);
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k) {
+        if (k < N) {
+            if (k == bath) dy[k] = -sum;
+            yf[k] = fmaxf(yf[k] + dy[k], 0.0f);
+            s += yf[k];
+        }
+    }
+    const float invs = 1.0f / s;
     float Tn = T0;
     for (int it = 0; it < 30; ++it) {
-        float h1, cp1;
-        mix_h_cp(tb, N, T_mid, Tn, y, h1, cp1);
-        const float d = (h1 - h0) / cp1;
+        const int rg = (Tn >= T_mid) ? 1 : 0;
+        float h1 = 0.0f, c1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < N) {
+                const float *a = tb.nasa_cp + (rg * N + k) * 5;
+                const float *b = tb.nasa_h + (rg * N + k) * 6;
+                float c = __ldg(a + 4);
+                c = fmaf(c, Tn, __ldg(a + 3)); c = fmaf(c, Tn, __ldg(a + 2)); c = fmaf(c, Tn, __ldg(a + 1));
+                c = fmaf(c, Tn, __ldg(a));
+                float hh = __ldg(b + 4);
+                hh = fmaf(hh, Tn, __ldg(b + 3)); hh = fmaf(hh, Tn, __ldg(b + 2)); hh = fmaf(hh, Tn, __ldg(b + 1));
+                hh = fmaf(hh, Tn, __ldg(b));
+                hh = hh * Tn + __ldg(b + 5);
+                const float yw = yf[k] * invs * __ldg(tb.invW + k);
+                h1 = fmaf(yw, hh, h1);
+                c1 = fmaf(yw, c, c1);
+            }
+        }
+        const float d = (h1 - h0) / c1;        // both in units of R
         Tn -= d;
         if (fabsf(d) < 1e-4f) break;
     }
+    double s64 = 0.0;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k)
+        if (k < N) s64 += fmax(Y[(int64_t)k * ld + i] + (double)dy[k], 0.0);
+    const double inv = 1.0 / s64;
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k)
+        if (k < N) {
+            double *q = Y + (int64_t)k * ld + i;
+            *q = fmax(*q + (double)dy[k], 0.0) * inv;
+        }
     T[i] = (double)Tn;
-    for (int k = 0; k < N; ++k) Y[(int64_t)k * ld + i] = y[k];
     if (status) status[i] = CHEM_CELL_OK;
 }
 
@@ -389,8 +416,10 @@ int check_state_args(int64_t ncells, int64_t ld, const void *T, const void *p, c
 // prologue + four layers on cells [0, n) of the given SoA pointers; normalised outputs into m->out
 int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p, const double *Y,
                   cudaStream_t st) {
+    void *pb = prof_begin(st);
     prologue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, T, p, Y, nullptr, m->N, m->n_in_pad, m->mu_x,
                                                                  m->isd_x, m->a0);
+    prof_end(pb, st, "prologue_kernel", 0.0, (double)n * ((m->N + 2) * 8 + m->n_in_pad * 2));
     int rc = check_cuda(cudaGetLastError(), "prologue");
     if (rc) return rc;
     const __nv_bfloat16 *x = m->a0;
@@ -653,9 +682,21 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
         const int64_t n = (ncells - c0 < m->chunk) ? ncells - c0 : m->chunk;
         rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
         if (rc) return rc;
-        epilogue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
-            n, ld, m->out, m->n_out_pad, m->N, m->bath, m->n_out, m->out_sp_dev, m->mu_u, m->sd_u, mech->dev.f32,
-            (float)mech->T_mid, T + c0, Y + c0, status ? status + c0 : nullptr);
+        void *pb = prof_begin(st);
+        const unsigned eg = (unsigned)((n + 127) / 128);
+        if (m->N <= 16)
+            epilogue_kernel<16><<<eg, 128, 0, st>>>(n, ld, m->out, m->n_out_pad, m->N, m->bath, m->mu_u, m->sd_u,
+                                                    mech->dev.f32, (float)mech->T_mid, T + c0, Y + c0,
+                                                    status ? status + c0 : nullptr);
+        else if (m->N <= 32)
+            epilogue_kernel<32><<<eg, 128, 0, st>>>(n, ld, m->out, m->n_out_pad, m->N, m->bath, m->mu_u, m->sd_u,
+                                                    mech->dev.f32, (float)mech->T_mid, T + c0, Y + c0,
+                                                    status ? status + c0 : nullptr);
+        else
+            epilogue_kernel<64><<<eg, 128, 0, st>>>(n, ld, m->out, m->n_out_pad, m->N, m->bath, m->mu_u, m->sd_u,
+                                                    mech->dev.f32, (float)mech->T_mid, T + c0, Y + c0,
+                                                    status ? status + c0 : nullptr);
+        prof_end(pb, st, "epilogue_kernel", 0.0, (double)n * (m->N * 16 + 16 + m->n_out_pad * 4));
         rc = check_cuda(cudaGetLastError(), "chem_step_ann epilogue");
         if (rc) return rc;
     }

@@ -183,10 +183,14 @@ int launch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, 
     int blocks = (int)(need < max_blocks ? need : max_blocks);
     const PropTables<real> &tb = (sizeof(real) == 4) ? *reinterpret_cast<const PropTables<real> *>(&m->dev.f32)
                                                       : *reinterpret_cast<const PropTables<real> *>(&m->dev.f64);
+    void *pb = prof_begin(st);
     props_kernel<real, in_t, NMAX><<<blocks, 128, 0, st>>>(
         m->N, m->dev.Np, real(m->T_mid), tb, ncells, ld, static_cast<const in_t *>(T), static_cast<const in_t *>(p),
         static_cast<const in_t *>(Y), static_cast<real *>(cp), static_cast<real *>(h), static_cast<real *>(mu),
         static_cast<real *>(lam), static_cast<real *>(Dk));
+    prof_end(pb, st, std::string("props_kernel<") + (sizeof(real) == 4 ? "f32" : "f64") + ">",
+             (double)ncells * (16.0 * m->N * m->N + 30.0 * m->N),
+             (double)ncells * ((m->N + 2) * sizeof(in_t) + (4 + m->N) * sizeof(real)));
     return check_cuda(cudaGetLastError(), "props_eval launch");
 }
 

@@ -627,8 +627,10 @@ extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, d
     unsigned int *queue = m->dev.counters;
     int rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "chem_step_stiff: queue reset");
     if (rc) return rc;
+    void *pb = prof_begin(st);
     stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue, nullptr,
                                                     nullptr, CHEM_CELL_OK);
+    prof_end(pb, st, "stiff_kernel", 0.0, 0.0);
     return check_cuda(cudaGetLastError(), "chem_step_stiff launch");
 }
 

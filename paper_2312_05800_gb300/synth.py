@@ -474,7 +474,8 @@ def states_profiles(m: Mech, ncells: int, seed: int, ld: int | None = None,
     equivalence ratio phi = phi_lo + s (phi_hi - phi_lo); a progress variable
     c ~ U[0,1] blends the unburnt fuel/air mixture with its complete-combustion
     products, and each intermediate species gets a bump 4c(1-c) with a seeded
-    amplitude. T rises from 300 K to a burnt value estimated from the seeded
+    amplitude (a fixed property of the mechanism, the same for every state
+    seed). T rises from 300 K to a burnt value estimated from the seeded
     formation enthalpies with a constant cp of 1400 J/kg/K (the estimate only
     shapes the sample; it is not the method's thermodynamics). Mass fractions
     then get a log-normal perturbation exp(noise * xi) and are renormalised.
@@ -518,7 +519,9 @@ def states_profiles(m: Mech, ncells: int, seed: int, ld: int | None = None,
     T = 300.0 + c * (Tb - 300.0)
     Y = (1.0 - c)[None, :] * Yu + c[None, :] * Yb
     majors = {fuel, ox, bath, water} | ({co2} if co2 is not None else set())
-    amp = 10.0 ** rng.uniform(-6.0, -2.0, N)
+    # the intermediates' peak amplitudes belong to the mechanism (fixed per mechanism), so every
+    # state seed samples the same distribution; only the per-cell draws depend on `seed`
+    amp = 10.0 ** np.random.default_rng(7000 + N).uniform(-6.0, -2.0, N)
     bump = 4.0 * c * (1.0 - c)
     for k in range(N):
         if k not in majors:

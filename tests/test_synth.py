@@ -42,3 +42,12 @@ def test_perturbation_fraction():
     assert mask.sum() == 100
     assert np.allclose(np.abs(T2[mask] - T[mask])[T[mask] > 600], 300.0)
     assert np.abs(Y2[:, :5000].sum(axis=0) - 1).max() < 1e-14
+
+
+def test_state_seeds_sample_one_distribution():
+    # different state seeds draw from the same distribution (per-species statistics agree)
+    m = synth.mech_c2()
+    a = synth.states_profiles(m, 20000, 11)[2][:, :20000]
+    b = synth.states_profiles(m, 20000, 12)[2][:, :20000]
+    la, lb = np.log10(a).mean(axis=1), np.log10(b).mean(axis=1)
+    assert np.abs(la - lb).max() < 0.05
