@@ -340,16 +340,20 @@ def bench_ann(args, rank, world, local):
     dm = binding.Mech(smech)
     N = smech.N
     # ---- training (untimed): GPU stiff pairs, statistics, Adam on Eq. 5
-    t0 = time.perf_counter()
-    data = train.make_training_set(dm, smech, args.train_pairs, seed=2103 + 1000 * rank)
-    t_data = time.perf_counter() - t0
     net = binding.Mlp(dm, hidden=(1600, 800, 400), dt=DT, seed=3003, chunk=262144, max_batch=4096)
-    train.fit_norm(net, data)
-    t0 = time.perf_counter()
-    hist = train.train(net, data, epochs=args.epochs, batch=4096, lr0=args.lr)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    del data
+    if args.untrained:
+        t_data = t_train = 0.0
+        hist = [float("nan")]
+    else:
+        t0 = time.perf_counter()
+        data = train.make_training_set(dm, smech, args.train_pairs, seed=2103 + 1000 * rank)
+        t_data = time.perf_counter() - t0
+        train.fit_norm(net, data)
+        t0 = time.perf_counter()
+        hist = train.train(net, data, epochs=args.epochs, batch=4096, lr0=args.lr)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        del data
     # ---- inference workload
     ncells = args.cells
     T, p, Y = synth.states_profiles(smech, ncells, 2003 + 1000 * rank, ld=synth.padded_ld(ncells))
@@ -363,7 +367,7 @@ def bench_ann(args, rank, world, local):
     hh, mu, lam = torch.empty_like(cp), torch.empty_like(cp), torch.empty_like(cp)
     Dk = torch.empty(N, ld, dtype=torch.float32, device=dev)
     # ---- accuracy on held-out cells against a tight stiff integration
-    ne = min(args.eval_cells, ncells)
+    ne = min(args.eval_cells, ncells) if not args.untrained else 4
     Ta, Ya = T0.clone(), Y0.clone()
     binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_BF16, None, Ta, p0, Ya, status)
     Tr, Yr = T0.clone(), Y0.clone()
@@ -519,6 +523,9 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-cells", type=int, default=32768)
     ap.add_argument("--stiff-sample", type=int, default=262144)
+    ap.add_argument("--untrained", action="store_true",
+                    help="profiling captures only: skip training and the accuracy check (kernel times do not "
+                         "depend on the weights)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

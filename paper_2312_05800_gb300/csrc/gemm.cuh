@@ -3,13 +3,13 @@
 // This is the dense contraction of every MLP layer (Sec. 3.2: hidden layers of
 // 1600, 800 and 400 GELU units), forward and backward.
 //
-// Roles (320 threads per CTA, one CTA per SM, static round-robin over tiles):
+// Roles (576 threads per CTA, one CTA per SM, static round-robin over tiles):
 //   warp 0      TMA producer: 128 x 64 tile of X and BN x 64 tile of W per
 //               k-block into a STAGES-deep ring (128-byte swizzle).
 //   warp 1      TMEM allocation and the single MMA-issuing thread:
 //               tcgen05.mma kind::f16, M = 128, N = BN, K = 16 per instruction,
 //               accumulating in one of two TMEM buffers (columns 0 and 256).
-//   warps 2..9  epilogue: two warps per TMEM lane quadrant (warp w reads TMEM
+//   warps 2..17 epilogue: four warps per TMEM lane quadrant (warp w reads TMEM
 //               lanes 32 (w % 4) .. +31, i.e. output rows) split the 16-column
 //               chunks between them; tcgen05.ld, then the functor. BF16 GELU
 //               outputs are staged per warp in shared memory (double buffered)
@@ -25,8 +25,8 @@
 
 namespace chemgb {
 
-constexpr int kGemmThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kStageBytesPerWarp = 32 * 16 * 2;   // one 32 x 16 BF16 chunk
 constexpr int kBM = 128;
 constexpr int kBK = 64;
@@ -43,22 +43,38 @@ struct GemmSmem {
     static_assert(kBBytes % 1024 == 0, "B tile must keep 1024-byte alignment");
 };
 
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // erf by Abramowitz and Stegun (1964) formula 7.1.26: for x >= 0,
 // erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x),
-// absolute error <= 1.5e-7 (far below the BF16 rounding of the activations);
-// odd in x.
+// absolute error <= 1.5e-7; odd in x. The reciprocal and the exponential use
+// the hardware approximations (relative error ~2^-22), which keeps the total
+// error near 2e-7, far below the BF16 rounding of the activations.
 __device__ __forceinline__ float erf_as(float x) {
     const float ax = fabsf(x);
-    const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
+    const float t = rcp_approx(fmaf(0.3275911f, ax, 1.0f));
     float y = fmaf(1.061405429f, t, -1.453152027f);
     y = fmaf(y, t, 1.421413741f);
     y = fmaf(y, t, -0.284496736f);
     y = fmaf(y, t, 0.254829592f);
-    const float r = 1.0f - y * t * __expf(-ax * ax);
+    const float e = ex2_approx(ax * (ax * -1.4426950408889634f));   // exp(-x^2)
+    const float r = fmaf(-y * t, e, 1.0f);
     return copysignf(r, x);
 }
 // GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative Phi(z) + z phi(z)
-__device__ __forceinline__ float gelu_exact(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_exact(float z) {
+    const float hz = 0.5f * z;
+    return fmaf(hz, erf_as(z * 0.70710678118654752f), hz);
+}
 __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
@@ -75,15 +91,24 @@ struct EpiGelu {
     float *pre;      // may be null
     int64_t ldp;
     // TMA stores clip at 16-byte granularity in the row, so they are used only
-    // when every row of the output ends on a 16-byte boundary (N % 8 == 0)
-    __host__ __device__ __forceinline__ bool tma_store() const { return pre == nullptr && (N & 7) == 0; }
-    // the 16 BF16 values of (row, col0..col0+15), two per 32-bit word
+    // when rows end on whole 16-column chunks (N % 16 == 0) with a 16-byte
+    // aligned bias (read as float4)
+    __host__ __device__ __forceinline__ bool tma_store() const {
+        return pre == nullptr && (N & 15) == 0 && bias != nullptr && (reinterpret_cast<uintptr_t>(bias) & 15) == 0;
+    }
+    // the 16 BF16 values of (row, col0..col0+15), two per 32-bit word (N % 8 == 0 on this path,
+    // and the bias is padded to whole 16-float groups)
     __device__ __forceinline__ void compute(int col0, const float (&v)[16], uint32_t (&w)[8]) const {
+        float b[16];
+        const float4 *bp = reinterpret_cast<const float4 *>(bias + col0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 q = __ldg(bp + i);
+            b[4 * i] = q.x; b[4 * i + 1] = q.y; b[4 * i + 2] = q.z; b[4 * i + 3] = q.w;
+        }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float b0 = (col0 + 2 * i < N) ? __ldg(bias + col0 + 2 * i) : 0.0f;
-            const float b1 = (col0 + 2 * i + 1 < N) ? __ldg(bias + col0 + 2 * i + 1) : 0.0f;
-            __nv_bfloat162 h = __floats2bfloat162_rn(gelu_exact(v[2 * i] + b0), gelu_exact(v[2 * i + 1] + b1));
+            __nv_bfloat162 h = __floats2bfloat162_rn(gelu_exact(v[2 * i] + b[2 * i]), gelu_exact(v[2 * i + 1] + b[2 * i + 1]));
             w[i] = *reinterpret_cast<uint32_t *>(&h);
         }
     }
@@ -265,7 +290,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
     } else {
         const int quad = warp & 3;
-        const int group = (warp - 2) >> 2;          // 0 or 1: which half of the column chunks
+        const int group = (warp - 2) >> 2;          // 0..3: which quarter of the column chunks
         const bool tma = epi.tma_store();
         uint8_t *my_stage = staging + (size_t)(warp - 2) * 2 * kStageBytesPerWarp;
         int nstore = 0;
@@ -280,7 +305,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int row0 = m_blk * kBM + quad * 32;
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u;
 #pragma unroll 1
-            for (int c = group; c < BN / 16; c += 2) {
+            for (int c = group; c < BN / 16; c += kEpiWarps / 4) {
                 const int col0 = n_blk * BN + c * 16;
                 if (col0 >= N) break;               // warp-uniform
                 float v[16];

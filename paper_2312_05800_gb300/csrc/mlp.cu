@@ -111,6 +111,18 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
                                                        const float *__restrict__ sd_u, PropTables<float> tb,
                                                        float T_mid, double *__restrict__ T, double *__restrict__ Y,
                                                        int32_t *__restrict__ status) {
+    // per species and range: cp/R coefficients (5), H/R coefficients (6), 1/W -> 3 float4
+    __shared__ float4 tab[2 * NMAX * 3];
+    for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
+        const int rg = e / N, k = e % N;
+        const float *a = tb.nasa_cp + (rg * N + k) * 5;
+        const float *b = tb.nasa_h + (rg * N + k) * 6;
+        float4 *o = tab + (rg * NMAX + k) * 3;
+        o[0] = make_float4(a[0], a[1], a[2], a[3]);
+        o[1] = make_float4(a[4], b[0], b[1], b[2]);
+        o[2] = make_float4(b[3], b[4], b[5], tb.invW[k]);
+    }
+    __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const float *ur = u + i * ldu;
@@ -130,12 +142,11 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
                 dy[k] = fmaf(__ldg(sd_u + j), ur[j], __ldg(mu_u + j));
                 sum += dy[k];
             }
-            const float *b = tb.nasa_h + (r0 * N + k) * 6;
-            float hh = __ldg(b + 4);
-            hh = fmaf(hh, T0, __ldg(b + 3)); hh = fmaf(hh, T0, __ldg(b + 2)); hh = fmaf(hh, T0, __ldg(b + 1));
-            hh = fmaf(hh, T0, __ldg(b));
-            hh = hh * T0 + __ldg(b + 5);               // H_k / R
-            h0 = fmaf(y * __ldg(tb.invW + k), hh, h0);
+            const float4 *q = tab + (r0 * NMAX + k) * 3;
+            const float4 q1 = q[1], q2 = q[2];
+            float hh = fmaf(fmaf(fmaf(fmaf(q2.y, T0, q2.x), T0, q1.w), T0, q1.z), T0, q1.y);
+            hh = hh * T0 + q2.z;                       // H_k / R
+            h0 = fmaf(y * q2.w, hh, h0);
         }
     }
     float s = 0.0f;
@@ -155,16 +166,12 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
             if (k < N) {
-                const float *a = tb.nasa_cp + (rg * N + k) * 5;
-                const float *b = tb.nasa_h + (rg * N + k) * 6;
-                float c = __ldg(a + 4);
-                c = fmaf(c, Tn, __ldg(a + 3)); c = fmaf(c, Tn, __ldg(a + 2)); c = fmaf(c, Tn, __ldg(a + 1));
-                c = fmaf(c, Tn, __ldg(a));
-                float hh = __ldg(b + 4);
-                hh = fmaf(hh, Tn, __ldg(b + 3)); hh = fmaf(hh, Tn, __ldg(b + 2)); hh = fmaf(hh, Tn, __ldg(b + 1));
-                hh = fmaf(hh, Tn, __ldg(b));
-                hh = hh * Tn + __ldg(b + 5);
-                const float yw = yf[k] * invs * __ldg(tb.invW + k);
+                const float4 *q = tab + (rg * NMAX + k) * 3;
+                const float4 q0 = q[0], q1 = q[1], q2 = q[2];
+                const float c = fmaf(fmaf(fmaf(fmaf(q1.x, Tn, q0.w), Tn, q0.z), Tn, q0.y), Tn, q0.x);
+                float hh = fmaf(fmaf(fmaf(fmaf(q2.y, Tn, q2.x), Tn, q1.w), Tn, q1.z), Tn, q1.y);
+                hh = hh * Tn + q2.z;
+                const float yw = yf[k] * invs * q2.w;
                 h1 = fmaf(yw, hh, h1);
                 c1 = fmaf(yw, c, c1);
             }

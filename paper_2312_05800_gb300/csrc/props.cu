@@ -31,6 +31,34 @@ __device__ __forceinline__ void load4(const real *p, real &a, real &b, real &c, 
     }
 }
 
+// FP32 tables always fit (8 N Np floats <= 131 KB for N <= 64); FP64 tables stay in global memory.
+constexpr size_t kPropsSmemMax = 8 * 64 * 64 * 4;
+template <typename real>
+__host__ __device__ constexpr bool tables_in_smem() { return sizeof(real) == 4; }
+
+// Copies the per-pair tables (3 Wilke + 5 resistance rows per species) into
+// shared memory when they fit; the inner loops then read them with broadcast
+// LDS.128 instead of uniform global loads.
+template <typename real>
+__device__ __forceinline__ void stage_pair_tables(const PropTables<real> &tb, int N, int Np, real *sh) {
+    const int nw = 3 * N * Np, nd = 5 * N * Np;
+    for (int e = threadIdx.x; e < nw; e += blockDim.x) sh[e] = tb.wilke[e];
+    for (int e = threadIdx.x; e < nd; e += blockDim.x) sh[nw + e] = tb.diff[e];
+    __syncthreads();
+}
+
+template <typename real>
+__device__ __forceinline__ void load4s(const real *p, real &a, real &b, real &c, real &d) {
+    if constexpr (sizeof(real) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a = v.x; b = v.y; c = v.z; d = v.w;
+    } else {
+        const double2 v0 = reinterpret_cast<const double2 *>(p)[0];
+        const double2 v1 = reinterpret_cast<const double2 *>(p)[1];
+        a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+    }
+}
+
 template <typename real, typename in_t, int NMAX>
 __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, PropTables<real> tb, int64_t ncells,
                                                     int64_t ld, const in_t *__restrict__ Tg,
@@ -40,6 +68,12 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
                                                     real *__restrict__ Dkg) {
     const real R = real(kR);
     const bool transport = (mug != nullptr) || (lamg != nullptr) || (Dkg != nullptr);
+    extern __shared__ __align__(16) unsigned char props_smem[];
+    real *shtab = reinterpret_cast<real *>(props_smem);
+    constexpr bool in_smem = tables_in_smem<real>();
+    if (in_smem && transport) stage_pair_tables(tb, N, Np, shtab);
+    const real *wil = in_smem ? shtab : tb.wilke;
+    const real *dif = in_smem ? shtab + 3 * N * Np : tb.diff;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
         const real T = real(Tg[i]);
@@ -120,27 +154,38 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
             cpR = fma(cpR, T, __ldg(a + 1));
             cpR = fma(cpR, T, __ldg(a + 0));
             const real lamk = muk * (cpR + real(1.25)) * R * iw;   // Eucken
-            const real *t0 = tb.wilke + (0 * N + k) * Np;
-            const real *t1 = tb.wilke + (1 * N + k) * Np;
-            const real *t2 = tb.wilke + (2 * N + k) * Np;
-            const real *d0 = tb.diff + (0 * N + k) * Np;
-            const real *d1 = tb.diff + (1 * N + k) * Np;
-            const real *d2 = tb.diff + (2 * N + k) * Np;
-            const real *d3 = tb.diff + (3 * N + k) * Np;
-            const real *d4 = tb.diff + (4 * N + k) * Np;
+            const real *t0 = wil + (0 * N + k) * Np;
+            const real *t1 = wil + (1 * N + k) * Np;
+            const real *t2 = wil + (2 * N + k) * Np;
+            const real *d0 = dif + (0 * N + k) * Np;
+            const real *d1 = dif + (1 * N + k) * Np;
+            const real *d2 = dif + (2 * N + k) * Np;
+            const real *d3 = dif + (3 * N + k) * Np;
+            const real *d4 = dif + (4 * N + k) * Np;
             real a0 = 0, a1 = 0, a2 = 0, ds = 0, gs = 0;
 #pragma unroll
             for (int j4 = 0; j4 < NMAX; j4 += 4) {
                 if (j4 < N) {
                     real w0[4], w1[4], w2[4], g0[4], g1[4], g2[4], g3[4], g4[4];
-                    load4(t0 + j4, w0[0], w0[1], w0[2], w0[3]);
-                    load4(t1 + j4, w1[0], w1[1], w1[2], w1[3]);
-                    load4(t2 + j4, w2[0], w2[1], w2[2], w2[3]);
-                    load4(d0 + j4, g0[0], g0[1], g0[2], g0[3]);
-                    load4(d1 + j4, g1[0], g1[1], g1[2], g1[3]);
-                    load4(d2 + j4, g2[0], g2[1], g2[2], g2[3]);
-                    load4(d3 + j4, g3[0], g3[1], g3[2], g3[3]);
-                    load4(d4 + j4, g4[0], g4[1], g4[2], g4[3]);
+                    if constexpr (in_smem) {
+                        load4s(t0 + j4, w0[0], w0[1], w0[2], w0[3]);
+                        load4s(t1 + j4, w1[0], w1[1], w1[2], w1[3]);
+                        load4s(t2 + j4, w2[0], w2[1], w2[2], w2[3]);
+                        load4s(d0 + j4, g0[0], g0[1], g0[2], g0[3]);
+                        load4s(d1 + j4, g1[0], g1[1], g1[2], g1[3]);
+                        load4s(d2 + j4, g2[0], g2[1], g2[2], g2[3]);
+                        load4s(d3 + j4, g3[0], g3[1], g3[2], g3[3]);
+                        load4s(d4 + j4, g4[0], g4[1], g4[2], g4[3]);
+                    } else {
+                        load4(t0 + j4, w0[0], w0[1], w0[2], w0[3]);
+                        load4(t1 + j4, w1[0], w1[1], w1[2], w1[3]);
+                        load4(t2 + j4, w2[0], w2[1], w2[2], w2[3]);
+                        load4(d0 + j4, g0[0], g0[1], g0[2], g0[3]);
+                        load4(d1 + j4, g1[0], g1[1], g1[2], g1[3]);
+                        load4(d2 + j4, g2[0], g2[1], g2[2], g2[3]);
+                        load4(d3 + j4, g3[0], g3[1], g3[2], g3[3]);
+                        load4(d4 + j4, g4[0], g4[1], g4[2], g4[3]);
+                    }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int j = j4 + u;   // padded columns have zero weights
@@ -171,20 +216,27 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 template <typename real, typename in_t, int NMAX>
 int launch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
                  void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
-    static int max_blocks = 0;
-    if (max_blocks == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, props_kernel<real, in_t, NMAX>, 128, 0);
-        max_blocks = sms * (per_sm > 0 ? per_sm : 1);
+    const bool transport = mu || lam || Dk;
+    const size_t smem = (transport && tables_in_smem<real>()) ? (size_t)8 * m->N * m->dev.Np * sizeof(real) : 0;
+    static size_t configured = 0;
+    if (smem > configured) {
+        int rc = check_cuda(cudaFuncSetAttribute(props_kernel<real, in_t, NMAX>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPropsSmemMax),
+                            "props_eval smem attribute");
+        if (rc) return rc;
+        configured = kPropsSmemMax;
     }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, props_kernel<real, in_t, NMAX>, 128, smem);
+    const int max_blocks = sms * (per_sm > 0 ? per_sm : 1);
     int64_t need = (ncells + 127) / 128;
     int blocks = (int)(need < max_blocks ? need : max_blocks);
     const PropTables<real> &tb = (sizeof(real) == 4) ? *reinterpret_cast<const PropTables<real> *>(&m->dev.f32)
                                                       : *reinterpret_cast<const PropTables<real> *>(&m->dev.f64);
     void *pb = prof_begin(st);
-    props_kernel<real, in_t, NMAX><<<blocks, 128, 0, st>>>(
+    props_kernel<real, in_t, NMAX><<<blocks, 128, smem, st>>>(
         m->N, m->dev.Np, real(m->T_mid), tb, ncells, ld, static_cast<const in_t *>(T), static_cast<const in_t *>(p),
         static_cast<const in_t *>(Y), static_cast<real *>(cp), static_cast<real *>(h), static_cast<real *>(mu),
         static_cast<real *>(lam), static_cast<real *>(Dk));
