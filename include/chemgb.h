@@ -262,6 +262,35 @@ int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
 int chem_mlp_error(const chem_mlp *mlp, int *host_err);
 
 /* ---------------------------------------------------------------------------
+ * Out-of-distribution test and stiff fallback of the learned step
+ * ---------------------------------------------------------------------------
+ * The paper has no such guard: it applies its networks to every cell. Here the
+ * network is trusted only where it was trained; other cells go to the plain
+ * method (chem_step_stiff's integrator), which is both fallback and judge.
+ * chem_mlp_fit_ood builds, from n training states (T, p, Y; device, SoA), an
+ * nbins^3 occupancy grid over the per-cell features
+ *     (T, h/R = sum_k (Y_k / W_k) H_k/R, Y_species)        (FP32, NASA-7)
+ * spanning the training range plus 5 % on each side. A cell is in the
+ * distribution iff its bin lies inside the grid and the 3 x 3 x 3 block of
+ * bins around it holds at least min_count training states. The call enables
+ * the test (nbins <= 64; synchronises the stream).
+ * With the test enabled, chem_step_ann applies the network only to cells in
+ * the distribution; the others keep their state and are integrated by the
+ * stiff method with the `fallback` options (defaults when NULL), status
+ * CHEM_CELL_FALLBACK on success or the stiff error code.
+ */
+int chem_mlp_fit_ood(chem_mlp *mlp, const chem_mech *mech, int64_t n, int64_t ld, const double *T, const double *p,
+                     const double *Y, int32_t species, int32_t nbins, int32_t min_count, chem_stream_t stream);
+/* Turns the test on or off (on requires a fitted grid). */
+int chem_mlp_set_ood(chem_mlp *mlp, int enable);
+/* flags[i] (uint8, device) = 1 when cell i is outside the training distribution. */
+int chem_mlp_ood_flags(const chem_mlp *mlp, const chem_mech *mech, int64_t ncells, int64_t ld, const double *T,
+                       const double *p, const double *Y, uint8_t *flags, chem_stream_t stream);
+/* The fitted grid's feature ranges lo3[3], hi3[3] (host floats) and settings. */
+int chem_mlp_get_ood(const chem_mlp *mlp, float *lo3, float *hi3, int32_t *nbins, int32_t *species,
+                     int32_t *min_count);
+
+/* ---------------------------------------------------------------------------
  * chem_step_ann -- the learned method: advance every cell by the network
  * ---------------------------------------------------------------------------
  * Sec. 3.2: the network predicts u*(t) = Y(t + dt) - Y(t) from (T, p, Y). Per
@@ -271,8 +300,9 @@ int chem_mlp_error(const chem_mlp *mlp, int *host_err);
  * T [ld], Y [N][ld] (double, device) are updated in place; p [ld] is read.
  * dt must equal the dt the network was created for (CHEM_EINVAL otherwise).
  * prec: CHEM_PREC_BF16. status [ld] (int32, device, may be NULL) receives
- * CHEM_CELL_OK. fallback: options of the stiff integrator for cells routed to
- * it (reserved; may be NULL).
+ * CHEM_CELL_OK, or for cells outside the network's training distribution (when
+ * the test of chem_mlp_fit_ood is enabled) the stiff fallback's code.
+ * fallback: stiff options for those cells (NULL = defaults).
  */
 int chem_step_ann(const chem_mech *mech, const chem_mlp *mlp, int64_t ncells, int64_t ld, double dt, int prec,
                   const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,

@@ -77,3 +77,42 @@ def step_ann(mech, layers, stats, T, p, Y, round_bf16=False):
         if np.all(np.abs(d[:n]) < 1e-10):
             break
     return Tn, Yn
+
+
+# ---------------------------------------------------------------------------
+# out-of-distribution test (not in the paper): occupancy grid over (T, h/R, Y_s)
+# ---------------------------------------------------------------------------
+
+def ood_features(mech, T, p, Y, species):
+    """(T, h/R, Y_species) per cell, FP64; h is the NASA-7 mixture enthalpy (J/kg)."""
+    import oracle as O
+    from paper_2312_05800_gb300 import synth
+    n = T.shape[0]
+    h = O.props(mech, T, p, Y)[1]
+    return np.stack([np.asarray(T, np.float64), h / synth.R_GAS, np.asarray(Y[species], np.float64)], axis=1)[:n]
+
+
+def ood_fit(features, nbins=64, kmin=4, margin=0.05):
+    """Grid over the training range +/- margin; mask[i, j, k] = the 3x3x3 block
+    around bin (i, j, k) holds at least kmin training samples."""
+    lo = features.min(axis=0)
+    hi = features.max(axis=0)
+    w = hi - lo
+    lo, hi = lo - margin * w, hi + margin * w
+    b = np.floor((features - lo) / (hi - lo) * nbins).astype(np.int64)
+    counts = np.zeros((nbins,) * 3, np.int64)
+    np.add.at(counts, (b[:, 0], b[:, 1], b[:, 2]), 1)
+    padded = np.pad(counts, 1)
+    nb = nbins
+    block = sum(padded[1 + a:1 + a + nb, 1 + c:1 + c + nb, 1 + d:1 + d + nb]
+                for a in (-1, 0, 1) for c in (-1, 0, 1) for d in (-1, 0, 1))
+    return {"lo": lo, "hi": hi, "nbins": nbins, "mask": block >= kmin, "counts": counts}
+
+
+def ood_flags(fit, features):
+    """True where a cell is outside the training distribution."""
+    nb = fit["nbins"]
+    u = (features - fit["lo"]) / (fit["hi"] - fit["lo"]) * nb
+    outside = ~np.all((u >= 0) & (u < nb), axis=1)
+    b = np.clip(np.floor(u).astype(np.int64), 0, nb - 1)
+    return outside | ~fit["mask"][b[:, 0], b[:, 1], b[:, 2]]

@@ -78,6 +78,10 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_fit_norm.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
     L.chem_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, i64, vp]
     L.chem_mlp_error.argtypes = [vp, vp]
+    L.chem_mlp_fit_ood.argtypes = [vp, vp, i64, i64, vp, vp, vp, i32, i32, i32, vp]
+    L.chem_mlp_set_ood.argtypes = [vp, i32]
+    L.chem_mlp_ood_flags.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, vp]
+    L.chem_mlp_get_ood.argtypes = [vp, vp, vp, vp, vp, vp]
     L.chem_mlp_save.argtypes = [vp, ctypes.c_char_p]
     L.chem_mlp_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
     L.chem_step_ann.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp]
@@ -269,6 +273,30 @@ class Mlp:
             self.free()
         except Exception:
             pass
+
+
+def chem_mlp_fit_ood(mlp: Mlp, mech: Mech, n: int, ld: int, T, p, Y, species: int, nbins: int = 64,
+                     min_count: int = 4, stream=None):
+    _check(lib().chem_mlp_fit_ood(mlp.handle, mech.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), species, nbins,
+                                  min_count, _stream(stream)))
+
+
+def chem_mlp_set_ood(mlp: Mlp, enable: bool):
+    _check(lib().chem_mlp_set_ood(mlp.handle, 1 if enable else 0))
+
+
+def chem_mlp_ood_flags(mlp: Mlp, mech: Mech, ncells: int, ld: int, T, p, Y, flags, stream=None):
+    _check(lib().chem_mlp_ood_flags(mlp.handle, mech.handle, ncells, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(flags),
+                                    _stream(stream)))
+
+
+def chem_mlp_get_ood(mlp: Mlp):
+    import numpy as np
+    lo, hi = np.zeros(3, np.float32), np.zeros(3, np.float32)
+    nb, sp, km = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().chem_mlp_get_ood(mlp.handle, lo.ctypes.data, hi.ctypes.data, ctypes.byref(nb), ctypes.byref(sp),
+                                  ctypes.byref(km)))
+    return lo, hi, nb.value, sp.value, km.value
 
 
 def chem_mlp_fit_norm(mlp: Mlp, n: int, ld: int, T, p, Y, Y1, stream=None):

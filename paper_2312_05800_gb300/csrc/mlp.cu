@@ -14,9 +14,17 @@
 #include "gemm_launch.cuh"
 
 namespace chemgb {
+int launch_stiff_list(const chem_mech *m, int64_t capacity, int64_t ld, double dt, const chem_ode_opts &o, double *T,
+                      const double *p, double *Y, int32_t *status, const int32_t *list, const unsigned int *count,
+                      int ok_status, cudaStream_t st);
+}
+
+namespace chemgb {
 namespace {
 
 constexpr int kLayers = 4;
+constexpr int kOodMaxBins = 64;
+constexpr int kOodBlocks = 512;
 constexpr float kLambdaBC = 0.1f;     // Box-Cox lambda (Sec. 3.2)
 constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
 
@@ -56,6 +64,16 @@ struct chem_mlp {
     __nv_bfloat16 *tx0, *th[3], *tdout, *tdz[3], *tT0, *tT1;
     float *tz[3], *tout, *loss_part;
     int *err;
+    // out-of-distribution grid over (T, h/R, Y_s) and the fallback queue
+    uint32_t *ood_counts;                   // [64^3]
+    uint8_t *ood_mask;                      // [64^3]
+    float *ood_range_dev;                   // lo[3], inv_width[3]
+    float ood_lo[3], ood_hi[3];
+    int ood_nb, ood_kmin, ood_species, ood_fitted, ood_enabled;
+    int32_t *fb_queue;                      // [chunk]
+    unsigned int *fb_count;
+    int32_t *fb_status;                     // [chunk] when the caller passes no status array
+    float *ood_part;                        // per-block feature extrema
     int64_t adam_t;
     void *blob;
     size_t blob_bytes;
@@ -100,17 +118,53 @@ __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict_
     }
 }
 
+// Out-of-distribution features of one cell (FP32): T, h/R = sum_k (Y_k / W_k) H_k/R, Y_s.
+__device__ __forceinline__ void ood_features(const PropTables<float> &tb, int N, float T_mid, int64_t ld, int64_t i,
+                                             const double *T, const double *Y, int s, float f[3]) {
+    const float t = (float)T[i];
+    const int rg = (t >= T_mid) ? 1 : 0;
+    float h = 0.0f;
+    for (int k = 0; k < N; ++k) {
+        const float *b = tb.nasa_h + (rg * N + k) * 6;
+        float hh = fmaf(fmaf(fmaf(fmaf(__ldg(b + 4), t, __ldg(b + 3)), t, __ldg(b + 2)), t, __ldg(b + 1)), t, __ldg(b));
+        hh = hh * t + __ldg(b + 5);
+        h = fmaf((float)Y[(int64_t)k * ld + i] * __ldg(tb.invW + k), hh, h);
+    }
+    f[0] = t;
+    f[1] = h;
+    f[2] = (float)Y[(int64_t)s * ld + i];
+}
+
+// Bin of a feature vector, or -1 outside the grid range.
+__device__ __forceinline__ int ood_bin(const float f[3], const float *range, int nb) {
+    int idx = 0;
+    for (int d = 0; d < 3; ++d) {
+        const float u = (f[d] - range[d]) * range[3 + d];
+        if (!(u >= 0.0f) || u >= (float)nb) return -1;
+        idx = idx * nb + (int)u;
+    }
+    return idx;
+}
+
 // Per cell: dY_k = sigma_k u_k + mu_k (output species), dY_bath = -sum dY_k,
 // Y' = max(Y + dY, 0) renormalised, T' from h(T', Y') = h(T, Y) by Newton.
 // dY and the provisional Y' live in FP32 registers (species loops unrolled to
 // the compile-time bound NMAX) for the enthalpy Newton iteration; the final
 // clamp and renormalisation are FP64 so that sum Y' = 1 to FP64 round-off.
+struct OodRoute {
+    const float *range;      // null: no test
+    const uint8_t *mask;
+    int nb, species;
+    int32_t *queue;
+    unsigned int *count;
+};
+
 template <int NMAX>
 __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu,
                                                        int N, int bath, const float *__restrict__ mu_u,
                                                        const float *__restrict__ sd_u, PropTables<float> tb,
                                                        float T_mid, double *__restrict__ T, double *__restrict__ Y,
-                                                       int32_t *__restrict__ status) {
+                                                       int32_t *__restrict__ status, OodRoute ood) {
     // per species and range: cp/R coefficients (5), H/R coefficients (6), 1/W -> 3 float4
     __shared__ float4 tab[2 * NMAX * 3];
     for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
@@ -147,6 +201,16 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
             float hh = fmaf(fmaf(fmaf(fmaf(q2.y, T0, q2.x), T0, q1.w), T0, q1.z), T0, q1.y);
             hh = hh * T0 + q2.z;                       // H_k / R
             h0 = fmaf(y * q2.w, hh, h0);
+        }
+    }
+    if (ood.range) {
+        // a cell outside the training distribution keeps its state and goes to the stiff integrator
+        const float f[3] = {T0, h0, (float)Y[(int64_t)ood.species * ld + i]};
+        const int b = ood_bin(f, ood.range, ood.nb);
+        if (b < 0 || ood.mask[b] == 0) {
+            const unsigned int q = atomicAdd(ood.count, 1u);
+            ood.queue[q] = (int32_t)i;
+            return;
         }
     }
     float s = 0.0f;
@@ -193,6 +257,65 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
         }
     T[i] = (double)Tn;
     if (status) status[i] = CHEM_CELL_OK;
+}
+
+// per-block minima and maxima of the three features (fixed-order tree reduction)
+__global__ void ood_extrema_kernel(int64_t n, int64_t ld, const double *T, const double *Y, PropTables<float> tb,
+                                   int N, float T_mid, int s, float *part) {
+    __shared__ float smin[3][256], smax[3][256];
+    float mn[3] = {3.4e38f, 3.4e38f, 3.4e38f}, mx[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float f[3];
+        ood_features(tb, N, T_mid, ld, i, T, Y, s, f);
+        for (int d = 0; d < 3; ++d) { mn[d] = fminf(mn[d], f[d]); mx[d] = fmaxf(mx[d], f[d]); }
+    }
+    for (int d = 0; d < 3; ++d) { smin[d][threadIdx.x] = mn[d]; smax[d][threadIdx.x] = mx[d]; }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int d = 0; d < 3; ++d) {
+                smin[d][threadIdx.x] = fminf(smin[d][threadIdx.x], smin[d][threadIdx.x + w]);
+                smax[d][threadIdx.x] = fmaxf(smax[d][threadIdx.x], smax[d][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 3; ++d) { part[blockIdx.x * 6 + d] = smin[d][0]; part[blockIdx.x * 6 + 3 + d] = smax[d][0]; }
+}
+
+__global__ void ood_hist_kernel(int64_t n, int64_t ld, const double *T, const double *Y, PropTables<float> tb, int N,
+                                float T_mid, int s, const float *range, int nb, uint32_t *counts) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float f[3];
+        ood_features(tb, N, T_mid, ld, i, T, Y, s, f);
+        const int b = ood_bin(f, range, nb);
+        if (b >= 0) atomicAdd(counts + b, 1u);
+    }
+}
+
+// in-distribution mask: the 3 x 3 x 3 neighbourhood of a bin holds >= kmin samples
+__global__ void ood_mask_kernel(int nb, int kmin, const uint32_t *counts, uint8_t *mask) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb * nb * nb) return;
+    const int i = b / (nb * nb), j = (b / nb) % nb, k = b % nb;
+    uint32_t c = 0;
+    for (int di = -1; di <= 1; ++di)
+        for (int dj = -1; dj <= 1; ++dj)
+            for (int dk = -1; dk <= 1; ++dk) {
+                const int a = i + di, bb = j + dj, cc = k + dk;
+                if (a >= 0 && a < nb && bb >= 0 && bb < nb && cc >= 0 && cc < nb) c += counts[(a * nb + bb) * nb + cc];
+            }
+    mask[b] = (c >= (uint32_t)kmin) ? 1 : 0;
+}
+
+__global__ void ood_flags_kernel(int64_t n, int64_t ld, const double *T, const double *Y, PropTables<float> tb, int N,
+                                 float T_mid, int s, const float *range, int nb, const uint8_t *mask, uint8_t *out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float f[3];
+    ood_features(tb, N, T_mid, ld, i, T, Y, s, f);
+    const int b = ood_bin(f, range, nb);
+    out[i] = (b < 0 || mask[b] == 0) ? 1 : 0;
 }
 
 // L1 loss of Eq. 5 on normalised outputs; dL/du = sign(u - u*)/B written as BF16.
@@ -523,6 +646,13 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->tT0, (size_t)B * maxw * 2});
     parts.push_back({(void **)&m->tT1, (size_t)B * maxw * 2});
     parts.push_back({(void **)&m->loss_part, (size_t)B * 4});
+    parts.push_back({(void **)&m->ood_counts, (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins * 4});
+    parts.push_back({(void **)&m->ood_mask, (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins});
+    parts.push_back({(void **)&m->ood_range_dev, 64});
+    parts.push_back({(void **)&m->fb_queue, (size_t)C * 4});
+    parts.push_back({(void **)&m->fb_count, 64});
+    parts.push_back({(void **)&m->fb_status, (size_t)C * 4});
+    parts.push_back({(void **)&m->ood_part, (size_t)kOodBlocks * 6 * 4});
     size_t total = 0;
     for (auto &pp : parts) total = align256(total) + pp.second;
     total = align256(total);
@@ -689,24 +819,122 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
         const int64_t n = (ncells - c0 < m->chunk) ? ncells - c0 : m->chunk;
         rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
         if (rc) return rc;
+        OodRoute route{nullptr, nullptr, 0, 0, nullptr, nullptr};
+        int32_t *st_chunk = status ? status + c0 : m->fb_status;
+        if (m->ood_enabled) {
+            route = OodRoute{m->ood_range_dev, m->ood_mask, m->ood_nb, m->ood_species, m->fb_queue, m->fb_count};
+            rc = check_cuda(cudaMemsetAsync(m->fb_count, 0, sizeof(unsigned int), st), "chem_step_ann: queue reset");
+            if (rc) return rc;
+        }
         void *pb = prof_begin(st);
         const unsigned eg = (unsigned)((n + 127) / 128);
         if (m->N <= 16)
             epilogue_kernel<16><<<eg, 128, 0, st>>>(n, ld, m->out, m->n_out_pad, m->N, m->bath, m->mu_u, m->sd_u,
                                                     mech->dev.f32, (float)mech->T_mid, T + c0, Y + c0,
-                                                    status ? status + c0 : nullptr);
+                                                    st_chunk, route);
         else if (m->N <= 32)
             epilogue_kernel<32><<<eg, 128, 0, st>>>(n, ld, m->out, m->n_out_pad, m->N, m->bath, m->mu_u, m->sd_u,
                                                     mech->dev.f32, (float)mech->T_mid, T + c0, Y + c0,
-                                                    status ? status + c0 : nullptr);
+                                                    st_chunk, route);
         else
             epilogue_kernel<64><<<eg, 128, 0, st>>>(n, ld, m->out, m->n_out_pad, m->N, m->bath, m->mu_u, m->sd_u,
                                                     mech->dev.f32, (float)mech->T_mid, T + c0, Y + c0,
-                                                    status ? status + c0 : nullptr);
+                                                    st_chunk, route);
         prof_end(pb, st, "epilogue_kernel", 0.0, (double)n * (m->N * 16 + 16 + m->n_out_pad * 4));
         rc = check_cuda(cudaGetLastError(), "chem_step_ann epilogue");
         if (rc) return rc;
+        if (m->ood_enabled) {
+            chem_ode_opts o;
+            chem_ode_opts_default(&o);
+            if (fallback) o = *fallback;
+            void *pf = prof_begin(st);
+            rc = launch_stiff_list(mech, n, ld, dt, o, T + c0, p + c0, Y + c0, st_chunk, m->fb_queue, m->fb_count,
+                                   CHEM_CELL_FALLBACK, st);
+            prof_end(pf, st, "stiff_kernel (fallback)", 0.0, 0.0);
+            if (rc) return rc;
+        }
     }
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_fit_ood(chem_mlp *m, const chem_mech *mech, int64_t n, int64_t ld, const double *T,
+                                const double *p, const double *Y, int32_t species, int32_t nbins, int32_t min_count,
+                                chem_stream_t stream) {
+    if (!m || !mech) return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: null handle");
+    int rc = check_state_args(n, ld, T, p, Y, "chem_mlp_fit_ood");
+    if (rc) return rc;
+    if (n < 1 || species < 0 || species >= m->N || nbins < 2 || nbins > kOodMaxBins || min_count < 1)
+        return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: need n >= 1, a valid species, 2 <= nbins <= 64, min_count >= 1");
+    if (mech->N != m->N) return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: network and mechanism disagree");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const float Tmid = (float)mech->T_mid;
+    ood_extrema_kernel<<<kOodBlocks, 256, 0, st>>>(n, ld, T, Y, mech->dev.f32, m->N, Tmid, species, m->ood_part);
+    std::vector<float> part(kOodBlocks * 6);
+    rc = check_cuda(cudaMemcpyAsync(part.data(), m->ood_part, part.size() * 4, cudaMemcpyDeviceToHost, st),
+                    "chem_mlp_fit_ood extrema");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_ood sync");
+    if (rc) return rc;
+    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+    for (int b = 0; b < kOodBlocks; ++b)
+        for (int d = 0; d < 3; ++d) { lo[d] = std::fmin(lo[d], part[b * 6 + d]); hi[d] = std::fmax(hi[d], part[b * 6 + 3 + d]); }
+    float range[6];
+    for (int d = 0; d < 3; ++d) {
+        float w = hi[d] - lo[d];
+        if (!(w > 0.0f)) w = std::fmax(std::fabs(lo[d]) * 1e-3f, 1e-30f);
+        m->ood_lo[d] = lo[d] - 0.05f * w;                 // 5 % margin on both sides
+        m->ood_hi[d] = hi[d] + 0.05f * w;
+        range[d] = m->ood_lo[d];
+        range[3 + d] = (float)nbins / (m->ood_hi[d] - m->ood_lo[d]);
+    }
+    rc = check_cuda(cudaMemcpyAsync(m->ood_range_dev, range, sizeof(range), cudaMemcpyHostToDevice, st), "ood range");
+    if (!rc) rc = check_cuda(cudaMemsetAsync(m->ood_counts, 0, (size_t)nbins * nbins * nbins * 4, st), "ood reset");
+    if (rc) return rc;
+    ood_hist_kernel<<<kOodBlocks, 256, 0, st>>>(n, ld, T, Y, mech->dev.f32, m->N, Tmid, species, m->ood_range_dev,
+                                                nbins, m->ood_counts);
+    const int nbins3 = nbins * nbins * nbins;
+    ood_mask_kernel<<<(nbins3 + 255) / 256, 256, 0, st>>>(nbins, min_count, m->ood_counts, m->ood_mask);
+    rc = check_cuda(cudaGetLastError(), "chem_mlp_fit_ood");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_ood sync");
+    if (rc) return rc;
+    m->ood_nb = nbins;
+    m->ood_kmin = min_count;
+    m->ood_species = species;
+    m->ood_fitted = 1;
+    m->ood_enabled = 1;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_set_ood(chem_mlp *m, int enable) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_set_ood: null handle");
+    if (enable && !m->ood_fitted) return set_error(CHEM_EINVAL, "chem_mlp_set_ood: fit the grid first");
+    m->ood_enabled = enable ? 1 : 0;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_ood_flags(const chem_mlp *m, const chem_mech *mech, int64_t ncells, int64_t ld,
+                                  const double *T, const double *p, const double *Y, uint8_t *flags,
+                                  chem_stream_t stream) {
+    if (!m || !mech) return set_error(CHEM_EINVAL, "chem_mlp_ood_flags: null handle");
+    if (!m->ood_fitted) return set_error(CHEM_EINVAL, "chem_mlp_ood_flags: fit the grid first");
+    int rc = check_state_args(ncells, ld, T, p, Y, "chem_mlp_ood_flags");
+    if (rc) return rc;
+    if (ncells == 0) return CHEM_OK;
+    if (!flags) return set_error(CHEM_EINVAL, "chem_mlp_ood_flags: null flags");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ood_flags_kernel<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(ncells, ld, T, Y, mech->dev.f32, m->N,
+                                                                        (float)mech->T_mid, m->ood_species,
+                                                                        m->ood_range_dev, m->ood_nb, m->ood_mask, flags);
+    return check_cuda(cudaGetLastError(), "chem_mlp_ood_flags");
+}
+
+extern "C" int chem_mlp_get_ood(const chem_mlp *m, float *lo3, float *hi3, int32_t *nbins, int32_t *species,
+                                int32_t *min_count) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_ood: null handle");
+    if (!m->ood_fitted) return set_error(CHEM_EINVAL, "chem_mlp_get_ood: the grid is not fitted");
+    for (int d = 0; d < 3; ++d) { if (lo3) lo3[d] = m->ood_lo[d]; if (hi3) hi3[d] = m->ood_hi[d]; }
+    if (nbins) *nbins = m->ood_nb;
+    if (species) *species = m->ood_species;
+    if (min_count) *min_count = m->ood_kmin;
     return CHEM_OK;
 }
 

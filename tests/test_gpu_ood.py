@@ -1,0 +1,78 @@
+"""Out-of-distribution test and stiff fallback of the learned step on the GPU,
+against the oracle grid (FP64 features) and the GPU / oracle stiff integrator.
+
+The grid decision is an integer taken from FP32 features on the GPU and FP64
+features in the oracle: cells whose features sit on a bin edge may land in
+either bin, so the two sides must agree on >= 99.9 % of cells and on the
+recall / false-positive rates to within 0.2 %."""
+import numpy as np
+import pytest
+
+from oracle import ann as A
+from paper_2312_05800_gb300 import synth
+from tests.gpu_util import dev_mech, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(ntr=100000, ne=40000):
+    import torch
+    from paper_2312_05800_gb300 import binding
+    m = synth.mech_c2()
+    T, p, Y = synth.states_profiles(m, ntr, 2103)
+    Te, pe, Ye = synth.states_profiles(m, ne, 2003)
+    T2, Y2, moved = synth.perturb_off_manifold(Te, Ye, ne, 0.02, 2004)
+    net = binding.Mlp(dev_mech("c2"), hidden=(64, 64, 64), chunk=8192)
+    binding.chem_mlp_fit_ood(net, dev_mech("c2"), ntr, T.shape[0], to_dev(T), to_dev(p), to_dev(Y), m.roles["water"])
+    return m, net, (T, p, Y, ntr), (T2, pe, Y2, ne, moved)
+
+
+def test_grid_and_flags_match_oracle(oracle):
+    import torch
+    from paper_2312_05800_gb300 import binding
+    m, net, (T, p, Y, ntr), (T2, pe, Y2, ne, moved) = _setup()
+    lo, hi, nb, sp, km = binding.chem_mlp_get_ood(net)
+    F = A.ood_features(m, T[:ntr], p[:ntr], Y[:, :ntr], sp)
+    fit = A.ood_fit(F, nbins=nb, kmin=km)
+    assert np.allclose(lo, fit["lo"], rtol=1e-5, atol=1e-6 * np.abs(fit["hi"] - fit["lo"]))
+    assert np.allclose(hi, fit["hi"], rtol=1e-5, atol=1e-6 * np.abs(fit["hi"] - fit["lo"]))
+    flags = torch.zeros(T2.shape[0], dtype=torch.uint8, device="cuda")
+    binding.chem_mlp_ood_flags(net, dev_mech("c2"), ne, T2.shape[0], to_dev(T2), to_dev(pe), to_dev(Y2), flags)
+    torch.cuda.synchronize()
+    g = flags.cpu().numpy()[:ne].astype(bool)
+    o = A.ood_flags(fit, A.ood_features(m, T2[:ne], pe[:ne], Y2[:, :ne], sp))
+    assert np.mean(g == o) >= 0.999
+    mv = moved[:ne]
+    assert abs(g[mv].mean() - o[mv].mean()) <= 0.002 + 1.0 / mv.sum()
+    assert abs(g[~mv].mean() - o[~mv].mean()) <= 0.002
+    net.free()
+
+
+def test_fallback_cells_take_the_stiff_result(oracle):
+    import torch
+    from paper_2312_05800_gb300 import binding
+    m, net, _, (T2, pe, Y2, ne, moved) = _setup(ntr=60000, ne=6000)
+    ld = T2.shape[0]
+    flags = torch.zeros(ld, dtype=torch.uint8, device="cuda")
+    binding.chem_mlp_ood_flags(net, dev_mech("c2"), ne, ld, to_dev(T2), to_dev(pe), to_dev(Y2), flags)
+    opts = binding.make_opts(rtol=1e-6, atol_Y=1e-13, atol_T=1e-6, h0=1e-9, max_steps=20000)
+    Ta, pa, Ya = to_dev(T2), to_dev(pe), to_dev(Y2)
+    st = torch.full((ld,), -1, dtype=torch.int32, device="cuda")
+    binding.chem_step_ann(dev_mech("c2"), net, ne, ld, 1e-6, 0, opts, Ta, pa, Ya, st)
+    Ts, Ys = to_dev(T2), to_dev(Y2)
+    ss = torch.zeros(ld, dtype=torch.int32, device="cuda")
+    binding.chem_step_stiff(dev_mech("c2"), ne, ld, 1e-6, opts, Ts, pa, Ys, ss)
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy()[:ne].astype(bool)
+    s = st.cpu().numpy()[:ne]
+    assert f.sum() > 0 and np.array_equal(s == 1, f) and np.all(s[~f] == 0)
+    # fallback cells: exactly the stiff integrator's result (same kernel, same options)
+    Tg, Yg, Tr, Yr = Ta.cpu().numpy(), Ya.cpu().numpy(), Ts.cpu().numpy(), Ys.cpu().numpy()
+    assert np.array_equal(Tg[:ne][f], Tr[:ne][f]) and np.array_equal(Yg[:, :ne][:, f], Yr[:, :ne][:, f])
+    # and the oracle's stiff step on a few of them
+    idx = np.where(f)[0][:8]
+    import oracle as O
+    To, Yo, so, _ = O.step_stiff(m, T2[idx].copy(), pe[idx].copy(), Y2[:, idx].copy(), 1e-6, rtol=1e-6,
+                                 atol_Y=1e-13, atol_T=1e-6, max_steps=20000)
+    assert np.all(np.abs(Tg[idx] - To) <= 1e-4 * To)
+    net.free()
