@@ -353,7 +353,11 @@ def bench_ann(args, rank, world, local):
         hist = train.train(net, data, epochs=args.epochs, batch=4096, lr0=args.lr)
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
+        # out-of-distribution guard fitted on the training states; off-grid cells fall back to stiff
+        binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["water"])
         del data
+    fb_opts = binding.make_opts(**STIFF_OPTS)
+    tiles = binding.chem_mlp_autotune(net, 262144)
     # ---- inference workload
     ncells = args.cells
     T, p, Y = synth.states_profiles(smech, ncells, 2003 + 1000 * rank, ld=synth.padded_ld(ncells))
@@ -369,7 +373,7 @@ def bench_ann(args, rank, world, local):
     # ---- accuracy on held-out cells against a tight stiff integration
     ne = min(args.eval_cells, ncells) if not args.untrained else 4
     Ta, Ya = T0.clone(), Y0.clone()
-    binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_BF16, None, Ta, p0, Ya, status)
+    binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Ta, p0, Ya, status)
     Tr, Yr = T0.clone(), Y0.clone()
     binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**TIGHT_OPTS), Tr, p0, Yr, status)
     Ts, Ys = T0.clone(), Y0.clone()
@@ -380,11 +384,11 @@ def bench_ann(args, rank, world, local):
     acc_stiff = accuracy(smech, T, Y, Ts, Ys, Tr, Yr, ne)
     del Ta, Ya, Tr, Yr, Ts, Ys
 
-    def step():
+    def step(st=stream):
         Tw.copy_(T0)
         Yw.copy_(Y0)
-        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, None, Tw, p0, Yw, status, stream)
-        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, st)
+        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, st)
 
     for _ in range(args.warmup):
         step()
@@ -403,6 +407,26 @@ def bench_ann(args, rank, world, local):
         torch.cuda.synchronize()
     prof = binding.chem_prof_read()
     binding.chem_prof_enable(False)
+    n_fallback = int((status[:ncells] == binding.CELL_FALLBACK).sum().item())
+    n_failed = int((status[:ncells] >= 2).sum().item())
+    # the same step captured once as a CUDA graph and replayed
+    graph = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream(dev)
+    gs.wait_stream(stream)
+    with torch.cuda.stream(gs):
+        step(None)
+    gs.synchronize()
+    with torch.cuda.graph(graph):
+        step(None)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(args.steps):
+        graph.replay()
+    g1.record(stream)
+    torch.cuda.synchronize()
+    graph_ms = g0.elapsed_time(g1) / args.steps
+    del graph
     if world > 1:
         torch.distributed.barrier()
     total_s = ev[0].elapsed_time(ev[1]) / 1e3
@@ -428,6 +452,38 @@ def bench_ann(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     stiff_value = ns / (e0.elapsed_time(e1) / 1e3)
+    # ---- batched + fallback: the same cells with 2 % moved off the manifold (T +/- 300 K, Y noise 0.2)
+    T4, Y4, moved = synth.perturb_off_manifold(T, Y, ncells, 0.02, 2004 + 1000 * rank)
+    T4d, Y4d = torch.from_numpy(T4).to(dev), torch.from_numpy(Y4).to(dev)
+    Tw.copy_(T4d)
+    Yw.copy_(Y4d)
+    torch.cuda.synchronize()
+    binding.chem_prof_enable(True)
+    e0.record(stream)
+    binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, stream)
+    binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof4 = binding.chem_prof_read()
+    binding.chem_prof_enable(False)
+    st4 = status[:ncells].cpu().numpy()
+    mv = moved[:ncells]
+    flagged = st4 == binding.CELL_FALLBACK
+    c4_ms = e0.elapsed_time(e1)
+    ne4 = min(args.eval_cells, ncells)
+    Tr4, Yr4 = T4d.clone(), Y4d.clone()
+    binding.chem_step_stiff(dm, ne4, ld, DT, binding.make_opts(**TIGHT_OPTS), Tr4, p0, Yr4, status)
+    acc_c4 = accuracy(smech, T4, Y4, Tw.cpu().numpy(), Yw.cpu().numpy(), Tr4.cpu().numpy(), Yr4.cpu().numpy(), ne4)
+    batched = {"value": ncells / (c4_ms / 1e3), "unit": "cells/s", "ms_per_step": c4_ms,
+               "perturbed_cells": int(mv.sum()), "fallback_cells": int(flagged.sum()),
+               "recall": float(flagged[mv].mean()), "false_positive_rate": float(flagged[~mv].mean()),
+               "failed_cells": int((st4 >= 2).sum()),
+               "fallback_ms": sum(v[1] for k, v in prof4.items() if "fallback" in k),
+               "accuracy_vs_tight_stiff": acc_c4,
+               "workload": "the same 4,194,304 cells with a seeded 2 % moved off the manifold (T +/- 300 K, "
+                           "Y x exp(0.2 xi)); guard + stiff fallback (rtol 1e-3) in the step"}
+    del T4d, Y4d, Tr4, Yr4
+
     # ---- end to end through the C ABI with pinned host buffers
     Th, ph, Yh = torch.from_numpy(T).pin_memory(), torch.from_numpy(p).pin_memory(), torch.from_numpy(Y).pin_memory()
     Tout, Yout = torch.empty_like(Th).pin_memory(), torch.empty_like(Yh).pin_memory()
@@ -443,7 +499,7 @@ def bench_ann(args, rank, world, local):
         Tw.copy_(Th, non_blocking=True)
         p0.copy_(ph, non_blocking=True)
         Yw.copy_(Yh, non_blocking=True)
-        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, None, Tw, p0, Yw, status, stream)
+        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, stream)
         binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
         Tout.copy_(Tw, non_blocking=True)
         Yout.copy_(Yw, non_blocking=True)
@@ -460,7 +516,8 @@ def bench_ann(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "ANN chemistry + props: c2 stratified-profile cells, 30 species / 180 reactions, "
                                    "MLP 32-1600-800-400-29, dt 1 us",
-                       "path": "chem_step_ann (BF16 tcgen05 GEMMs, FP32 accumulation) + props_eval (FP32)",
+                       "path": "chem_step_ann (BF16 tcgen05 GEMMs, FP32 accumulation; out-of-distribution cells to "
+                               "the FP64 stiff integrator) + props_eval (FP32)",
                        "cells_per_gpu": ncells, "l2": "inputs larger than L2 (1 GB FP64 state)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_rtol1e-3_vs_tight_stiff": acc_stiff,
@@ -478,6 +535,12 @@ def bench_ann(args, rank, world, local):
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
                                        for k, v in gemm.items()}},
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "guard": {"ood": not args.untrained, "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
+                      "fallback_rtol": STIFF_OPTS["rtol"]},
+            "autotuned_tiles": tiles,
+            "graph": {"ms_per_step": graph_ms, "cells_per_s": world * ncells / (graph_ms / 1e3),
+                      "note": "the whole step captured once as a CUDA graph and replayed"},
+            "batched_fallback": batched,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks * 6 + 1),
             "clocks": clk.summary()}

@@ -258,6 +258,13 @@ int chem_mlp_forward(const chem_mlp *mlp, int64_t ncells, int64_t ld, const doub
  * the species against the mechanism and returns CHEM_EIO on a damaged file. */
 int chem_mlp_save(const chem_mlp *mlp, const char *path);
 int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
+/* Autotuner (no counterpart in the paper): for each layer, times every
+ * compiled output-tile width of the tensor-core GEMM on `rows` rows of the
+ * inference workspace (CUDA events, the first launch discarded) and keeps the
+ * fastest for chem_step_ann / chem_mlp_forward. tiles_out[4] (host, may be
+ * NULL) receives the choice. Synchronises the stream; results are bitwise
+ * the same for every tile width. */
+int chem_mlp_autotune(chem_mlp *mlp, int64_t rows, int32_t *tiles_out, chem_stream_t stream);
 /* Sticky error word of the network's pipeline waits (0 = none); synchronises the device. */
 int chem_mlp_error(const chem_mlp *mlp, int *host_err);
 

@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_set_ood.argtypes = [vp, i32]
     L.chem_mlp_ood_flags.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, vp]
     L.chem_mlp_get_ood.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.chem_mlp_autotune.argtypes = [vp, i64, vp, vp]
     L.chem_mlp_save.argtypes = [vp, ctypes.c_char_p]
     L.chem_mlp_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
     L.chem_step_ann.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp]
@@ -297,6 +298,13 @@ def chem_mlp_get_ood(mlp: Mlp):
     _check(lib().chem_mlp_get_ood(mlp.handle, lo.ctypes.data, hi.ctypes.data, ctypes.byref(nb), ctypes.byref(sp),
                                   ctypes.byref(km)))
     return lo, hi, nb.value, sp.value, km.value
+
+
+def chem_mlp_autotune(mlp: Mlp, rows: int = 262144, stream=None):
+    import numpy as np
+    t = np.zeros(4, np.int32)
+    _check(lib().chem_mlp_autotune(mlp.handle, rows, t.ctypes.data, _stream(stream)))
+    return [int(v) for v in t]
 
 
 def chem_mlp_fit_norm(mlp: Mlp, n: int, ld: int, T, p, Y, Y1, stream=None):

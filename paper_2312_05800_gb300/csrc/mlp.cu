@@ -25,6 +25,7 @@ namespace {
 constexpr int kLayers = 4;
 constexpr int kOodMaxBins = 64;
 constexpr int kOodBlocks = 512;
+constexpr int64_t kFallbackQueue = 8388608;   // cells queued for the stiff fallback before a flush
 constexpr float kLambdaBC = 0.1f;     // Box-Cox lambda (Sec. 3.2)
 constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
 
@@ -155,8 +156,9 @@ struct OodRoute {
     const float *range;      // null: no test
     const uint8_t *mask;
     int nb, species;
-    int32_t *queue;
+    int32_t *queue;          // absolute cell indices (the call's first cell is 0)
     unsigned int *count;
+    int64_t base;            // index of this chunk's first cell within the call
 };
 
 template <int NMAX>
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
         const int b = ood_bin(f, ood.range, ood.nb);
         if (b < 0 || ood.mask[b] == 0) {
             const unsigned int q = atomicAdd(ood.count, 1u);
-            ood.queue[q] = (int32_t)i;
+            ood.queue[q] = (int32_t)(ood.base + i);
             return;
         }
     }
@@ -649,7 +651,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->ood_counts, (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins * 4});
     parts.push_back({(void **)&m->ood_mask, (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins});
     parts.push_back({(void **)&m->ood_range_dev, 64});
-    parts.push_back({(void **)&m->fb_queue, (size_t)C * 4});
+    parts.push_back({(void **)&m->fb_queue, (size_t)(C > kFallbackQueue ? C : kFallbackQueue) * 4});
     parts.push_back({(void **)&m->fb_count, 64});
     parts.push_back({(void **)&m->fb_status, (size_t)C * 4});
     parts.push_back({(void **)&m->ood_part, (size_t)kOodBlocks * 6 * 4});
@@ -815,16 +817,43 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
     std::string why;
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_step_ann: " + why);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (m->ood_enabled && !status && ncells > m->chunk)
+        return set_error(CHEM_EINVAL, "chem_step_ann: with the out-of-distribution guard, calls of more than one "
+                                      "chunk need a status array");
+    const int64_t qcap = m->chunk > kFallbackQueue ? m->chunk : kFallbackQueue;
+    chem_ode_opts fo;
+    chem_ode_opts_default(&fo);
+    if (fallback) fo = *fallback;
+    int64_t queued = 0, flush_base = 0;     // cells of chunks routed since the last flush, first cell of them
+    // integrates every queued cell in one launch (cells are independent: one launch hides their latencies)
+    auto flush = [&](int64_t base) -> int {
+        if (!m->ood_enabled || queued == 0) return CHEM_OK;
+        int32_t *stq = status ? status + base : m->fb_status;
+        void *pf = prof_begin(st);
+        int r = launch_stiff_list(mech, queued, ld, dt, fo, T + base, p + base, Y + base, stq, m->fb_queue,
+                                  m->fb_count, CHEM_CELL_FALLBACK, st);
+        prof_end(pf, st, "stiff_kernel (fallback)", 0.0, 0.0);
+        queued = 0;
+        return r;
+    };
     for (int64_t c0 = 0; c0 < ncells; c0 += m->chunk) {
         const int64_t n = (ncells - c0 < m->chunk) ? ncells - c0 : m->chunk;
+        if (m->ood_enabled && queued + n > qcap) {
+            if ((rc = flush(flush_base))) return rc;
+        }
         rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
         if (rc) return rc;
-        OodRoute route{nullptr, nullptr, 0, 0, nullptr, nullptr};
+        OodRoute route{nullptr, nullptr, 0, 0, nullptr, nullptr, 0};
         int32_t *st_chunk = status ? status + c0 : m->fb_status;
         if (m->ood_enabled) {
-            route = OodRoute{m->ood_range_dev, m->ood_mask, m->ood_nb, m->ood_species, m->fb_queue, m->fb_count};
-            rc = check_cuda(cudaMemsetAsync(m->fb_count, 0, sizeof(unsigned int), st), "chem_step_ann: queue reset");
-            if (rc) return rc;
+            if (queued == 0) {
+                flush_base = c0;
+                rc = check_cuda(cudaMemsetAsync(m->fb_count, 0, sizeof(unsigned int), st), "chem_step_ann: queue reset");
+                if (rc) return rc;
+            }
+            route = OodRoute{m->ood_range_dev, m->ood_mask, m->ood_nb, m->ood_species, m->fb_queue, m->fb_count,
+                             c0 - flush_base};
+            queued += n;
         }
         void *pb = prof_begin(st);
         const unsigned eg = (unsigned)((n + 127) / 128);
@@ -843,18 +872,8 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
         prof_end(pb, st, "epilogue_kernel", 0.0, (double)n * (m->N * 16 + 16 + m->n_out_pad * 4));
         rc = check_cuda(cudaGetLastError(), "chem_step_ann epilogue");
         if (rc) return rc;
-        if (m->ood_enabled) {
-            chem_ode_opts o;
-            chem_ode_opts_default(&o);
-            if (fallback) o = *fallback;
-            void *pf = prof_begin(st);
-            rc = launch_stiff_list(mech, n, ld, dt, o, T + c0, p + c0, Y + c0, st_chunk, m->fb_queue, m->fb_count,
-                                   CHEM_CELL_FALLBACK, st);
-            prof_end(pf, st, "stiff_kernel (fallback)", 0.0, 0.0);
-            if (rc) return rc;
-        }
     }
-    return CHEM_OK;
+    return flush(flush_base);
 }
 
 extern "C" int chem_mlp_fit_ood(chem_mlp *m, const chem_mech *mech, int64_t n, int64_t ld, const double *T,
@@ -1152,4 +1171,56 @@ extern "C" int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp *
     m->adam_t = adam_t;
     *out = m;
     return CHEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: the fastest compiled tile width per layer, timed on the inference
+// workspace with CUDA events (the operands' values do not change the work)
+// ---------------------------------------------------------------------------
+extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_autotune: null handle");
+    if (rows < 128) rows = 128;
+    if (rows > m->chunk) rows = m->chunk;
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_autotune: " + why);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t e0, e1;
+    int rc = check_cuda(cudaEventCreate(&e0), "autotune event");
+    if (rc) return rc;
+    rc = check_cuda(cudaEventCreate(&e1), "autotune event");
+    if (rc) { cudaEventDestroy(e0); return rc; }
+    for (int l = 0; l < kLayers && !rc; ++l) {
+        Layer &L = m->L[l];
+        const __nv_bfloat16 *x = (l == 0) ? m->a0 : m->h[l - 1];
+        const int64_t ldx = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
+        float best = 3.4e38f;
+        int best_bn = L.tile;
+        for (int bn : kTileWidths) {
+            if (bn < 64 && L.out > 64) continue;
+            if (bn > 2 * ((L.out + 15) / 16) * 16 && bn > 64) continue;   // tiles far wider than the layer
+            float ms_sum = 0.0f;
+            for (int rep = 0; rep < 4 && !rc; ++rep) {
+                rc = check_cuda(cudaEventRecord(e0, st), "autotune record");
+                if (rc) break;
+                if (l < 3)
+                    rc = gemm_gelu(bn, x, ldx, L.Wb, L.kin, (int)rows, L.out, L.kin, L.b, m->h[l], L.out, nullptr, 0,
+                                   m->err, st);
+                else
+                    rc = gemm_linear(bn, x, ldx, L.Wb, L.kin, (int)rows, L.out, L.kin, L.b, m->out, m->n_out_pad,
+                                     m->err, st);
+                if (rc) break;
+                rc = check_cuda(cudaEventRecord(e1, st), "autotune record");
+                if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "autotune sync");
+                float ms = 0.0f;
+                if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_sum += ms;                               // the first launch warms up
+            }
+            if (!rc && ms_sum < best) { best = ms_sum; best_bn = bn; }
+        }
+        L.tile = best_bn;
+        if (tiles_out) tiles_out[l] = best_bn;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
