@@ -354,7 +354,8 @@ def bench_ann(args, rank, world, local):
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         # out-of-distribution guard fitted on the training states; off-grid cells fall back to stiff
-        binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["water"])
+        binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["water"], 64,
+                                 args.ood_kmin)
         del data
     fb_opts = binding.make_opts(**STIFF_OPTS)
     tiles = binding.chem_mlp_autotune(net, 262144)
@@ -535,7 +536,8 @@ def bench_ann(args, rank, world, local):
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
                                        for k, v in gemm.items()}},
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-            "guard": {"ood": not args.untrained, "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
+            "guard": {"ood": not args.untrained, "grid": "64^3 over (T, h/R, Y_water), neighbourhood >= %d"
+                      % args.ood_kmin, "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
                       "fallback_rtol": STIFF_OPTS["rtol"]},
             "autotuned_tiles": tiles,
             "graph": {"ms_per_step": graph_ms, "cells_per_s": world * ncells / (graph_ms / 1e3),
@@ -586,6 +588,8 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-cells", type=int, default=32768)
     ap.add_argument("--stiff-sample", type=int, default=262144)
+    ap.add_argument("--ood-kmin", type=int, default=2,
+                    help="training states the 3x3x3 neighbourhood of a cell's bin must hold for the network")
     ap.add_argument("--untrained", action="store_true",
                     help="profiling captures only: skip training and the accuracy check (kernel times do not "
                          "depend on the weights)")

@@ -177,6 +177,32 @@ extern "C" int chem_mech_load_bytes(const void *data, size_t nbytes, chem_mech *
     }
     int Np = (N + 3) & ~3;
 
+    // Device order of the reactions: Troe fall-off first, then three-body, then
+    // elementary (stable within each type). Lanes of a warp take consecutive
+    // reactions, so the long fall-off and third-body code paths then occupy
+    // few warp iterations; sums over reactions only change their order.
+    {
+        std::vector<int> order;
+        for (int t : {2, 1, 0})
+            for (int j = 0; j < R; ++j)
+                if (rtype[j] == t) order.push_back(j);
+        auto perm_d = [&](std::vector<double> &v, int w) {
+            std::vector<double> o(v.size());
+            for (int j = 0; j < R; ++j)
+                for (int i = 0; i < w; ++i) o[(size_t)j * w + i] = v[(size_t)order[j] * w + i];
+            v.swap(o);
+        };
+        auto perm_i = [&](std::vector<int32_t> &v, int w) {
+            std::vector<int32_t> o(v.size());
+            for (int j = 0; j < R; ++j)
+                for (int i = 0; i < w; ++i) o[(size_t)j * w + i] = v[(size_t)order[j] * w + i];
+            v.swap(o);
+        };
+        perm_i(rtype, 1); perm_i(reac, 3); perm_i(prod, 3);
+        perm_d(A, 1); perm_d(beta, 1); perm_d(Ea, 1); perm_d(A0, 1); perm_d(beta0, 1); perm_d(Ea0, 1);
+        perm_d(troe, 4); perm_d(eff, N);
+    }
+
     BlobBuilder bb;
     auto o32 = add_prop_tables<float>(bb, N, Np, W, lo, hi, visc, diff);
     auto o64 = add_prop_tables<double>(bb, N, Np, W, lo, hi, visc, diff);
