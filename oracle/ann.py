@@ -25,41 +25,105 @@ def to_bf16(x):
     return b.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+# FP8 E4M3 (the "fn" variant: 4 exponent bits, bias 7, 3 mantissa bits, no
+# infinities, one NaN pattern per sign): finite values are 0, m 2^-9 (m = 1..7,
+# subnormal) and (1 + m/8) 2^e (e = -6..8, m = 0..7, except m = 7 at e = 8),
+# the largest 448.
+E4M3_MAX = 448.0
+
+
+def e4m3_decode(codes):
+    """Values of E4M3 codes (uint8) from the format definition; NaN for 0x7f / 0xff."""
+    c = np.asarray(codes, np.int64)
+    sign = np.where(c & 0x80, -1.0, 1.0)
+    e = (c >> 3) & 0xF
+    m = c & 0x7
+    mag = np.where(e == 0, m * 2.0 ** -9, (1.0 + m / 8.0) * 2.0 ** (e - 7.0))
+    mag = np.where((e == 0xF) & (m == 7), np.nan, mag)
+    return sign * mag
+
+
+def to_e4m3(x):
+    """Round to the nearest E4M3 value, ties to even, saturating at +-448 (also for
+    infinities); NaN stays NaN. Returned as float64."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(np.where(np.isfinite(a) & (a > 0), a, 1.0))
+    e = np.maximum(ex.astype(np.float64) - 1.0, -6.0)   # floor(log2 a); below 2^-6 the spacing is 2^-9
+    q = 2.0 ** (e - 3.0)
+    r = np.rint(a / q) * q               # np.rint rounds halves to even; a / q is exact
+    r = np.minimum(r, E4M3_MAX)
+    r = np.where(np.isnan(x), np.nan, r)
+    return np.copysign(r, x)
+
+
+def quantize_rows(W):
+    """Per output row: sw = fl32(max |W| / 448) (1 for a zero row) and the E4M3
+    values of fl32(W / sw). W holds FP32 values."""
+    W = np.asarray(W, np.float64)
+    amax = np.abs(W).max(axis=1)
+    sw = np.where(amax > 0, (amax / E4M3_MAX).astype(np.float32).astype(np.float64), 1.0)
+    Wq = to_e4m3((W / sw[:, None]).astype(np.float32).astype(np.float64))
+    return Wq, sw
+
+
+def calibrate_fp8(layers, z):
+    """E4M3 activation scales s_i = fl32(max |h_i| / 448) of the BF16 forward's h1, h2."""
+    h = to_bf16(np.asarray(z, np.float64))
+    s = []
+    for W, b in layers[:2]:
+        h = to_bf16(M.gelu(h @ to_bf16(W).T + b))
+        s.append(float(np.float32(np.abs(h).max() / E4M3_MAX)))
+    return s
+
+
 def out_species(mech):
     return [k for k in range(mech.N) if k != mech.bath]
 
 
-def network(layers, z, round_bf16=False):
+def network(layers, z, round_bf16=False, fp8_scales=None):
+    """The MLP on normalised inputs z [n, n_in]. round_bf16: BF16 operands as
+    stored by the device. fp8_scales = (s_1, s_2): additionally the two
+    hidden-to-hidden layers take E4M3 operands, h_q = E4M3(h / s) and the weights
+    of quantize_rows, with z = (h_q . Wq) fl32(sw s) + b (accumulation exact)."""
     h = np.asarray(z, np.float64)
-    if round_bf16:
+    if round_bf16 or fp8_scales is not None:
         h = to_bf16(h)
+    nl = len(layers)
     for i, (W, b) in enumerate(layers):
-        Wq = to_bf16(W) if round_bf16 else W
-        pre = h @ Wq.T + b
-        if i < len(layers) - 1:
+        if fp8_scales is not None and i in (1, 2):
+            Wq, sw = quantize_rows(W)
+            cs = (sw * np.float64(np.float32(fp8_scales[i - 1]))).astype(np.float32).astype(np.float64)
+            pre = (h @ Wq.T) * cs + b
+        else:
+            Wq = to_bf16(W) if (round_bf16 or fp8_scales is not None) else W
+            pre = h @ Wq.T + b
+        if i < nl - 1:
             h = M.gelu(pre)
-            if round_bf16:
+            if fp8_scales is not None and i in (0, 1):
+                h = to_e4m3(h / np.float64(np.float32(fp8_scales[i])))
+            elif round_bf16 or fp8_scales is not None:
                 h = to_bf16(h)
         else:
             h = pre
     return h
 
 
-def forward_u(mech, layers, stats, T, p, Y, round_bf16=False):
+def forward_u(mech, layers, stats, T, p, Y, round_bf16=False, fp8_scales=None):
     mu_x, sd_x, mu_u, sd_u = stats
     x = M.features(T, p, Y)
     z = (x - mu_x) / sd_x
-    if round_bf16:
+    if round_bf16 or fp8_scales is not None:
         # the device forms z in FP32
         z = np.asarray(z, np.float32).astype(np.float64)
-    return network(layers, z, round_bf16)
+    return network(layers, z, round_bf16, fp8_scales)
 
 
-def step_ann(mech, layers, stats, T, p, Y, round_bf16=False):
+def step_ann(mech, layers, stats, T, p, Y, round_bf16=False, fp8_scales=None):
     """Returns (T', Y') for SoA inputs T[n], p[n], Y[N, n]."""
     import oracle as O
     mu_x, sd_x, mu_u, sd_u = stats
-    u = forward_u(mech, layers, stats, T, p, Y, round_bf16)
+    u = forward_u(mech, layers, stats, T, p, Y, round_bf16, fp8_scales)
     dY = u * sd_u + mu_u
     Yn = np.array(Y, dtype=np.float64)
     sp = out_species(mech)
