@@ -45,7 +45,10 @@ NCELLS_ANN = 4194304
 DT = 1.0e-6
 TIGHT_OPTS = dict(rtol=1e-6, atol_Y=1e-13, atol_T=1e-6, h0=1e-9, max_steps=20000)
 STIFF_OPTS = dict(rtol=1e-3, atol_Y=1e-9, atol_T=1e-3, h0=1e-9, max_steps=10000)
+PARITY_OPTS = dict(rtol=1e-9, atol_Y=1e-15, atol_T=1e-9, h0=1e-9, max_steps=10000)
 MECH = "c2"
+HIDDEN = {"c2": (1600, 800, 400), "c5": (2048, 1024, 512)}
+CELLS = {("ann", "c2"): NCELLS_ANN, ("stiff", "c2"): NCELLS, ("ann", "c5"): 16777216, ("stiff", "c5"): 1048576}
 SEED = 2002
 METRIC = "chem+props cells/s at stated dY/T error: ANN (BF16/FP8) vs stiff integrator, 1 GB300"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
@@ -120,6 +123,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def stiff_workload(mech) -> str:
+    return "%s stratified-profile cells, %d species / %d reactions, dt 1 us" % (MECH, mech.N, mech.R)
+
+
+def ann_workload(mech) -> str:
+    widths = [mech.N + 2, *HIDDEN[MECH], mech.N - 1]
+    return "ANN chemistry + props: %s, MLP %s" % (stiff_workload(mech), "-".join(str(w) for w in widths))
+
+
 def make_inputs(rank: int, ncells: int = NCELLS):
     from paper_2312_05800_gb300 import synth
     mech = synth.get_mech(MECH)
@@ -161,8 +173,7 @@ def run_reference(args):
             cpu_baseline_ann(smech, T, p, Y, sample)
         vals = [cpu_baseline_ann(smech, T, p, Y, sample)["value"] for _ in range(args.steps)]
         v = statistics.median(vals)
-        cfg = {"workload": "ANN chemistry + props: c2 stratified-profile cells, 30 species / 180 reactions, "
-                           "MLP 32-1600-800-400-29, dt 1 us", "path": "oracle ANN step (FP64) + props",
+        cfg = {"workload": ann_workload(smech), "path": "oracle ANN step (FP64) + props",
                "cells_per_step": sample}
         desc = "first %d cells per step: oracle ANN step (FP64) + props" % sample
     else:
@@ -171,8 +182,7 @@ def run_reference(args):
         for _ in range(args.warmup):
             run_cpu_oracle(mech, T, p, Y, sample)
         v = sample / statistics.median([run_cpu_oracle(mech, T, p, Y, sample) for _ in range(args.steps)])
-        cfg = {"workload": "c2 stratified-profile cells, 30 species / 180 reactions, dt 1 us",
-               "path": "oracle stiff+props", "cells_per_step": sample, "rtol": STIFF_OPTS["rtol"]}
+        cfg = {"workload": stiff_workload(mech), "path": "oracle stiff+props", "cells_per_step": sample, "rtol": STIFF_OPTS["rtol"]}
         desc = "first %d cells per step: oracle stiff + props at rtol %g" % (sample, STIFF_OPTS["rtol"])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "cells/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample / v,
@@ -278,6 +288,20 @@ def bench_stiff(args, rank, world, local):
     e2e_s = e0.elapsed_time(e1) / 1e3
     e2e_value = world * NCELLS * e2e_steps / e2e_s
 
+    # the integrator at the parity setting (rtol 1e-9) on a sample of the same cells
+    nt = min(16384, NCELLS)
+    Tw.copy_(T0)
+    Yw.copy_(Y0)
+    e0.record(stream)
+    binding.chem_step_stiff(dm, nt, NCELLS, DT, binding.make_opts(**PARITY_OPTS), Tw, p0, Yw, status, nsteps, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tight = {"value": nt / (e0.elapsed_time(e1) / 1e3), "unit": "cells/s", "rtol": PARITY_OPTS["rtol"],
+             "sample": "first %d cells, stiff only" % nt,
+             "mean_steps_per_cell": float(nsteps[:nt].double().mean().item()),
+             "failed_cells": int((status[:nt] != 0).sum().item())}
+    dgemm = measure_dgemm_tflops(dev)
+
     flops_step = stiff_flops_per_step(N, mech.R, int((mech.rtype != 0).sum()), int((mech.rtype == 2).sum()))
     kern_s = statistics.mean(kern_ms) / 1e3
     achieved = steps_total * flops_step / kern_s / 1e12
@@ -285,14 +309,16 @@ def bench_stiff(args, rank, world, local):
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "c2 stratified-profile cells, 30 species / 180 reactions, dt 1 us",
+            "config": {"workload": stiff_workload(mech),
                        "path": "stiff+props (FP64 Rodas3 rtol 1e-3, FP32 props)", "cells_per_gpu": NCELLS,
                        "l2": "inputs larger than L2 (0.5 GB FP64 state)",
                        "mean_steps_per_cell": steps_total / NCELLS, "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                          "kernel": "stiff_kernel", "flops_per_step": flops_step,
-                         "peak_source": "FP64 nominal: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz"},
+                         "peak_source": "FP64 nominal: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz",
+                         "dgemm_tflops_measured": dgemm},
+            "stiff_parity_setting": tight,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks}
@@ -306,6 +332,22 @@ def bench_stiff(args, rank, world, local):
     return line
 
 
+
+
+def measure_dgemm_tflops(dev) -> float:
+    """FP64 throughput of cuBLAS DGEMM (4096^3, CUDA events): a measured ceiling for FP64 arithmetic."""
+    import torch
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    b = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        torch.matmul(a, b)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        torch.matmul(a, b)
+    e1.record()
+    torch.cuda.synchronize()
+    return 5 * 2.0 * 4096 ** 3 / (e0.elapsed_time(e1) / 1e3) / 1e12
 
 
 def measured_peak(key: str, fallback: float):
@@ -339,8 +381,10 @@ def bench_ann(args, rank, world, local):
     smech = synth.get_mech(MECH)
     dm = binding.Mech(smech)
     N = smech.N
+    hidden = HIDDEN[MECH]
     # ---- training (untimed): GPU stiff pairs, statistics, Adam on Eq. 5
-    net = binding.Mlp(dm, hidden=(1600, 800, 400), dt=DT, seed=3003, chunk=262144, max_batch=4096)
+    net = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3003, chunk=262144, max_batch=4096)
+    fp8 = not args.untrained and not args.no_fp8
     if args.untrained:
         t_data = t_train = 0.0
         hist = [float("nan")]
@@ -356,6 +400,9 @@ def bench_ann(args, rank, world, local):
         # out-of-distribution guard fitted on the training states; off-grid cells fall back to stiff
         binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["water"], 64,
                                  args.ood_kmin)
+        if fp8:
+            # E4M3 activation scales from the BF16 forward of training states
+            binding.chem_mlp_calibrate_fp8(net, min(data.n, 262144), data.ld, data.T, data.p, data.Y)
         del data
     fb_opts = binding.make_opts(**STIFF_OPTS)
     tiles = binding.chem_mlp_autotune(net, 262144)
@@ -379,16 +426,20 @@ def bench_ann(args, rank, world, local):
     binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**TIGHT_OPTS), Tr, p0, Yr, status)
     Ts, Ys = T0.clone(), Y0.clone()
     binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**STIFF_OPTS), Ts, p0, Ys, status)
+    T8, Y8 = T0.clone(), Y0.clone()
+    if fp8:
+        binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_FP8, fb_opts, T8, p0, Y8, status)
     torch.cuda.synchronize()
-    Ta, Ya, Tr, Yr, Ts, Ys = [x.cpu().numpy() for x in (Ta, Ya, Tr, Yr, Ts, Ys)]
+    Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8 = [x.cpu().numpy() for x in (Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8)]
     acc_ann = accuracy(smech, T, Y, Ta, Ya, Tr, Yr, ne)
     acc_stiff = accuracy(smech, T, Y, Ts, Ys, Tr, Yr, ne)
-    del Ta, Ya, Tr, Yr, Ts, Ys
+    acc_fp8 = accuracy(smech, T, Y, T8, Y8, Tr, Yr, ne) if fp8 else None
+    del Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8
 
-    def step(st=stream):
+    def step(st=stream, prec=binding.CHEM_PREC_BF16):
         Tw.copy_(T0)
         Yw.copy_(Y0)
-        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, st)
+        binding.chem_step_ann(dm, net, ncells, ld, DT, prec, fb_opts, Tw, p0, Yw, status, st)
         binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, st)
 
     for _ in range(args.warmup):
@@ -428,6 +479,35 @@ def bench_ann(args, rank, world, local):
     torch.cuda.synchronize()
     graph_ms = g0.elapsed_time(g1) / args.steps
     del graph
+    # ---- the same step with the hidden-to-hidden layers on E4M3 operands
+    fp8_line = None
+    if fp8:
+        for _ in range(args.warmup):
+            step(prec=binding.CHEM_PREC_FP8)
+        torch.cuda.synchronize()
+        binding.chem_prof_enable(True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            step(prec=binding.CHEM_PREC_FP8)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        prof8 = binding.chem_prof_read()
+        binding.chem_prof_enable(False)
+        f8_ms = g0.elapsed_time(g1) / args.steps
+        g8 = {k: v for k, v in prof8.items() if k.startswith("gemm_tn_kernel")}
+        e8 = {k: v for k, v in g8.items() if "e4m3" in k}
+        e8_ms, e8_fl = sum(v[1] for v in e8.values()), sum(v[2] for v in e8.values())
+        peak8 = measured_peak("bf16_tflops", 1900.0)[0] * 2.0
+        fp8_line = {"value": world * ncells / (f8_ms / 1e3), "unit": "cells/s", "ms_per_step": f8_ms,
+                    "accuracy_vs_tight_stiff": acc_fp8, "act_scales": [float(v) for v in
+                                                                      binding.chem_mlp_get_fp8_scales(net)],
+                    "e4m3_gemm_roofline": {"bound": "tensor", "achieved": e8_fl / (e8_ms / 1e3) / 1e12 if e8_ms else None,
+                                           "peak": peak8, "unit": "TFLOP/s",
+                                           "frac": (e8_fl / (e8_ms / 1e3) / 1e12 / peak8) if e8_ms else None,
+                                           "peak_source": "measured BF16 x 2 (the nominal FP8 / BF16 ratio)"},
+                    "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof8.items()},
+                    "layers": "h1 -> h2 and h2 -> h3 on E4M3 operands (per-row weight scales, per-tensor "
+                              "activation scales), first and output layers BF16"}
     if world > 1:
         torch.distributed.barrier()
     total_s = ev[0].elapsed_time(ev[1]) / 1e3
@@ -481,8 +561,8 @@ def bench_ann(args, rank, world, local):
                "failed_cells": int((st4 >= 2).sum()),
                "fallback_ms": sum(v[1] for k, v in prof4.items() if "fallback" in k),
                "accuracy_vs_tight_stiff": acc_c4,
-               "workload": "the same 4,194,304 cells with a seeded 2 % moved off the manifold (T +/- 300 K, "
-                           "Y x exp(0.2 xi)); guard + stiff fallback (rtol 1e-3) in the step"}
+               "workload": "the same %d cells with a seeded 2 %% moved off the manifold (T +/- 300 K, "
+                           "Y x exp(0.2 xi)); guard + stiff fallback (rtol 1e-3) in the step" % ncells}
     del T4d, Y4d, Tr4, Yr4
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -515,8 +595,7 @@ def bench_ann(args, rank, world, local):
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "ANN chemistry + props: c2 stratified-profile cells, 30 species / 180 reactions, "
-                                   "MLP 32-1600-800-400-29, dt 1 us",
+            "config": {"workload": ann_workload(smech),
                        "path": "chem_step_ann (BF16 tcgen05 GEMMs, FP32 accumulation; out-of-distribution cells to "
                                "the FP64 stiff integrator) + props_eval (FP32)",
                        "cells_per_gpu": ncells, "l2": "inputs larger than L2 (1 GB FP64 state)",
@@ -543,6 +622,7 @@ def bench_ann(args, rank, world, local):
             "graph": {"ms_per_step": graph_ms, "cells_per_s": world * ncells / (graph_ms / 1e3),
                       "note": "the whole step captured once as a CUDA graph and replayed"},
             "batched_fallback": batched,
+            "fp8": fp8_line,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks * 6 + 1),
             "clocks": clk.summary()}
@@ -558,7 +638,7 @@ def cpu_baseline_ann(smech, T, p, Y, sample=4096):
     from oracle import mlp as M
     from paper_2312_05800_gb300 import synth
     O.build()
-    widths = [smech.N + 2, 1600, 800, 400, smech.N - 1]
+    widths = [smech.N + 2, *HIDDEN[MECH], smech.N - 1]
     layers = synth.mlp_layers(widths, 3003)
     x = M.features(T[:sample], p[:sample], Y[:, :sample])
     mu_x, sd_x = M.zscore_stats(x)
@@ -572,13 +652,16 @@ def cpu_baseline_ann(smech, T, p, Y, sample=4096):
 
 
 def main():
-    global NCELLS
+    global NCELLS, MECH
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="ann", choices=["ann", "stiff"])
+    ap.add_argument("--mech", default=MECH, choices=sorted(HIDDEN),
+                    help="mechanism (c2: 30 species, MLP 1600/800/400; c5: 53 species, MLP 2048/1024/512)")
+    ap.add_argument("--no-fp8", action="store_true", help="skip the E4M3 variant of the learned step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=None,
                     help="cells per GPU (default 4,194,304 for ann, 2,097,152 for stiff); smaller values only for "
@@ -594,12 +677,13 @@ def main():
                     help="profiling captures only: skip training and the accuracy check (kernel times do not "
                          "depend on the weights)")
     args = ap.parse_args()
+    MECH = args.mech
     if args.impl == "reference":
         run_reference(args)
         return
     import torch
     if args.cells is None:
-        args.cells = NCELLS_ANN if args.path == "ann" else NCELLS
+        args.cells = CELLS[(args.path, MECH)]
     NCELLS = args.cells
     if NCELLS % 4:
         raise SystemExit("--cells must be a multiple of 4")

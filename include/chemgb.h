@@ -252,6 +252,37 @@ int chem_mlp_fit_norm(chem_mlp *mlp, int64_t n, int64_t ld, const double *T, con
 /* Normalised network outputs u [ncells][ldu] (float, device) for SoA states. */
 int chem_mlp_forward(const chem_mlp *mlp, int64_t ncells, int64_t ld, const double *T, const double *p,
                      const double *Y, float *u, int64_t ldu, chem_stream_t stream);
+/* The same at precision prec: CHEM_PREC_BF16 as chem_mlp_forward, or
+ * CHEM_PREC_FP8 (below). CHEM_EINVAL for FP8 without current E4M3 scales. */
+int chem_mlp_forward_prec(const chem_mlp *mlp, int prec, int64_t ncells, int64_t ld, const double *T,
+                          const double *p, const double *Y, float *u, int64_t ldu, chem_stream_t stream);
+
+/* Reduced-precision inference (no counterpart in the paper, which states no
+ * precision). With CHEM_PREC_FP8 the two hidden-to-hidden layers (h1 -> h2,
+ * h2 -> h3: about 94 % of the multiply-adds of a 1600/800/400 network) run on
+ * FP8-E4M3 operands with FP32 accumulation; the first layer (whose inputs are
+ * the state) and the output layer stay BF16. For hidden-to-hidden layer l:
+ *   sw_l[n]  = max_k |W_l[n][k]| / 448   (per output row; 1 for a zero row)
+ *   Wq_l     = E4M3(W_l[n][k] / sw_l[n]),  h_q = E4M3(h / s_h)
+ *   z_l[n]   = (sum_k h_q[k] Wq_l[n][k]) * (sw_l[n] * s_h) + b_l[n]
+ * with E4M3 rounding to nearest even, saturating at +-448, and s_h the
+ * per-tensor scale of the layer's input activation (s_1 for h1, s_2 for h2).
+ * The E4M3 weights are made from the FP32 parameters when scales are set and
+ * become stale (FP8 calls fail with CHEM_EINVAL) after set_params, set_norm,
+ * fit_norm or a training step; checkpoints do not hold them.
+ *
+ * chem_mlp_set_fp8_scales: act_scale[2] = {s_1, s_2} (host, positive, finite);
+ * quantises the weights; synchronises the device.
+ * chem_mlp_calibrate_fp8: s_i = max |h_i| / 448 over the BF16 forward of n
+ * cells (device SoA, e.g. the training states), then as set_fp8_scales.
+ * chem_mlp_get_fp8_scales: the current {s_1, s_2} (CHEM_EINVAL if none).
+ * chem_mlp_get_fp8_weights: layer 1 or 2; Wq [out][in] (host bytes, E4M3
+ * codes) and sw [out] (host floats). */
+int chem_mlp_set_fp8_scales(chem_mlp *mlp, const float *act_scale);
+int chem_mlp_calibrate_fp8(chem_mlp *mlp, int64_t n, int64_t ld, const double *T, const double *p, const double *Y,
+                           chem_stream_t stream);
+int chem_mlp_get_fp8_scales(const chem_mlp *mlp, float *act_scale);
+int chem_mlp_get_fp8_weights(const chem_mlp *mlp, int layer, uint8_t *Wq, float *sw);
 /* Checkpoint (host path): statistics, FP32 parameters, Adam moments and step
  * count, with a version header and an FNV-1a checksum. Training resumed from a
  * checkpoint continues bit for bit (training is deterministic). load checks
@@ -306,7 +337,8 @@ int chem_mlp_get_ood(const chem_mlp *mlp, float *lo3, float *hi3, int32_t *nbins
  * (adiabatic, constant pressure) by Newton iteration on the NASA-7 enthalpy.
  * T [ld], Y [N][ld] (double, device) are updated in place; p [ld] is read.
  * dt must equal the dt the network was created for (CHEM_EINVAL otherwise).
- * prec: CHEM_PREC_BF16. status [ld] (int32, device, may be NULL) receives
+ * prec: CHEM_PREC_BF16, or CHEM_PREC_FP8 after chem_mlp_calibrate_fp8 /
+ * chem_mlp_set_fp8_scales. status [ld] (int32, device, may be NULL) receives
  * CHEM_CELL_OK, or for cells outside the network's training distribution (when
  * the test of chem_mlp_fit_ood is enabled) the stiff fallback's code.
  * fallback: stiff options for those cells (NULL = defaults).

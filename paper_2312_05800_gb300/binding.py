@@ -77,6 +77,11 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_get_norm.argtypes = [vp, vp, vp, vp, vp]
     L.chem_mlp_fit_norm.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
     L.chem_mlp_forward.argtypes = [vp, i64, i64, vp, vp, vp, vp, i64, vp]
+    L.chem_mlp_forward_prec.argtypes = [vp, i32, i64, i64, vp, vp, vp, vp, i64, vp]
+    L.chem_mlp_set_fp8_scales.argtypes = [vp, vp]
+    L.chem_mlp_get_fp8_scales.argtypes = [vp, vp]
+    L.chem_mlp_calibrate_fp8.argtypes = [vp, i64, i64, vp, vp, vp, vp]
+    L.chem_mlp_get_fp8_weights.argtypes = [vp, i32, vp, vp]
     L.chem_mlp_error.argtypes = [vp, vp]
     L.chem_mlp_fit_ood.argtypes = [vp, vp, i64, i64, vp, vp, vp, i32, i32, i32, vp]
     L.chem_mlp_set_ood.argtypes = [vp, i32]
@@ -313,6 +318,39 @@ def chem_mlp_fit_norm(mlp: Mlp, n: int, ld: int, T, p, Y, Y1, stream=None):
 
 def chem_mlp_forward(mlp: Mlp, ncells: int, ld: int, T, p, Y, u, ldu: int, stream=None):
     _check(lib().chem_mlp_forward(mlp.handle, ncells, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(u), ldu, _stream(stream)))
+
+
+def chem_mlp_forward_prec(mlp: Mlp, prec: int, ncells: int, ld: int, T, p, Y, u, ldu: int, stream=None):
+    _check(lib().chem_mlp_forward_prec(mlp.handle, prec, ncells, ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(u), ldu,
+                                       _stream(stream)))
+
+
+def chem_mlp_set_fp8_scales(mlp: Mlp, scales):
+    import numpy as np
+    a = np.ascontiguousarray(scales, dtype=np.float32)
+    assert a.size == 2
+    _check(lib().chem_mlp_set_fp8_scales(mlp.handle, a.ctypes.data))
+
+
+def chem_mlp_get_fp8_scales(mlp: Mlp):
+    import numpy as np
+    a = np.zeros(2, np.float32)
+    _check(lib().chem_mlp_get_fp8_scales(mlp.handle, a.ctypes.data))
+    return a
+
+
+def chem_mlp_calibrate_fp8(mlp: Mlp, n: int, ld: int, T, p, Y, stream=None):
+    _check(lib().chem_mlp_calibrate_fp8(mlp.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), _stream(stream)))
+
+
+def chem_mlp_get_fp8_weights(mlp: Mlp, layer: int):
+    """(Wq [out][in] uint8 E4M3 codes, sw [out] float32) of hidden-to-hidden layer 1 or 2."""
+    import numpy as np
+    fo, fi = mlp.widths[layer + 1], mlp.widths[layer]
+    Wq = np.zeros((fo, fi), np.uint8)
+    sw = np.zeros(fo, np.float32)
+    _check(lib().chem_mlp_get_fp8_weights(mlp.handle, layer, Wq.ctypes.data, sw.ctypes.data))
+    return Wq, sw
 
 
 def chem_step_ann(mech: Mech, mlp: Mlp, ncells: int, ld: int, dt: float, prec: int, fallback, T, p, Y, status=None,

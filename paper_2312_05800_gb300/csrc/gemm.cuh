@@ -1,25 +1,29 @@
-// gemm.cuh -- persistent, warp-specialised BF16 GEMM on the 5th-generation
-// tensor cores: Y[M][N] = epilogue(X[M][K] * W[N][K]^T), FP32 accumulation.
-// This is the dense contraction of every MLP layer (Sec. 3.2: hidden layers of
-// 1600, 800 and 400 GELU units), forward and backward.
+// gemm.cuh -- persistent, warp-specialised GEMM on the 5th-generation tensor
+// cores: Y[M][N] = epilogue(X[M][K] * W[N][K]^T), FP32 accumulation, BF16 or
+// FP8-E4M3 operands (the epilogue type says which). This is the dense
+// contraction of every MLP layer (Sec. 3.2: hidden layers of 1600, 800 and 400
+// GELU units), forward and backward.
 //
 // Roles (576 threads per CTA, one CTA per SM, static round-robin over tiles):
-//   warp 0      TMA producer: 128 x 64 tile of X and BN x 64 tile of W per
-//               k-block into a STAGES-deep ring (128-byte swizzle).
+//   warp 0      TMA producer: 128-row tile of X and BN-row tile of W, 128 bytes
+//               of K per row (64 BF16 or 128 E4M3), per k-block into a
+//               STAGES-deep ring (128-byte swizzle).
 //   warp 1      TMEM allocation and the single MMA-issuing thread:
-//               tcgen05.mma kind::f16, M = 128, N = BN, K = 16 per instruction,
+//               tcgen05.mma kind::f16 (K = 16) or kind::f8f6f4 (K = 32),
+//               M = 128, N = BN, four instructions per k-block,
 //               accumulating in one of two TMEM buffers (columns 0 and 256).
 //   warps 2..17 epilogue: four warps per TMEM lane quadrant (warp w reads TMEM
 //               lanes 32 (w % 4) .. +31, i.e. output rows) split the 16-column
-//               chunks between them; tcgen05.ld, then the functor. BF16 GELU
-//               outputs are staged per warp in shared memory (double buffered)
-//               and written by TMA tensor stores.
+//               chunks between them; tcgen05.ld, then the functor. BF16 or
+//               E4M3 GELU outputs are staged per warp in shared memory (double
+//               buffered) and written by TMA tensor stores.
 // Ragged M, N and K: TMA fills out-of-range operand elements with zeros, TMA
 // stores clip at the tensor bounds, and direct stores mask rows >= M and
 // columns >= N.
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "tc.cuh"
 
@@ -29,7 +33,8 @@ constexpr int kEpiWarps = 16;
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kStageBytesPerWarp = 32 * 16 * 2;   // one 32 x 16 BF16 chunk
 constexpr int kBM = 128;
-constexpr int kBK = 64;
+constexpr int kBK = 64;                     // BF16 elements per k-block row (128 bytes)
+constexpr int kBK8 = 128;                   // E4M3 elements per k-block row (128 bytes)
 constexpr uint32_t kTmemCols = 512;
 
 template <int BN, int STAGES>
@@ -84,6 +89,8 @@ __device__ __forceinline__ float gelu_grad(float z) {
 // Y = bf16(GELU(acc + b)); optionally also the FP32 pre-activation acc + b.
 // Without a pre-activation the kernel stages the BF16 chunk and stores it by TMA.
 struct EpiGelu {
+    static constexpr bool kF8 = false;       // operand type: BF16
+    static constexpr int kOutBytes = 32;     // bytes of a 16-column output chunk row (TMA store)
     int M, N;
     const float *bias;
     __nv_bfloat16 *out;
@@ -96,6 +103,7 @@ struct EpiGelu {
     __host__ __device__ __forceinline__ bool tma_store() const {
         return pre == nullptr && (N & 15) == 0 && bias != nullptr && (reinterpret_cast<uintptr_t>(bias) & 15) == 0;
     }
+    const void *tma_ptr() const { return tma_store() ? out : nullptr; }
     // the 16 BF16 values of (row, col0..col0+15), two per 32-bit word (N % 8 == 0 on this path,
     // and the bias is padded to whole 16-float groups)
     __device__ __forceinline__ void compute(int col0, const float (&v)[16], uint32_t (&w)[8]) const {
@@ -146,11 +154,14 @@ struct EpiGelu {
 
 // Y = acc + b in FP32 (b may be null).
 struct EpiLinear {
+    static constexpr bool kF8 = false;
+    static constexpr int kOutBytes = 32;
     int M, N;
     const float *bias;
     float *out;
     int64_t ldo;
-    __device__ __forceinline__ bool tma_store() const { return false; }
+    __host__ __device__ __forceinline__ bool tma_store() const { return false; }
+    const void *tma_ptr() const { return nullptr; }
     __device__ __forceinline__ void compute(int, const float (&)[16], uint32_t (&)[8]) const {}
     __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
         if (row >= M) return;
@@ -175,12 +186,15 @@ struct EpiLinear {
 
 // Y = bf16(acc * GELU'(Z)), Z the FP32 pre-activation of the layer below (backward pass).
 struct EpiGeluGrad {
+    static constexpr bool kF8 = false;
+    static constexpr int kOutBytes = 32;
     int M, N;
     const float *z;
     int64_t ldz;
     __nv_bfloat16 *out;
     int64_t ldo;
-    __device__ __forceinline__ bool tma_store() const { return false; }
+    __host__ __device__ __forceinline__ bool tma_store() const { return false; }
+    const void *tma_ptr() const { return nullptr; }
     __device__ __forceinline__ void compute(int, const float (&)[16], uint32_t (&)[8]) const {}
     __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
         if (row >= M) return;
@@ -189,6 +203,82 @@ struct EpiGeluGrad {
 #pragma unroll
         for (int i = 0; i < 16; ++i)
             if (col0 + i < N) o[i] = __float2bfloat16_rn(v[i] * gelu_grad(zr[i]));
+    }
+};
+
+// Hidden layers of the reduced-precision forward. z = acc * cs[n] + b[n], where
+// cs = (weight scale of output n) x (input activation scale) when the operands
+// are E4M3 (F8IN) and 1 otherwise; h = GELU(z), stored as E4M3(h * inv_so)
+// with round-to-nearest-even and saturation at +-448 (F8OUT) or as BF16(h).
+template <bool F8IN, bool F8OUT>
+struct EpiGeluQ {
+    static constexpr bool kF8 = F8IN;
+    static constexpr int kOutBytes = F8OUT ? 16 : 32;
+    int M, N;
+    const float *bias;    // [N, padded to a multiple of 16]
+    const float *cs;      // [N, padded to a multiple of 16]; used when F8IN
+    void *out;
+    int64_t ldo;          // elements
+    float inv_so;         // used when F8OUT
+    __host__ __device__ __forceinline__ bool tma_store() const {
+        return (N & 15) == 0 && (reinterpret_cast<uintptr_t>(bias) & 15) == 0 &&
+               (!F8IN || (reinterpret_cast<uintptr_t>(cs) & 15) == 0);
+    }
+    const void *tma_ptr() const { return tma_store() ? out : nullptr; }
+    __device__ __forceinline__ float act(float v, float c, float b) const {
+        return gelu_exact(F8IN ? fmaf(v, c, b) : v + b);
+    }
+    __device__ __forceinline__ void compute(int col0, const float (&v)[16], uint32_t (&w)[8]) const {
+        float b[16], c[16];
+        const float4 *bp = reinterpret_cast<const float4 *>(bias + col0);
+        const float4 *cp = reinterpret_cast<const float4 *>(cs + col0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float4 q = __ldg(bp + i);
+            b[4 * i] = q.x; b[4 * i + 1] = q.y; b[4 * i + 2] = q.z; b[4 * i + 3] = q.w;
+            if (F8IN) {
+                const float4 r = __ldg(cp + i);
+                c[4 * i] = r.x; c[4 * i + 1] = r.y; c[4 * i + 2] = r.z; c[4 * i + 3] = r.w;
+            } else {
+                c[4 * i] = c[4 * i + 1] = c[4 * i + 2] = c[4 * i + 3] = 1.0f;
+            }
+        }
+        if (F8OUT) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+                    make_float2(act(v[4 * i], c[4 * i], b[4 * i]) * inv_so,
+                                act(v[4 * i + 1], c[4 * i + 1], b[4 * i + 1]) * inv_so),
+                    __NV_SATFINITE, __NV_E4M3);
+                const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                    make_float2(act(v[4 * i + 2], c[4 * i + 2], b[4 * i + 2]) * inv_so,
+                                act(v[4 * i + 3], c[4 * i + 3], b[4 * i + 3]) * inv_so),
+                    __NV_SATFINITE, __NV_E4M3);
+                w[i] = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(act(v[2 * i], c[2 * i], b[2 * i]),
+                                                         act(v[2 * i + 1], c[2 * i + 1], b[2 * i + 1]));
+                w[i] = *reinterpret_cast<uint32_t *>(&h);
+            }
+        }
+    }
+    // ragged output widths: element stores, columns >= N skipped
+    __device__ __forceinline__ void operator()(int row, int col0, const float (&v)[16]) const {
+        if (row >= M) return;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int col = col0 + i;
+            if (col >= N) break;
+            const float h = act(v[i], F8IN ? __ldg(cs + col) : 1.0f, __ldg(bias + col));
+            if (F8OUT)
+                static_cast<__nv_fp8_storage_t *>(out)[(int64_t)row * ldo + col] =
+                    __nv_cvt_float_to_fp8(h * inv_so, __NV_SATFINITE, __NV_E4M3);
+            else
+                static_cast<__nv_bfloat16 *>(out)[(int64_t)row * ldo + col] = __float2bfloat16_rn(h);
+        }
     }
 };
 
@@ -216,7 +306,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m_tiles = (M + kBM - 1) / kBM, n_tiles = (N + BN - 1) / BN;
     const int tiles = m_tiles * n_tiles;
-    const int kblocks = (K + kBK - 1) / kBK;
+    constexpr int kBKe = Epi::kF8 ? kBK8 : kBK;   // elements of K per k-block
+    const int kblocks = (K + kBKe - 1) / kBKe;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
@@ -246,8 +337,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, tc::kErrTimeoutEmpty); ok = false; break; }
                     tc::mbar_arrive_expect_tx(&full[s], L::kABytes + L::kBBytes);
-                    tc::tma_load_2d(sA + s * L::kABytes, &tmA, &full[s], kb * kBK, m_blk * kBM);
-                    tc::tma_load_2d(sB + s * L::kBBytes, &tmB, &full[s], kb * kBK, n_blk * BN);
+                    tc::tma_load_2d(sA + s * L::kABytes, &tmA, &full[s], kb * kBKe, m_blk * kBM);
+                    tc::tma_load_2d(sB + s * L::kBBytes, &tmB, &full[s], kb * kBKe, n_blk * BN);
                 }
             }
             // every issued load lands before the CTA may exit (bounded)
@@ -259,7 +350,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
+            constexpr uint32_t idesc = Epi::kF8 ? tc::idesc_e4m3_f32(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
             int it = 0, t = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
@@ -275,10 +366,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     tc::tc_fence_after();
                     const uint32_t a0 = tc::smem_u32(sA + s * L::kABytes);
                     const uint32_t b0 = tc::smem_u32(sB + s * L::kBBytes);
+                    // four instructions of 32 bytes of K each (16 BF16 or 32 E4M3)
 #pragma unroll
-                    for (int kk = 0; kk < kBK / 16; ++kk)
-                        tc::umma_f16(d_tmem, tc::sdesc_kmajor_sw128(a0 + kk * 32), tc::sdesc_kmajor_sw128(b0 + kk * 32),
-                                     idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = tc::sdesc_kmajor_sw128(a0 + kk * 32), bd = tc::sdesc_kmajor_sw128(b0 + kk * 32);
+                        if (Epi::kF8) tc::umma_f8(d_tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        else tc::umma_f16(d_tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    }
                     tc::umma_commit(&empty[s]);
                 }
                 if (!ok) break;
@@ -317,9 +411,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     uint8_t *buf = my_stage + (nstore & 1) * kStageBytesPerWarp;
                     if (nstore >= 2 && lane == 0) tc::bulk_wait_read<1>();   // this buffer's previous store has read it
                     __syncwarp();
-                    uint4 *dst = reinterpret_cast<uint4 *>(buf + lane * 32);
+                    uint4 *dst = reinterpret_cast<uint4 *>(buf + lane * Epi::kOutBytes);
                     dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                    if (Epi::kOutBytes == 32) dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
                     tc::fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {

@@ -31,20 +31,22 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled_fn() {
     return fn;
 }
 
-// 2-D BF16 tensor map over a row-major [rows][cols] matrix with row stride ld
-// (elements), box = box_rows x 64 columns, 128-byte swizzle, zero fill outside.
-inline int make_tmap_bf16(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
-    if (!aligned16(ptr) || (ld * 2) % 16 != 0)
+// 2-D operand tensor map over a row-major [rows][cols] matrix of BF16 (esize 2)
+// or E4M3 (esize 1) with row stride ld (elements): box = box_rows x 128 bytes,
+// 128-byte swizzle, zero fill outside.
+inline int make_tmap_operand(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int box_rows,
+                             int esize) {
+    if (!aligned16(ptr) || (ld * esize) % 16 != 0)
         return set_error(CHEM_EINVAL, "GEMM operand: base must be 16-byte aligned and rows a multiple of 16 bytes");
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esize), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled_fn();
     if (!enc) return set_error(CHEM_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims,
-                                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                     const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(CHEM_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
     return CHEM_OK;
 }
@@ -59,28 +61,23 @@ inline int num_sms() {
     return sms;
 }
 
-// Output tensor map for the TMA-store epilogue: BF16 [rows][cols], box 32 rows x 16 columns, no swizzle.
-inline int make_tmap_out_bf16(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld) {
-    if (!aligned16(ptr) || (ld * 2) % 16 != 0)
+// Output tensor map for the TMA-store epilogue: [rows][cols] of BF16 (esize 2)
+// or E4M3 (esize 1), box 32 rows x 16 columns, no swizzle.
+inline int make_tmap_out(CUtensorMap *map, const void *ptr, int64_t rows, int64_t cols, int64_t ld, int esize) {
+    if (!aligned16(ptr) || (ld * esize) % 16 != 0)
         return set_error(CHEM_EINVAL, "GEMM output: base must be 16-byte aligned and rows a multiple of 16 bytes");
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
     cuuint32_t box[2] = {16, 32};
     cuuint32_t estr[2] = {1, 1};
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled_fn();
     if (!enc) return set_error(CHEM_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                     const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(CHEM_ECUDA, "cuTensorMapEncodeTiled (output) failed (" + std::to_string((int)r) + ")");
     return CHEM_OK;
 }
-
-template <class Epi> struct EpiOut { static const void *ptr(const Epi &) { return nullptr; } static int64_t ld(const Epi &) { return 0; } };
-template <> struct EpiOut<EpiGelu> {
-    static const void *ptr(const EpiGelu &e) { return e.tma_store() ? e.out : nullptr; }
-    static int64_t ld(const EpiGelu &e) { return e.ldo; }
-};
 
 template <int BN, int STAGES, class Epi>
 int launch_gemm_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K, const Epi &epi,
@@ -95,14 +92,15 @@ int launch_gemm_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M
         configured = true;
     }
     CUtensorMap ta, tb;
-    int rc = make_tmap_bf16(&ta, X, M, K, ldx, kBM);
+    const int esize = Epi::kF8 ? 1 : 2;
+    int rc = make_tmap_operand(&ta, X, M, K, ldx, kBM, esize);
     if (rc) return rc;
-    rc = make_tmap_bf16(&tb, W, N, K, ldw, BN);
+    rc = make_tmap_operand(&tb, W, N, K, ldw, BN, esize);
     if (rc) return rc;
     CUtensorMap tc;
     std::memset(&tc, 0, sizeof(tc));
-    if (const void *op = EpiOut<Epi>::ptr(epi)) {
-        rc = make_tmap_out_bf16(&tc, op, M, N, EpiOut<Epi>::ld(epi));
+    if (const void *op = epi.tma_ptr()) {
+        rc = make_tmap_out(&tc, op, M, N, epi.ldo, Epi::kOutBytes / 16);
         if (rc) return rc;
     }
     const int tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
@@ -112,8 +110,9 @@ int launch_gemm_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M
     void *pb = prof_begin(st);
     gemm_tn_kernel<BN, STAGES, Epi><<<grid, kGemmThreads, L::kTotal, st>>>(ta, tb, tc, M, N, K, epi, err);
     if (pb)
-        prof_end(pb, st, "gemm_tn_kernel<" + std::to_string(BN) + "> " + std::to_string(N) + "x" + std::to_string(K),
-                 2.0 * M * N * K, 2.0 * ((double)M * K + (double)N * K));
+        prof_end(pb, st, "gemm_tn_kernel<" + std::to_string(BN) + (Epi::kF8 ? ",e4m3> " : "> ") + std::to_string(N) +
+                             "x" + std::to_string(K),
+                 2.0 * M * N * K, (double)esize * ((double)M * K + (double)N * K));
     return check_cuda(cudaGetLastError(), "GEMM launch");
 }
 
@@ -154,5 +153,10 @@ int gemm_linear(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, 
                 const float *bias, float *out, int64_t ldo, int *err, cudaStream_t st, int max_ctas = 0);
 int gemm_gelu_grad(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K,
                    const float *z, int64_t ldz, void *out, int64_t ldo, int *err, cudaStream_t st, int max_ctas = 0);
+// Reduced-precision hidden layer (EpiGeluQ): f8in selects E4M3 operands (X, W) with the per-column
+// scale cs, f8out an E4M3 output scaled by inv_so; otherwise BF16.
+int gemm_gelu_q(bool f8in, bool f8out, int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N,
+                int K, const float *bias, const float *cs, void *out, int64_t ldo, float inv_so, int *err,
+                cudaStream_t st, int max_ctas = 0);
 
 }  // namespace chemgb

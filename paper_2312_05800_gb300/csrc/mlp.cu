@@ -4,6 +4,7 @@
 // clamp + renormalise, T from the conserved enthalpy), and training (L1 loss
 // of Eq. 5, backward through the same GEMM kernel, Adam).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <cmath>
 #include <cstdio>
@@ -28,8 +29,13 @@ constexpr int kOodBlocks = 512;
 constexpr int64_t kFallbackQueue = 8388608;   // cells queued for the stiff fallback before a flush
 constexpr float kLambdaBC = 0.1f;     // Box-Cox lambda (Sec. 3.2)
 constexpr float kAdamB1 = 0.9f, kAdamB2 = 0.999f, kAdamEps = 1e-8f;
+constexpr float kE4M3Max = 448.0f;    // largest finite E4M3 value
 
 inline int64_t pad8(int64_t x) { return (x + 7) & ~int64_t(7); }
+inline int64_t pad16(int64_t x) { return (x + 15) & ~int64_t(15); }
+// the layers whose operands are E4M3 in the reduced-precision forward: the two
+// hidden-to-hidden layers (their inputs are GELU activations, not the state)
+inline bool fp8_layer(int l) { return l == 1 || l == 2; }
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -44,6 +50,9 @@ struct Layer {
     float *mW, *vW, *mb, *vb;   // Adam moments
     float *gW, *gb;       // gradients of the last training step
     int tile;             // forward tile width
+    int kin8;             // input width padded to 16 (row length of Wq)
+    uint8_t *Wq;          // E4M3 [out][kin8] (hidden-to-hidden layers only)
+    float *sw, *cs;       // per-output weight scale; sw x the input activation scale [outp padded to 16]
 };
 
 }  // namespace chemgb
@@ -76,6 +85,11 @@ struct chem_mlp {
     int32_t *fb_status;                     // [chunk] when the caller passes no status array
     float *ood_part;                        // per-block feature extrema
     int64_t adam_t;
+    // reduced-precision forward: E4M3 scales of the activations h1 and h2 (the
+    // inputs of the E4M3 layers) and whether the quantised weights are current
+    float act_scale[2];
+    int fp8_ready;
+    unsigned int *amax;                     // [2] calibration maxima (float bits)
     void *blob;
     size_t blob_bytes;
     int device;
@@ -473,6 +487,51 @@ __global__ void norm_stats_kernel(int64_t n, int64_t ld, const double *__restric
 }
 
 // ---------------------------------------------------------------------------
+// E4M3 weights of a hidden-to-hidden layer, one block per output row n:
+// sw[n] = max_k |W[n][k]| / 448 (1 for an all-zero row), Wq[n][k] = E4M3(W[n][k] / sw[n])
+// rounded to nearest even with saturation, zero padding up to kin8, cs[n] = sw[n] * s_in.
+__global__ void quant_rows_kernel(int in, int kin, int kin8, const float *__restrict__ W, uint8_t *__restrict__ Wq,
+                                  float *__restrict__ sw, float *__restrict__ cs, float s_in) {
+    __shared__ float red[32];
+    const int n = blockIdx.x;
+    const float *w = W + (int64_t)n * kin;
+    float a = 0.0f;
+    for (int k = threadIdx.x; k < in; k += blockDim.x) a = fmaxf(a, fabsf(w[k]));
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    if (warp == 0) {
+        a = lane < nw ? red[lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        if (lane == 0) red[0] = a;
+    }
+    __syncthreads();
+    a = red[0];
+    const float sc = a > 0.0f ? __fdiv_rn(a, kE4M3Max) : 1.0f;
+    for (int k = threadIdx.x; k < kin8; k += blockDim.x)
+        Wq[(int64_t)n * kin8 + k] = k < in ? __nv_cvt_float_to_fp8(__fdiv_rn(w[k], sc), __NV_SATFINITE, __NV_E4M3) : 0;
+    if (threadIdx.x == 0) {
+        sw[n] = sc;
+        cs[n] = __fmul_rn(sc, s_in);
+    }
+}
+
+// max |h| over rows [0, rows) x columns [0, cols) of a BF16 activation matrix, into *amax (float bits;
+// the maximum of non-negative floats is the maximum of their bit patterns)
+__global__ void amax_bf16_kernel(int64_t rows, int cols, int64_t ld, const __nv_bfloat16 *__restrict__ h,
+                                 unsigned int *amax) {
+    float a = 0.0f;
+    const int64_t total = rows * cols;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = e / cols, c = e - r * cols;
+        a = fmaxf(a, fabsf(__bfloat162float(h[r * ld + c])));
+    }
+    for (int o = 16; o > 0; o >>= 1) a = fmaxf(a, __shfl_xor_sync(0xffffffffu, a, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(a));
+}
+
+// ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
 
@@ -545,26 +604,60 @@ int check_state_args(int64_t ncells, int64_t ld, const void *T, const void *p, c
     return CHEM_OK;
 }
 
-// prologue + four layers on cells [0, n) of the given SoA pointers; normalised outputs into m->out
+// prologue + the first nlayers layers on cells [0, n) of the given SoA pointers; with all four,
+// the normalised outputs are in m->out. prec CHEM_PREC_FP8 runs the hidden-to-hidden layers on
+// E4M3 operands: h1 and h2 are stored as E4M3 (scales act_scale) in the buffers of h[0] and h[1],
+// h3 as BF16 for the BF16 output layer.
 int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p, const double *Y,
-                  cudaStream_t st) {
+                  cudaStream_t st, int prec = CHEM_PREC_BF16, int nlayers = kLayers) {
     void *pb = prof_begin(st);
     prologue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, T, p, Y, nullptr, m->N, m->n_in_pad, m->mu_x,
                                                                  m->isd_x, m->a0);
     prof_end(pb, st, "prologue_kernel", 0.0, (double)n * ((m->N + 2) * 8 + m->n_in_pad * 2));
     int rc = check_cuda(cudaGetLastError(), "prologue");
     if (rc) return rc;
-    const __nv_bfloat16 *x = m->a0;
+    const void *x = m->a0;
     int64_t ldx = m->n_in_pad;
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < 3 && l < nlayers; ++l) {
         const Layer &L = m->L[l];
-        rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->h[l], L.out, nullptr, 0, m->err, st);
+        if (prec == CHEM_PREC_FP8) {
+            const bool f8in = fp8_layer(l), f8out = fp8_layer(l + 1);
+            const int64_t ldo = f8out ? m->L[l + 1].kin8 : L.out;
+            const float inv_so = f8out ? 1.0f / m->act_scale[l] : 1.0f;
+            rc = gemm_gelu_q(f8in, f8out, L.tile, x, ldx, f8in ? (const void *)L.Wq : (const void *)L.Wb,
+                             f8in ? L.kin8 : L.kin, (int)n, L.out, f8in ? L.in : L.kin, L.b, L.cs, m->h[l], ldo,
+                             inv_so, m->err, st);
+            ldx = ldo;
+        } else {
+            rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->h[l], L.out, nullptr, 0, m->err,
+                           st);
+            ldx = L.out;
+        }
         if (rc) return rc;
         x = m->h[l];
-        ldx = L.out;
     }
+    if (nlayers < kLayers) return CHEM_OK;
     const Layer &L = m->L[3];
     return gemm_linear(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->out, m->n_out_pad, m->err, st);
+}
+
+// E4M3 weights and scales of the hidden-to-hidden layers from the FP32 masters and act_scale
+int quantize_fp8(chem_mlp *m, cudaStream_t st) {
+    for (int l = 0; l < kLayers; ++l) {
+        if (!fp8_layer(l)) continue;
+        Layer &L = m->L[l];
+        quant_rows_kernel<<<L.out, 256, 0, st>>>(L.in, L.kin, L.kin8, L.W, L.Wq, L.sw, L.cs, m->act_scale[l - 1]);
+    }
+    return check_cuda(cudaGetLastError(), "quantize_fp8");
+}
+
+int check_prec(const chem_mlp *m, int prec, const char *who) {
+    if (prec == CHEM_PREC_BF16) return CHEM_OK;
+    if (prec != CHEM_PREC_FP8) return set_error(CHEM_EINVAL, std::string(who) + ": unknown precision");
+    if (!m->fp8_ready)
+        return set_error(CHEM_EINVAL, std::string(who) + ": no E4M3 scales for the current parameters (call "
+                                                         "chem_mlp_calibrate_fp8 or chem_mlp_set_fp8_scales)");
+    return CHEM_OK;
 }
 
 }  // namespace
@@ -605,6 +698,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
         L.out = m->widths[l + 1];
         L.kin = (int)pad8(L.in);
         L.outp = (int)pad8(L.out);
+        L.kin8 = (int)pad16(L.in);
         L.tile = default_tile_width(L.out);
     }
     for (int j = 0; j < m->n_in; ++j) { m->h_mu_x[j] = 0.0; m->h_sd_x[j] = 1.0; }
@@ -624,7 +718,13 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
         parts.push_back({(void **)&L.vb, o * 4});
         parts.push_back({(void **)&L.gW, w * 4});
         parts.push_back({(void **)&L.gb, o * 4});
+        if (fp8_layer(l)) {
+            parts.push_back({(void **)&L.Wq, (size_t)L.out * L.kin8});
+            parts.push_back({(void **)&L.sw, (size_t)pad16(L.out) * 4});
+            parts.push_back({(void **)&L.cs, (size_t)pad16(L.out) * 4});
+        }
     }
+    parts.push_back({(void **)&m->amax, 64});
     parts.push_back({(void **)&m->mu_x, (size_t)m->n_in_pad * 4});
     parts.push_back({(void **)&m->isd_x, (size_t)m->n_in_pad * 4});
     parts.push_back({(void **)&m->mu_u, (size_t)m->n_out_pad * 4});
@@ -722,6 +822,7 @@ extern "C" int chem_mlp_set_params(chem_mlp *m, const float *host) {
         cudaMemset(L.vb, 0, (size_t)L.outp * 4);
     }
     m->adam_t = 0;
+    m->fp8_ready = 0;     // E4M3 weights and activation scales must be redone for new parameters
     rc = refresh_bf16(m, 0);
     if (rc) return rc;
     return check_cuda(cudaDeviceSynchronize(), "chem_mlp_set_params");
@@ -750,6 +851,7 @@ extern "C" int chem_mlp_set_norm(chem_mlp *m, const double *mu_x, const double *
         m->h_mu_u[j] = mu_u[j];
         m->h_sd_u[j] = (sd_u[j] < 1e-30) ? 1.0 : sd_u[j];
     }
+    m->fp8_ready = 0;     // the activation scales were calibrated under the old statistics
     return upload_norm(m);
 }
 
@@ -781,23 +883,99 @@ extern "C" int chem_mlp_fit_norm(chem_mlp *m, int64_t n, int64_t ld, const doubl
     return chem_mlp_set_norm(m, h.data(), h.data() + nf, h.data() + m->n_in, h.data() + nf + m->n_in);
 }
 
-extern "C" int chem_mlp_forward(const chem_mlp *m, int64_t ncells, int64_t ld, const double *T, const double *p,
-                                const double *Y, float *u, int64_t ldu, chem_stream_t stream) {
+extern "C" int chem_mlp_forward_prec(const chem_mlp *m, int prec, int64_t ncells, int64_t ld, const double *T,
+                                     const double *p, const double *Y, float *u, int64_t ldu, chem_stream_t stream) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_forward: null handle");
     int rc = check_state_args(ncells, ld, T, p, Y, "chem_mlp_forward");
     if (rc) return rc;
+    if ((rc = check_prec(m, prec, "chem_mlp_forward"))) return rc;
     if (ncells == 0) return CHEM_OK;
     if (!u || ldu < m->n_out) return set_error(CHEM_EINVAL, "chem_mlp_forward: null u or ldu < n_out");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int64_t c0 = 0; c0 < ncells; c0 += m->chunk) {
         const int64_t n = (ncells - c0 < m->chunk) ? ncells - c0 : m->chunk;
-        rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
+        rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st, prec);
         if (rc) return rc;
         rc = check_cuda(cudaMemcpy2DAsync(u + c0 * ldu, ldu * 4, m->out, m->n_out_pad * 4, m->n_out * 4, n,
                                           cudaMemcpyDeviceToDevice, st), "chem_mlp_forward copy");
         if (rc) return rc;
     }
     return CHEM_OK;
+}
+
+extern "C" int chem_mlp_forward(const chem_mlp *m, int64_t ncells, int64_t ld, const double *T, const double *p,
+                                const double *Y, float *u, int64_t ldu, chem_stream_t stream) {
+    return chem_mlp_forward_prec(m, CHEM_PREC_BF16, ncells, ld, T, p, Y, u, ldu, stream);
+}
+
+extern "C" int chem_mlp_set_fp8_scales(chem_mlp *m, const float *act_scale) {
+    if (!m || !act_scale) return set_error(CHEM_EINVAL, "chem_mlp_set_fp8_scales: null argument");
+    for (int i = 0; i < 2; ++i)
+        if (!(act_scale[i] > 0.0f) || !std::isfinite(act_scale[i]))
+            return set_error(CHEM_EINVAL, "chem_mlp_set_fp8_scales: scales must be positive and finite");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_set_fp8_scales: " + why);
+    m->act_scale[0] = act_scale[0];
+    m->act_scale[1] = act_scale[1];
+    int rc = quantize_fp8(m, 0);
+    if (!rc) rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_set_fp8_scales");
+    m->fp8_ready = rc == 0;
+    return rc;
+}
+
+extern "C" int chem_mlp_get_fp8_scales(const chem_mlp *m, float *act_scale) {
+    if (!m || !act_scale) return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_scales: null argument");
+    if (!m->fp8_ready) return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_scales: not calibrated");
+    act_scale[0] = m->act_scale[0];
+    act_scale[1] = m->act_scale[1];
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_calibrate_fp8(chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p,
+                                      const double *Y, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_calibrate_fp8: null handle");
+    int rc = check_state_args(n, ld, T, p, Y, "chem_mlp_calibrate_fp8");
+    if (rc) return rc;
+    if (n == 0) return set_error(CHEM_EINVAL, "chem_mlp_calibrate_fp8: no cells");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_calibrate_fp8: " + why);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    rc = check_cuda(cudaMemsetAsync(m->amax, 0, 2 * sizeof(unsigned int), st), "chem_mlp_calibrate_fp8");
+    for (int64_t c0 = 0; c0 < n && !rc; c0 += m->chunk) {
+        const int64_t k = (n - c0 < m->chunk) ? n - c0 : m->chunk;
+        rc = forward_chunk(m, k, ld, T + c0, p + c0, Y + c0, st, CHEM_PREC_BF16, 2);
+        for (int i = 0; i < 2 && !rc; ++i) {
+            amax_bf16_kernel<<<1024, 256, 0, st>>>(k, m->L[i].out, m->L[i].out, m->h[i], m->amax + i);
+            rc = check_cuda(cudaGetLastError(), "chem_mlp_calibrate_fp8");
+        }
+    }
+    unsigned int bits[2] = {0, 0};
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(bits, m->amax, sizeof(bits), cudaMemcpyDeviceToHost, st),
+                             "chem_mlp_calibrate_fp8");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_calibrate_fp8");
+    if (rc) return rc;
+    float sc[2];
+    for (int i = 0; i < 2; ++i) {
+        float a;
+        std::memcpy(&a, &bits[i], 4);
+        if (!(a > 0.0f) || !std::isfinite(a))
+            return set_error(CHEM_EINVAL, "chem_mlp_calibrate_fp8: hidden activations are all zero or not finite");
+        sc[i] = a / kE4M3Max;
+    }
+    return chem_mlp_set_fp8_scales(m, sc);
+}
+
+extern "C" int chem_mlp_get_fp8_weights(const chem_mlp *m, int layer, uint8_t *Wq, float *sw) {
+    if (!m || !Wq || !sw) return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_weights: null argument");
+    if (layer < 0 || layer >= kLayers || !fp8_layer(layer))
+        return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_weights: layer has no E4M3 weights (layers 1 and 2 have)");
+    if (!m->fp8_ready) return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_weights: not calibrated");
+    const Layer &L = m->L[layer];
+    int rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_get_fp8_weights");
+    if (!rc) rc = check_cuda(cudaMemcpy2D(Wq, L.in, L.Wq, L.kin8, L.in, L.out, cudaMemcpyDeviceToHost),
+                             "chem_mlp_get_fp8_weights");
+    if (!rc) rc = check_cuda(cudaMemcpy(sw, L.sw, (size_t)L.out * 4, cudaMemcpyDeviceToHost), "chem_mlp_get_fp8_weights");
+    return rc;
 }
 
 extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int64_t ld, double dt, int prec,
@@ -809,9 +987,9 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
         return set_error(CHEM_EINVAL, "chem_step_ann: network and mechanism disagree on the species");
     if (!(std::fabs(dt - m->dt) <= 1e-12 * m->dt))
         return set_error(CHEM_EINVAL, "chem_step_ann: dt differs from the step the network was trained for");
-    if (prec != 0) return set_error(CHEM_EUNSUPPORTED, "chem_step_ann: only CHEM_PREC_BF16 is built");
     int rc = check_state_args(ncells, ld, T, p, Y, "chem_step_ann");
     if (rc) return rc;
+    if ((rc = check_prec(m, prec, "chem_step_ann"))) return rc;
     if (ncells == 0) return CHEM_OK;
     if (status && !aligned16(status)) return set_error(CHEM_EINVAL, "chem_step_ann: status must be 16-byte aligned");
     std::string why;
@@ -841,7 +1019,7 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
         if (m->ood_enabled && queued + n > qcap) {
             if ((rc = flush(flush_base))) return rc;
         }
-        rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st);
+        rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st, prec);
         if (rc) return rc;
         OodRoute route{nullptr, nullptr, 0, 0, nullptr, nullptr, 0};
         int32_t *st_chunk = status ? status + c0 : m->fb_status;
@@ -1020,6 +1198,7 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     }
     // Adam
     m->adam_t += 1;
+    m->fp8_ready = 0;
     const float bc1 = 1.0f - std::pow(kAdamB1, (float)m->adam_t);
     const float bc2 = 1.0f - std::pow(kAdamB2, (float)m->adam_t);
     for (int l = 0; l < kLayers; ++l) {
