@@ -16,9 +16,12 @@ Paths (see --path):
       stiff integrator generates; its error against a tight stiff integration
       is measured on held-out cells and printed with the throughput, beside the
       plain method (stiff + props) timed on a sample of the same cells.
-  "stiff": chem_step_stiff (FP64 Rodas3 at rtol 1e-3, the loosest setting
-      tried; its error against a tight integration is far inside the ANN bars)
-      followed by props_eval (FP32 arithmetic on the FP64 state), 2,097,152 cells.
+  "stiff": chem_step_stiff (FP64 Rodas3 at rtol 1e-2: of rtol 1e-3, 3e-3, 1e-2,
+      3e-2 and 1e-1, the loosest whose error against a tight integration meets
+      the learned step's bars, 1e-3 relative on dY of the major species and 2 K,
+      with a factor 2 to spare) followed by props_eval (FP32 arithmetic on the
+      FP64 state), 2,097,152 cells. The same setting integrates the learned
+      step's out-of-distribution cells.
 
 Contract: python bench.py --gpus N --steps K --warmup W [--impl reference]
 prints one JSON line. Under torchrun each rank runs its own shard (the cells
@@ -44,7 +47,7 @@ NCELLS = 2097152
 NCELLS_ANN = 4194304
 DT = 1.0e-6
 TIGHT_OPTS = dict(rtol=1e-6, atol_Y=1e-13, atol_T=1e-6, h0=1e-9, max_steps=20000)
-STIFF_OPTS = dict(rtol=1e-3, atol_Y=1e-9, atol_T=1e-3, h0=1e-9, max_steps=10000)
+STIFF_OPTS = dict(rtol=1e-2, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000)
 PARITY_OPTS = dict(rtol=1e-9, atol_Y=1e-15, atol_T=1e-9, h0=1e-9, max_steps=10000)
 MECH = "c2"
 HIDDEN = {"c2": (1600, 800, 400), "c5": (2048, 1024, 512)}
@@ -310,7 +313,8 @@ def bench_stiff(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": stiff_workload(mech),
-                       "path": "stiff+props (FP64 Rodas3 rtol 1e-3, FP32 props)", "cells_per_gpu": NCELLS,
+                       "path": "stiff+props (FP64 Rodas3 rtol %g, FP32 props)" % STIFF_OPTS["rtol"],
+                       "cells_per_gpu": NCELLS,
                        "l2": "inputs larger than L2 (0.5 GB FP64 state)",
                        "mean_steps_per_cell": steps_total / NCELLS, "parallelism": "replicas" if world > 1 else "1 GPU"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -479,6 +483,20 @@ def bench_ann(args, rank, world, local):
     torch.cuda.synchronize()
     graph_ms = g0.elapsed_time(g1) / args.steps
     del graph
+    # ---- the HBM-bound part of props_eval alone: thermo only (cp, h) from the FP64 state
+    g0.record(stream)
+    for _ in range(args.steps):
+        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, None, None, None, stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    th_ms = g0.elapsed_time(g1) / args.steps
+    th_bytes = ncells * ((N + 2) * 8 + 2 * 4)
+    hbm_peak, hbm_src = measured_peak("hbm_gbs", 6800.0)
+    props_thermo = {"ms": th_ms, "bytes_per_cell": (N + 2) * 8 + 2 * 4,
+                    "achieved_GBps": th_bytes / (th_ms / 1e3) / 1e9, "peak_GBps": hbm_peak,
+                    "frac": th_bytes / (th_ms / 1e3) / 1e9 / hbm_peak, "peak_source": hbm_src,
+                    "note": "props_eval with mu, lambda, D_k null: NASA-7 cp and h only (reads T, p, Y in FP64, "
+                            "writes cp, h in FP32)"}
     # ---- the same step with the hidden-to-hidden layers on E4M3 operands
     fp8_line = None
     if fp8:
@@ -521,7 +539,7 @@ def bench_ann(args, rank, world, local):
     g_fl = sum(v[2] for v in gemm.values())
     peak, src = measured_peak("bf16_tflops", 1900.0)
     achieved = g_fl / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
-    # ---- the plain method on a sample of the same cells (stiff at rtol 1e-3 + props)
+    # ---- the plain method on a sample of the same cells (stiff at the throughput setting + props)
     ns = min(args.stiff_sample, ncells)
     torch.cuda.synchronize()
     Tw.copy_(T0)
@@ -562,7 +580,7 @@ def bench_ann(args, rank, world, local):
                "fallback_ms": sum(v[1] for k, v in prof4.items() if "fallback" in k),
                "accuracy_vs_tight_stiff": acc_c4,
                "workload": "the same %d cells with a seeded 2 %% moved off the manifold (T +/- 300 K, "
-                           "Y x exp(0.2 xi)); guard + stiff fallback (rtol 1e-3) in the step" % ncells}
+                           "Y x exp(0.2 xi)); guard + stiff fallback (rtol %g) in the step" % (ncells, STIFF_OPTS["rtol"])}
     del T4d, Y4d, Tr4, Yr4
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -600,9 +618,10 @@ def bench_ann(args, rank, world, local):
                                "the FP64 stiff integrator) + props_eval (FP32)",
                        "cells_per_gpu": ncells, "l2": "inputs larger than L2 (1 GB FP64 state)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
-            "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_rtol1e-3_vs_tight_stiff": acc_stiff,
+            "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_throughput_setting_vs_tight_stiff": acc_stiff,
                          "reference": "chem_step_stiff rtol 1e-6 on the first %d cells" % ne},
-            "stiff": {"value": stiff_value, "unit": "cells/s", "path": "chem_step_stiff rtol 1e-3 + props_eval",
+            "stiff": {"value": stiff_value, "unit": "cells/s",
+                      "path": "chem_step_stiff rtol %g + props_eval" % STIFF_OPTS["rtol"],
                       "sample": "first %d of the %d cells, one step" % (ns, ncells),
                       "ann_speedup": value / stiff_value},
             "training": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": 4096,
@@ -623,6 +642,7 @@ def bench_ann(args, rank, world, local):
                       "note": "the whole step captured once as a CUDA graph and replayed"},
             "batched_fallback": batched,
             "fp8": fp8_line,
+            "props_thermo": props_thermo,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks * 6 + 1),
             "clocks": clk.summary()}

@@ -8,7 +8,8 @@ prologue -> network -> epilogue, written out plainly:
   Y' = max(Y + dY, 0) / sum(max(Y + dY, 0))
   T' : h(T', Y') = h(T, Y)  (adiabatic, constant p), Newton to |dT| < 1e-10 K.
 round_bf16 rounds the operands at the points where the GPU stores BF16 (the
-network input, the weights and each hidden activation); accumulation stays FP64.
+weights and each hidden activation; the network input, formed in FP32, as the
+sum of two BF16 terms hi + lo); accumulation stays FP64.
 """
 from __future__ import annotations
 
@@ -69,12 +70,19 @@ def quantize_rows(W):
 
 def calibrate_fp8(layers, z):
     """E4M3 activation scales s_i = fl32(max |h_i| / 448) of the BF16 forward's h1, h2."""
-    h = to_bf16(np.asarray(z, np.float64))
+    h = split_bf16(z)
     s = []
     for W, b in layers[:2]:
         h = to_bf16(M.gelu(h @ to_bf16(W).T + b))
         s.append(float(np.float32(np.abs(h).max() / E4M3_MAX)))
     return s
+
+
+def split_bf16(z):
+    """z (FP32 values) as the sum of two BF16 terms: hi = bf16(z), lo = bf16(z - hi)."""
+    z = np.asarray(z, np.float64)
+    hi = to_bf16(z)
+    return hi + to_bf16(z - hi)
 
 
 def out_species(mech):
@@ -88,7 +96,7 @@ def network(layers, z, round_bf16=False, fp8_scales=None):
     of quantize_rows, with z = (h_q . Wq) fl32(sw s) + b (accumulation exact)."""
     h = np.asarray(z, np.float64)
     if round_bf16 or fp8_scales is not None:
-        h = to_bf16(h)
+        h = split_bf16(h)
     nl = len(layers)
     for i, (W, b) in enumerate(layers):
         if fp8_scales is not None and i in (1, 2):

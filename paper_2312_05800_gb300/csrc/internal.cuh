@@ -86,4 +86,32 @@ void prof_end(void *begin, cudaStream_t st, const std::string &tag, double flops
 int check_cuda(cudaError_t e, const char *what);
 bool device_ok(std::string *why);
 inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// Precision conversions by integer operations. On this part the FP64 pipe (which
+// also converts between FP32 and FP64) runs at 1/64 of the FP32 rate, so the
+// per-species conversions of the cell kernels are done on the integer pipe.
+// FP64 -> FP32 by truncating the mantissa (relative error < 2^-23); magnitudes
+// below 2^-126 become signed zero, above the FP32 range infinity; NaN stays NaN.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+    const int eb = static_cast<int>((b >> 52) & 0x7FF);
+    const unsigned int mant = static_cast<unsigned int>(b >> 29) & 0x7FFFFFu;
+    if (eb == 0x7FF) return __uint_as_float(sign | 0x7F800000u | mant);
+    const int e = eb - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+    return __uint_as_float(sign | (static_cast<unsigned int>(e) << 23) | mant);
+}
+// FP32 -> FP64, exact for normal numbers and zero; FP32 subnormals (below 2^-126)
+// become signed zero; infinities and NaN are kept.
+__device__ __forceinline__ double f32_to_f64_int(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const unsigned long long sign = static_cast<unsigned long long>(b & 0x80000000u) << 32;
+    const unsigned int e = (b >> 23) & 0xFFu;
+    if (e == 0) return __longlong_as_double(static_cast<long long>(sign));
+    const unsigned long long ed = (e == 0xFFu) ? 0x7FFull : static_cast<unsigned long long>(e) + 896ull;
+    const unsigned long long mant = static_cast<unsigned long long>(b & 0x7FFFFFu) << 29;
+    return __longlong_as_double(static_cast<long long>(sign | (ed << 52) | mant));
+}
 }  // namespace chemgb

@@ -43,9 +43,11 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 struct Layer {
     int in, out;          // logical widths
     int kin;              // padded input width (row length of W, multiple of 8)
+    int kx;               // forward GEMM K and row length of Wb: 2 kin for the first layer, whose
+                          // input is carried as two BF16 terms (hi + lo), else kin
     int outp;             // padded output width (multiple of 8)
     float *W, *b;         // FP32 master [out][kin], [outp]
-    __nv_bfloat16 *Wb;    // BF16 [out][kin]
+    __nv_bfloat16 *Wb;    // BF16 [out][kx] (the first layer: [W | W] for the hi and lo input terms)
     __nv_bfloat16 *Wt;    // BF16 transposed [in][outp]
     float *mW, *vW, *mb, *vb;   // Adam moments
     float *gW, *gb;       // gradients of the last training step
@@ -103,7 +105,10 @@ namespace {
 // kernels
 // ---------------------------------------------------------------------------
 
-// Rows z = (x - mu) / sigma, x = (T, p, F(Y_1..Y_N)), F(Y) = (max(Y,0)^0.1 - 1)/0.1, as BF16.
+// Rows z = (x - mu) / sigma, x = (T, p, F(Y_1..Y_N)), F(Y) = (max(Y,0)^0.1 - 1)/0.1, each value as
+// two BF16 terms z = hi + lo (hi = bf16(z), lo = bf16(z - hi): 16 significant bits, so the state
+// reaches the first layer at about 2^-17 relative instead of BF16's 2^-9). Row layout:
+// [hi(0 .. n_in_pad) | lo(0 .. n_in_pad)]; padding columns are 0.
 __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict__ T, const double *__restrict__ p,
                                 const double *__restrict__ Y, const int32_t *__restrict__ idx, int N, int n_in_pad,
                                 const float *__restrict__ mu, const float *__restrict__ isd,
@@ -111,9 +116,9 @@ __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t c = idx ? (int64_t)idx[i] : i;
-    __nv_bfloat16 *row = out + i * n_in_pad;
+    __nv_bfloat16 *row = out + i * 2 * n_in_pad;
     for (int j0 = 0; j0 < n_in_pad; j0 += 8) {
-        __align__(16) __nv_bfloat16 v[8];
+        __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int j = j0 + u;
@@ -127,9 +132,11 @@ __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict_
                 x = 0.0f;
             }
             const float z = (j < N + 2) ? (x - __ldg(mu + j)) * __ldg(isd + j) : 0.0f;
-            v[u] = __float2bfloat16_rn(z);
+            hi[u] = __float2bfloat16_rn(z);
+            lo[u] = __float2bfloat16_rn(z - __bfloat162float(hi[u]));
         }
-        *reinterpret_cast<uint4 *>(row + j0) = *reinterpret_cast<const uint4 *>(v);
+        *reinterpret_cast<uint4 *>(row + j0) = *reinterpret_cast<const uint4 *>(hi);
+        *reinterpret_cast<uint4 *>(row + n_in_pad + j0) = *reinterpret_cast<const uint4 *>(lo);
     }
 }
 
@@ -205,7 +212,7 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
         dy[k] = 0.0f;
         yf[k] = 0.0f;
         if (k < N) {
-            const float y = (float)Y[(int64_t)k * ld + i];
+            const float y = f64_to_f32_trunc(Y[(int64_t)k * ld + i]);
             yf[k] = y;
             if (k != bath) {
                 const int j = (k < bath) ? k : k - 1;   // outputs: the non-bath species, ascending
@@ -221,7 +228,7 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
     }
     if (ood.range) {
         // a cell outside the training distribution keeps its state and goes to the stiff integrator
-        const float f[3] = {T0, h0, (float)Y[(int64_t)ood.species * ld + i]};
+        const float f[3] = {T0, h0, f64_to_f32_trunc(Y[(int64_t)ood.species * ld + i])};
         const int b = ood_bin(f, ood.range, ood.nb);
         if (b < 0 || ood.mask[b] == 0) {
             const unsigned int q = atomicAdd(ood.count, 1u);
@@ -260,17 +267,24 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
         Tn -= d;
         if (fabsf(d) < 1e-4f) break;
     }
+    // FP64 update, clamp and renormalisation: three FP64-pipe instructions per species
+    // (the widening of dY and the clamp test of the sign bit run on the integer pipe)
+    double v[NMAX];
     double s64 = 0.0;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k)
-        if (k < N) s64 += fmax(Y[(int64_t)k * ld + i] + (double)dy[k], 0.0);
+    for (int k = 0; k < NMAX; ++k) {
+        v[k] = 0.0;
+        if (k < N) {
+            double t = Y[(int64_t)k * ld + i] + f32_to_f64_int(dy[k]);
+            if (__double_as_longlong(t) < 0) t = 0.0;
+            v[k] = t;
+            s64 += t;
+        }
+    }
     const double inv = 1.0 / s64;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k)
-        if (k < N) {
-            double *q = Y + (int64_t)k * ld + i;
-            *q = fmax(*q + (double)dy[k], 0.0) * inv;
-        }
+        if (k < N) Y[(int64_t)k * ld + i] = v[k] * inv;
     T[i] = (double)Tn;
     if (status) status[i] = CHEM_CELL_OK;
 }
@@ -400,7 +414,7 @@ __global__ void transpose_kernel(int rows, int cols, const __nv_bfloat16 *__rest
 }
 
 // Adam (Kingma and Ba 2015) on one layer; refreshes the BF16 and transposed BF16 copies.
-__global__ void adam_kernel(int out, int in, int kin, int outp, float *__restrict__ W, float *__restrict__ b,
+__global__ void adam_kernel(int out, int in, int kin, int kx, int outp, float *__restrict__ W, float *__restrict__ b,
                             const float *__restrict__ gW, const float *__restrict__ gb, float *__restrict__ mW,
                             float *__restrict__ vW, float *__restrict__ mb, float *__restrict__ vb,
                             __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Wt, float lr, float bc1,
@@ -418,7 +432,8 @@ __global__ void adam_kernel(int out, int in, int kin, int outp, float *__restric
         const float w = W[q] - lr * (m / bc1) / (sqrtf(v / bc2) + kAdamEps);
         W[q] = w;
         const __nv_bfloat16 wb = __float2bfloat16_rn(w);
-        Wb[q] = wb;
+        Wb[(int64_t)o * kx + k] = wb;
+        if (kx != kin) Wb[(int64_t)o * kx + kin + k] = wb;   // the lo-term copy of the first layer
         Wt[(int64_t)k * outp + o] = wb;
     } else if (t < nW + out) {
         const int o = (int)(t - nW);
@@ -432,13 +447,14 @@ __global__ void adam_kernel(int out, int in, int kin, int outp, float *__restric
 }
 
 // FP32 master -> BF16 copies (after set_params).
-__global__ void refresh_bf16_kernel(int out, int in, int kin, int outp, const float *__restrict__ W,
+__global__ void refresh_bf16_kernel(int out, int in, int kin, int kx, int outp, const float *__restrict__ W,
                                     __nv_bfloat16 *__restrict__ Wb, __nv_bfloat16 *__restrict__ Wt) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)out * kin) return;
     const int o = (int)(t / kin), k = (int)(t % kin);
     const __nv_bfloat16 wb = __float2bfloat16_rn(k < in ? W[t] : 0.0f);
-    Wb[t] = wb;
+    Wb[(int64_t)o * kx + k] = wb;
+    if (kx != kin) Wb[(int64_t)o * kx + kin + k] = wb;
     if (k < in) Wt[(int64_t)k * outp + o] = wb;
 }
 
@@ -590,7 +606,8 @@ int refresh_bf16(chem_mlp *m, cudaStream_t st) {
     for (int l = 0; l < kLayers; ++l) {
         const Layer &L = m->L[l];
         int64_t n = (int64_t)L.out * L.kin;
-        refresh_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L.out, L.in, L.kin, L.outp, L.W, L.Wb, L.Wt);
+        refresh_bf16_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L.out, L.in, L.kin, L.kx, L.outp, L.W, L.Wb,
+                                                                          L.Wt);
     }
     return check_cuda(cudaGetLastError(), "refresh_bf16");
 }
@@ -613,11 +630,11 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
     void *pb = prof_begin(st);
     prologue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, T, p, Y, nullptr, m->N, m->n_in_pad, m->mu_x,
                                                                  m->isd_x, m->a0);
-    prof_end(pb, st, "prologue_kernel", 0.0, (double)n * ((m->N + 2) * 8 + m->n_in_pad * 2));
+    prof_end(pb, st, "prologue_kernel", 0.0, (double)n * ((m->N + 2) * 8 + m->n_in_pad * 4));
     int rc = check_cuda(cudaGetLastError(), "prologue");
     if (rc) return rc;
     const void *x = m->a0;
-    int64_t ldx = m->n_in_pad;
+    int64_t ldx = 2 * m->n_in_pad;
     for (int l = 0; l < 3 && l < nlayers; ++l) {
         const Layer &L = m->L[l];
         if (prec == CHEM_PREC_FP8) {
@@ -625,11 +642,11 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
             const int64_t ldo = f8out ? m->L[l + 1].kin8 : L.out;
             const float inv_so = f8out ? 1.0f / m->act_scale[l] : 1.0f;
             rc = gemm_gelu_q(f8in, f8out, L.tile, x, ldx, f8in ? (const void *)L.Wq : (const void *)L.Wb,
-                             f8in ? L.kin8 : L.kin, (int)n, L.out, f8in ? L.in : L.kin, L.b, L.cs, m->h[l], ldo,
+                             f8in ? L.kin8 : L.kx, (int)n, L.out, f8in ? L.in : L.kx, L.b, L.cs, m->h[l], ldo,
                              inv_so, m->err, st);
             ldx = ldo;
         } else {
-            rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->h[l], L.out, nullptr, 0, m->err,
+            rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kx, (int)n, L.out, L.kx, L.b, m->h[l], L.out, nullptr, 0, m->err,
                            st);
             ldx = L.out;
         }
@@ -638,7 +655,7 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
     }
     if (nlayers < kLayers) return CHEM_OK;
     const Layer &L = m->L[3];
-    return gemm_linear(L.tile, x, ldx, L.Wb, L.kin, (int)n, L.out, L.kin, L.b, m->out, m->n_out_pad, m->err, st);
+    return gemm_linear(L.tile, x, ldx, L.Wb, L.kx, (int)n, L.out, L.kx, L.b, m->out, m->n_out_pad, m->err, st);
 }
 
 // E4M3 weights and scales of the hidden-to-hidden layers from the FP32 masters and act_scale
@@ -697,6 +714,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
         L.in = m->widths[l];
         L.out = m->widths[l + 1];
         L.kin = (int)pad8(L.in);
+        L.kx = (l == 0) ? 2 * L.kin : L.kin;
         L.outp = (int)pad8(L.out);
         L.kin8 = (int)pad16(L.in);
         L.tile = default_tile_width(L.out);
@@ -710,7 +728,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
         size_t w = (size_t)L.out * L.kin, o = (size_t)L.outp;
         parts.push_back({(void **)&L.W, w * 4});
         parts.push_back({(void **)&L.b, o * 4});
-        parts.push_back({(void **)&L.Wb, w * 2});
+        parts.push_back({(void **)&L.Wb, (size_t)L.out * L.kx * 2});
         parts.push_back({(void **)&L.Wt, (size_t)L.in * L.outp * 2});
         parts.push_back({(void **)&L.mW, w * 4});
         parts.push_back({(void **)&L.vW, w * 4});
@@ -732,12 +750,12 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->out_sp_dev, (size_t)64 * 4});
     parts.push_back({(void **)&m->err, 64});
     const int64_t C = m->chunk, B = m->max_batch;
-    parts.push_back({(void **)&m->a0, (size_t)C * m->n_in_pad * 2});
+    parts.push_back({(void **)&m->a0, (size_t)C * m->n_in_pad * 4});
     for (int i = 0; i < 3; ++i) parts.push_back({(void **)&m->h[i], (size_t)C * desc->n_hidden[i] * 2});
     parts.push_back({(void **)&m->out, (size_t)C * m->n_out_pad * 4});
     int maxw = m->n_in_pad > m->n_out_pad ? m->n_in_pad : m->n_out_pad;
     for (int i = 0; i < 3; ++i) maxw = desc->n_hidden[i] > maxw ? desc->n_hidden[i] : maxw;
-    parts.push_back({(void **)&m->tx0, (size_t)B * m->n_in_pad * 2});
+    parts.push_back({(void **)&m->tx0, (size_t)B * m->n_in_pad * 4});
     for (int i = 0; i < 3; ++i) {
         parts.push_back({(void **)&m->th[i], (size_t)B * desc->n_hidden[i] * 2});
         parts.push_back({(void **)&m->tz[i], (size_t)B * desc->n_hidden[i] * 4});
@@ -1153,17 +1171,17 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     prologue_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, ld, T, p, Y, idx, m->N, m->n_in_pad, m->mu_x, m->isd_x, m->tx0);
     if ((rc = check_cuda(cudaGetLastError(), "train prologue"))) return rc;
     const __nv_bfloat16 *x = m->tx0;
-    int64_t ldx = m->n_in_pad;
+    int64_t ldx = 2 * m->n_in_pad;
     for (int l = 0; l < 3; ++l) {
         const Layer &L = m->L[l];
-        rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kin, B, L.out, L.kin, L.b, m->th[l], L.out, m->tz[l], L.out, m->err, st);
+        rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->th[l], L.out, m->tz[l], L.out, m->err, st);
         if (rc) return rc;
         x = m->th[l];
         ldx = L.out;
     }
     {
         const Layer &L = m->L[3];
-        rc = gemm_linear(L.tile, x, ldx, L.Wb, L.kin, B, L.out, L.kin, L.b, m->tout, m->n_out_pad, m->err, st);
+        rc = gemm_linear(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->tout, m->n_out_pad, m->err, st);
         if (rc) return rc;
     }
     // loss and dL/du
@@ -1176,11 +1194,13 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     int lddz = m->n_out_pad;
     for (int l = 3; l >= 0; --l) {
         const Layer &L = m->L[l];
+        // the first layer's weight gradient takes the hi input term (BF16 precision suffices for a gradient)
         const __nv_bfloat16 *hin = (l == 0) ? m->tx0 : m->th[l - 1];
-        const int ldh = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
+        const int wh = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
+        const int ldh = (l == 0) ? 2 * m->n_in_pad : wh;
         dim3 tb(32, 8);
         transpose_kernel<<<dim3((lddz + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, lddz, dz, lddz, m->tT0, B);
-        transpose_kernel<<<dim3((ldh + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, ldh, hin, ldh, m->tT1, B);
+        transpose_kernel<<<dim3((wh + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, wh, hin, ldh, m->tT1, B);
         if ((rc = check_cuda(cudaGetLastError(), "train transpose"))) return rc;
         rc = gemm_linear(default_tile_width(L.kin), m->tT0, B, m->tT1, B, L.out, L.kin, B, nullptr, L.gW, L.kin, m->err,
                          st);
@@ -1204,7 +1224,7 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     for (int l = 0; l < kLayers; ++l) {
         Layer &L = m->L[l];
         const int64_t n = (int64_t)L.out * L.in + L.out;
-        adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L.out, L.in, L.kin, L.outp, L.W, L.b, L.gW, L.gb, L.mW,
+        adam_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(L.out, L.in, L.kin, L.kx, L.outp, L.W, L.b, L.gW, L.gb, L.mW,
                                                                  L.vW, L.mb, L.vb, L.Wb, L.Wt, lr, bc1, bc2);
     }
     return check_cuda(cudaGetLastError(), "train adam");
@@ -1371,7 +1391,7 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
     for (int l = 0; l < kLayers && !rc; ++l) {
         Layer &L = m->L[l];
         const __nv_bfloat16 *x = (l == 0) ? m->a0 : m->h[l - 1];
-        const int64_t ldx = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
+        const int64_t ldx = (l == 0) ? 2 * m->n_in_pad : m->L[l - 1].out;
         float best = 3.4e38f;
         int best_bn = L.tile;
         for (int bn : kTileWidths) {
@@ -1382,10 +1402,10 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
                 rc = check_cuda(cudaEventRecord(e0, st), "autotune record");
                 if (rc) break;
                 if (l < 3)
-                    rc = gemm_gelu(bn, x, ldx, L.Wb, L.kin, (int)rows, L.out, L.kin, L.b, m->h[l], L.out, nullptr, 0,
+                    rc = gemm_gelu(bn, x, ldx, L.Wb, L.kx, (int)rows, L.out, L.kx, L.b, m->h[l], L.out, nullptr, 0,
                                    m->err, st);
                 else
-                    rc = gemm_linear(bn, x, ldx, L.Wb, L.kin, (int)rows, L.out, L.kin, L.b, m->out, m->n_out_pad,
+                    rc = gemm_linear(bn, x, ldx, L.Wb, L.kx, (int)rows, L.out, L.kx, L.b, m->out, m->n_out_pad,
                                      m->err, st);
                 if (rc) break;
                 rc = check_cuda(cudaEventRecord(e1, st), "autotune record");

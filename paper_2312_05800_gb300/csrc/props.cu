@@ -59,6 +59,13 @@ __device__ __forceinline__ void load4s(const real *p, real &a, real &b, real &c,
     }
 }
 
+// state value -> working precision; FP64 -> FP32 on the integer pipe (truncation, < 2^-23 relative)
+template <typename real, typename in_t>
+__device__ __forceinline__ real to_real(in_t x) {
+    if constexpr (sizeof(real) == 4 && sizeof(in_t) == 8) return f64_to_f32_trunc(x);
+    else return real(x);
+}
+
 template <typename real, typename in_t, int NMAX>
 __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, PropTables<real> tb, int64_t ncells,
                                                     int64_t ld, const in_t *__restrict__ Tg,
@@ -76,8 +83,8 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
     const real *dif = in_smem ? shtab + 3 * N * Np : tb.diff;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
-        const real T = real(Tg[i]);
-        const real p = real(pg[i]);
+        const real T = to_real<real>(Tg[i]);
+        const real p = to_real<real>(pg[i]);
         const int rng = (T >= T_mid) ? 1 : 0;
         const real x = log(T) - real(6.907755278982137);   // ln(T / 1000)
         real S = 0, cpm = 0, hm = 0;
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
             if (k < N) {
-                const real y = real(Yg[(int64_t)k * ld + i]);
+                const real y = to_real<real>(Yg[(int64_t)k * ld + i]);
                 const real iw = __ldg(tb.invW + k);
                 const real *a = tb.nasa_cp + (rng * N + k) * 5;
                 const real *b = tb.nasa_h + (rng * N + k) * 6;

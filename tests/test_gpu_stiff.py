@@ -84,17 +84,22 @@ def test_status_codes_and_edges(oracle):
 
 
 def test_full_size_sampled(oracle):
-    # 2,097,152 cells at the bench's throughput tolerances; sampled cells vs the oracle
+    # 2,097,152 cells at the bench's throughput setting; sampled cells vs the oracle
     m = synth.mech_c2()
     n = 2097152
     T, p, Y = synth.states_profiles(m, n, 2002)
-    opts = dict(rtol=1e-3, atol_Y=1e-9, atol_T=1e-3, h0=1e-9, max_steps=10000)
+    rtol = 1e-2
+    opts = dict(rtol=rtol, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000)
     Tg, Yg, sg, ng = _gpu("c2", T, p, Y, n, n, **opts)
     assert np.all(sg == 0)
     import oracle as O
     idx = np.concatenate([np.random.default_rng(1).choice(n, 96, replace=False), [0, n - 1]])
     To, Yo, so, no = O.step_stiff(m, T[idx].copy(), p[idx].copy(), Y[:, idx].copy(), DT, **opts)
-    # same algorithm; a rare differing accept/reject decision moves the result by about the tolerance
-    assert np.all(np.abs(Tg[idx] - To) <= 1e-3 * To)
-    assert np.all(np.abs(Yg[:, idx] - Yo) <= 1e-3 * np.abs(Yo) + 1e-6)
-    assert np.mean(ng[idx] == no) > 0.8
+    # same algorithm: where the accept/reject decisions agree the results agree to round-off;
+    # a rare differing decision moves the result by about the tolerance
+    assert np.all(np.abs(Tg[idx] - To) <= rtol * To)
+    assert np.all(np.abs(Yg[:, idx] - Yo) <= rtol * np.abs(Yo) + 1e-6)
+    same = ng[idx] == no
+    assert np.mean(same) > 0.8
+    close = (np.abs(Tg[idx] - To) <= 1e-6 * To) & np.all(np.abs(Yg[:, idx] - Yo) <= 1e-6 * np.abs(Yo) + 1e-12, axis=0)
+    assert np.mean(close[same]) > 0.9

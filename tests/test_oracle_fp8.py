@@ -112,7 +112,7 @@ def test_fp8_network_error_level_on_random_weights():
               ((L["W"], L["b"]) for L in M.init_params([10, 256, 128, 64, 6], seed=5))]
     z = np.random.default_rng(6).normal(size=(400, 10))
     s = A.calibrate_fp8(layers, z)
-    h1 = A.to_bf16(M.gelu(A.to_bf16(z) @ A.to_bf16(layers[0][0]).T + layers[0][1]))
+    h1 = A.to_bf16(M.gelu(A.split_bf16(z) @ A.to_bf16(layers[0][0]).T + layers[0][1]))
     assert np.isclose(np.abs(h1).max() / s[0], 448.0, rtol=1e-6)
     u8 = A.network(layers, z, fp8_scales=s)
     u64 = A.network(layers, z)

@@ -83,3 +83,15 @@ def test_adam_first_step_closed_form():
     g = grads[0]["W"]
     assert np.allclose(layers[0]["W"], W0 - 1e-3 * g / (np.abs(g) + M.ADAM_EPS), rtol=0, atol=1e-15)
     assert layers[0]["b"][0] == 0.5
+
+
+def test_two_term_bf16_input():
+    # the network input is carried as hi + lo BF16 terms: 16 significant bits
+    from oracle import ann as A
+    rng = np.random.default_rng(9)
+    z = (rng.normal(size=20000) * 10.0 ** rng.uniform(-4, 2, 20000)).astype(np.float32).astype(np.float64)
+    s = A.split_bf16(z)
+    assert np.all(np.abs(s - z) <= 2.0 ** -16 * np.abs(z))
+    assert np.mean(np.abs(A.to_bf16(z) - z) > 2.0 ** -16 * np.abs(z)) > 0.9   # one BF16 term is not enough
+    b = A.to_bf16(z)
+    assert np.array_equal(A.split_bf16(b), b)                                 # BF16 values: lo = 0
