@@ -402,7 +402,7 @@ def bench_ann(args, rank, world, local):
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         # out-of-distribution guard fitted on the training states; off-grid cells fall back to stiff
-        binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["water"], 64,
+        binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["oxidizer"], 64,
                                  args.ood_kmin)
         if fp8:
             # E4M3 activation scales from the BF16 forward of training states
@@ -456,11 +456,13 @@ def bench_ann(args, rank, world, local):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     binding.chem_prof_enable(True)
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")          # lets a profiler select the timed launches
         ev[0].record(stream)
         for _ in range(args.steps):
             step()
         ev[1].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     prof = binding.chem_prof_read()
     binding.chem_prof_enable(False)
     n_fallback = int((status[:ncells] == binding.CELL_FALLBACK).sum().item())
@@ -634,7 +636,7 @@ def bench_ann(args, rank, world, local):
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
                                        for k, v in gemm.items()}},
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-            "guard": {"ood": not args.untrained, "grid": "64^3 over (T, h/R, Y_water), neighbourhood >= %d"
+            "guard": {"ood": not args.untrained, "grid": "64^3 over (T, h/R, Y_oxidizer), neighbourhood >= %d"
                       % args.ood_kmin, "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
                       "fallback_rtol": STIFF_OPTS["rtol"]},
             "autotuned_tiles": tiles,
@@ -686,8 +688,8 @@ def main():
     ap.add_argument("--cells", type=int, default=None,
                     help="cells per GPU (default 4,194,304 for ann, 2,097,152 for stiff); smaller values only for "
                          "profiling captures")
-    ap.add_argument("--train-pairs", type=int, default=524288)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--train-pairs", type=int, default=2097152)
+    ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-cells", type=int, default=32768)
     ap.add_argument("--stiff-sample", type=int, default=262144)

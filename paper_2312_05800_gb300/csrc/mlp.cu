@@ -183,13 +183,16 @@ struct OodRoute {
 };
 
 template <int NMAX>
-__global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu,
+__global__ void __launch_bounds__(128, (NMAX <= 32 ? 8 : 4)) epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu,
                                                        int N, int bath, const float *__restrict__ mu_u,
                                                        const float *__restrict__ sd_u, PropTables<float> tb,
                                                        float T_mid, double *__restrict__ T, double *__restrict__ Y,
                                                        int32_t *__restrict__ status, OodRoute ood) {
     // per species and range: cp/R coefficients (5), H/R coefficients (6), 1/W -> 3 float4
     __shared__ float4 tab[2 * NMAX * 3];
+    // dY per species and thread (column per thread: conflict-free), so that only the provisional
+    // Y' stays in registers and the kernel keeps more warps resident
+    __shared__ float dyS[NMAX][128];
     for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
         const int rg = e / N, k = e % N;
         const float *a = tb.nasa_cp + (rg * N + k) * 5;
@@ -202,23 +205,25 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const int t = threadIdx.x;
     const float *ur = u + i * ldu;
     const float T0 = (float)T[i];
     const int r0 = (T0 >= T_mid) ? 1 : 0;
-    float dy[NMAX], yf[NMAX];
+    float yf[NMAX];
     float sum = 0.0f, h0 = 0.0f;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
-        dy[k] = 0.0f;
         yf[k] = 0.0f;
         if (k < N) {
             const float y = f64_to_f32_trunc(Y[(int64_t)k * ld + i]);
             yf[k] = y;
+            float d = 0.0f;
             if (k != bath) {
                 const int j = (k < bath) ? k : k - 1;   // outputs: the non-bath species, ascending
-                dy[k] = fmaf(__ldg(sd_u + j), ur[j], __ldg(mu_u + j));
-                sum += dy[k];
+                d = fmaf(__ldg(sd_u + j), ur[j], __ldg(mu_u + j));
+                sum += d;
             }
+            dyS[k][t] = d;
             const float4 *q = tab + (r0 * NMAX + k) * 3;
             const float4 q1 = q[1], q2 = q[2];
             float hh = fmaf(fmaf(fmaf(fmaf(q2.y, T0, q2.x), T0, q1.w), T0, q1.z), T0, q1.y);
@@ -236,12 +241,12 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
             return;
         }
     }
+    dyS[bath][t] = -sum;
     float s = 0.0f;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
         if (k < N) {
-            if (k == bath) dy[k] = -sum;
-            yf[k] = fmaxf(yf[k] + dy[k], 0.0f);
+            yf[k] = fmaxf(yf[k] + dyS[k][t], 0.0f);
             s += yf[k];
         }
     }
@@ -267,24 +272,28 @@ __global__ void __launch_bounds__(128) epilogue_kernel(int64_t n, int64_t ld, co
         Tn -= d;
         if (fabsf(d) < 1e-4f) break;
     }
-    // FP64 update, clamp and renormalisation: three FP64-pipe instructions per species
-    // (the widening of dY and the clamp test of the sign bit run on the integer pipe)
-    double v[NMAX];
+    // FP64 update, clamp and renormalisation in two passes over the species (the state is
+    // re-read from cache): the widening of dY and the clamp test of the sign bit run on the
+    // integer pipe, leaving four FP64-pipe instructions per species
     double s64 = 0.0;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
-        v[k] = 0.0;
         if (k < N) {
-            double t = Y[(int64_t)k * ld + i] + f32_to_f64_int(dy[k]);
-            if (__double_as_longlong(t) < 0) t = 0.0;
-            v[k] = t;
-            s64 += t;
+            double y = Y[(int64_t)k * ld + i] + f32_to_f64_int(dyS[k][t]);
+            if (__double_as_longlong(y) < 0) y = 0.0;
+            s64 += y;
         }
     }
     const double inv = 1.0 / s64;
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k)
-        if (k < N) Y[(int64_t)k * ld + i] = v[k] * inv;
+    for (int k = 0; k < NMAX; ++k) {
+        if (k < N) {
+            double *q = Y + (int64_t)k * ld + i;
+            double y = *q + f32_to_f64_int(dyS[k][t]);
+            if (__double_as_longlong(y) < 0) y = 0.0;
+            *q = y * inv;
+        }
+    }
     T[i] = (double)Tn;
     if (status) status[i] = CHEM_CELL_OK;
 }

@@ -18,10 +18,11 @@ def _run(name, T, p, Y, n, ld, dtype):
     import torch
     from paper_2312_05800_gb300 import binding
     m = dev_mech(name)
-    td = torch.float32 if dtype == binding.CHEM_F32 else torch.float64
+    td = torch.float32 if dtype == binding.CHEM_F32 else torch.float64          # state
+    to = torch.float64 if dtype == binding.CHEM_F64 else torch.float32          # properties
     Td, pd, Yd = to_dev(T, td), to_dev(p, td), to_dev(Y, td)
-    outs = [torch.full((ld,), float("nan"), dtype=td, device="cuda") for _ in range(4)]
-    Dk = torch.full((m.N, ld), float("nan"), dtype=td, device="cuda")
+    outs = [torch.full((ld,), float("nan"), dtype=to, device="cuda") for _ in range(4)]
+    Dk = torch.full((m.N, ld), float("nan"), dtype=to, device="cuda")
     binding.props_eval(m, n, ld, dtype, Td, pd, Yd, *outs, Dk)
     torch.cuda.synchronize()
     return [o.double().cpu().numpy() for o in outs] + [Dk.double().cpu().numpy()]
@@ -99,3 +100,24 @@ def test_full_size_sampled(oracle):
     Ts, ps, Ys = T[idx].copy(), p[idx].copy(), Y[:, idx].copy()
     sub = [g[idx] for g in got[:4]] + [got[4][:, idx]]
     _compare(oracle, "c2", Ts, ps, Ys, idx.size, sub, 1e-5)
+
+
+@pytest.mark.parametrize("name,n", [("c2", 65531), ("c5", 8189)])
+def test_thermo_only_pass(oracle, name, n):
+    # without transport outputs props_eval runs the thermo-only kernel: cp and h bitwise equal to
+    # the full pass's (same FP32 arithmetic), from FP32 and from FP64 state; cells past n untouched
+    import torch
+    from paper_2312_05800_gb300 import binding
+    m = synth.get_mech(name)
+    ld = synth.padded_ld(n) + 8
+    T, p, Y = synth.states_profiles(m, n, 13, ld)
+    for dtype, td in ((binding.CHEM_F32, torch.float32), (binding.CHEM_F64_IN_F32, torch.float64)):
+        full = _run(name, T, p, Y, n, ld, dtype)
+        Td, pd, Yd = to_dev(T, td), to_dev(p, td), to_dev(Y, td)
+        cp = torch.full((ld,), float("nan"), dtype=torch.float32, device="cuda")
+        h = torch.full((ld,), float("nan"), dtype=torch.float32, device="cuda")
+        binding.props_eval(dev_mech(name), n, ld, dtype, Td, pd, Yd, cp, h, None, None, None)
+        torch.cuda.synchronize()
+        cp, h = cp.double().cpu().numpy(), h.double().cpu().numpy()
+        assert np.array_equal(cp[:n], full[0][:n]) and np.array_equal(h[:n], full[1][:n])
+        assert np.all(np.isnan(cp[n:])) and np.all(np.isnan(h[n:]))
