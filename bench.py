@@ -51,6 +51,9 @@ STIFF_OPTS = dict(rtol=1e-2, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000)
 PARITY_OPTS = dict(rtol=1e-9, atol_Y=1e-15, atol_T=1e-9, h0=1e-9, max_steps=10000)
 MECH = "c2"
 HIDDEN = {"c2": (1600, 800, 400), "c5": (2048, 1024, 512)}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the four GEMM launches of one 262,144-cell chunk
+# in the timed step (one capture of this configuration); unmeasured for other mechanisms
+GEMM_CHUNK_TRAFFIC = {"c2": 1510.9e6 + 1362.1e6}
 CELLS = {("ann", "c2"): NCELLS_ANN, ("stiff", "c2"): NCELLS, ("ann", "c5"): 16777216, ("stiff", "c5"): 1048576}
 SEED = 2002
 METRIC = "chem+props cells/s at stated dY/T error: ANN (BF16/FP8) vs stiff integrator, 1 GB300"
@@ -514,7 +517,7 @@ def bench_ann(args, rank, world, local):
         prof8 = binding.chem_prof_read()
         binding.chem_prof_enable(False)
         f8_ms = g0.elapsed_time(g1) / args.steps
-        g8 = {k: v for k, v in prof8.items() if k.startswith("gemm_tn_kernel")}
+        g8 = {k: v for k, v in prof8.items() if k.startswith("gemm_tn")}
         e8 = {k: v for k, v in g8.items() if "e4m3" in k}
         e8_ms, e8_fl = sum(v[1] for v in e8.values()), sum(v[2] for v in e8.values())
         peak8 = measured_peak("bf16_tflops", 1900.0)[0] * 2.0
@@ -536,7 +539,7 @@ def bench_ann(args, rank, world, local):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_s = float(t.item())
     value = world * ncells * args.steps / total_s
-    gemm = {k: v for k, v in prof.items() if k.startswith("gemm_tn_kernel")}
+    gemm = {k: v for k, v in prof.items() if k.startswith("gemm_tn")}
     g_ms = sum(v[1] for v in gemm.values())
     g_fl = sum(v[2] for v in gemm.values())
     peak, src = measured_peak("bf16_tflops", 1900.0)
@@ -630,7 +633,10 @@ def bench_ann(args, rank, world, local):
                          "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "data_s": t_data,
                          "train_s": t_train},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None,
+                         "traffic": GEMM_CHUNK_TRAFFIC.get(MECH),
+                         "traffic_unit": "DRAM bytes (read + write) of the four GEMM launches of one chunk of "
+                                         "262,144 cells, from one ncu capture of this configuration",
                          "kernel": "gemm_tn_kernel (all four layers; logical 2MNK flops)", "peak_source": src,
                          "per_shape": {k: {"launches": v[0], "ms": v[1],
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}

@@ -7,6 +7,14 @@
 //  - One warp per cell. Cells are popped from a device work queue (one atomic
 //    per cell), so cells with very different step counts balance across the
 //    persistent grid (one block of kWarps warps per resident slot).
+//  - Few cells (at most one per SM, e.g. the learned step's out-of-distribution
+//    cells): a team of the block's kWarps warps integrates each cell. The FP64
+//    pipe is per SM sub-partition, so a lone warp leaves three of them idle.
+//    The team splits the reaction pass (reactions over all 128 lanes) and the
+//    LU trailing updates (rows over warps); the rest runs redundantly in every
+//    warp on identical data, and one warp writes the shared results. Every
+//    value is computed by the same operations in the same order as by a lone
+//    warp, so the results are bitwise those of one warp per cell.
 //  - The state vector y = (T, Y_1..Y_N) is distributed over the lanes:
 //    component c lives in lane c % 32, register slot c / 32 (N <= 63).
 //  - Species work runs lane-per-species, reaction work lane-per-reaction; the
@@ -28,6 +36,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 4;
+constexpr size_t kSmemHeader = 16;   // the team's queue ticket, ahead of the warp slices
 
 // Rodas3 coefficients (g = 1/2 on the diagonal)
 constexpr double kGam = 0.5;
@@ -41,6 +50,17 @@ __device__ __forceinline__ double warp_sum(double v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
+
+// The warps integrating one cell: W = 1 (a lone warp) or W = kWarps (the block).
+template <int W>
+struct Team {
+    int wt;                    // rank of this warp in the team
+    __device__ __forceinline__ void sync() const {
+        if (W == 1) __syncwarp();
+        else asm volatile("bar.sync 1, %0;" ::"n"(W * 32) : "memory");
+    }
+    __device__ __forceinline__ bool lead() const { return W == 1 || wt == 0; }
+};
 
 struct Slice {                 // one warp's shared-memory slice
     double *G;                 // [n][n] Jacobian, then its LU factors
@@ -107,8 +127,9 @@ __device__ void troe_F(const double *tp, double T, double invT, double Prd, doub
 }
 
 // f = f(y) for the warp's cell. With jac, also stores what build_matrix needs.
-__device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double p, const double y[2], double f[2],
-                             bool jac) {
+template <int W>
+__device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int lane, double p, const double y[2],
+                             double f[2], bool jac) {
     const int N = m.N, R = m.R, n = N + 1;
     EvalInfo info;
     f[0] = 0.0;
@@ -119,8 +140,10 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
     info.T = T;
     info.invT = invT;
     const int rng = (T >= m.T_mid) ? 1 : 0;
-    __syncwarp();
-    // species pass: thermo and mixture sums (lane per species)
+    tm.sync();                 // every warp of the team is done reading the previous evaluation
+    // species pass: thermo and mixture sums (lane per species; in a team every warp
+    // computes them and the first writes the shared copies)
+    const bool wr = tm.lead();
     double S = 0.0, cp = 0.0, dcp = 0.0;
     double yw_s[2] = {0.0, 0.0};
     for (int s = 0; s < 2; ++s) {
@@ -140,9 +163,11 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
             yw_s[s] = yw;
             S += yw;
             cp += yw * cpR;
-            sh.HRT[k] = HRT;
-            sh.SR[k] = SR;
-            sh.cpR[k] = cpR;
+            if (wr) {
+                sh.HRT[k] = HRT;
+                sh.SR[k] = SR;
+                sh.cpR[k] = cpR;
+            }
             if (jac) dcp += yw * (a1 + T * (2.0 * a2 + T * (3.0 * a3 + T * 4.0 * a4)));
         }
     }
@@ -157,14 +182,15 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
     info.cp = cp;
     info.dcpdT = dcp;
     info.Wbar = Wbar;
-    for (int s = 0; s < 2; ++s) {
-        const int c = lane + 32 * s;
-        if (c >= 1 && c < n) sh.C[c - 1] = rho * yw_s[s];
-    }
-    __syncwarp();
-    // reaction pass (lane per reaction)
+    if (wr)
+        for (int s = 0; s < 2; ++s) {
+            const int c = lane + 32 * s;
+            if (c >= 1 && c < n) sh.C[c - 1] = rho * yw_s[s];
+        }
+    tm.sync();
+    // reaction pass (thread per reaction over the team's lanes)
     const double lnPRT = m.lnPR - lnT;
-    for (int j = lane; j < R; j += 32) {
+    for (int j = tm.wt * 32 + lane; j < R; j += 32 * W) {
         const int *re = m.reac + 3 * j;
         const int *pr = m.prod + 3 * j;
         const int r0 = __ldg(re), r1 = __ldg(re + 1), r2 = __ldg(re + 2);
@@ -238,7 +264,7 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
             }
         }
     }
-    __syncwarp();
+    tm.sync();
     // species gather: wdot_k = sum_j nu_kj q_j (reactions ascending)
     double Q = 0.0;
     const double RT = kR * T;
@@ -254,7 +280,7 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
                 if (jac) wt += (double)ent.y * sh.rdqT[ent.x];
             }
             const double Wk = __ldg(m.W + k);
-            if (jac) {
+            if (jac && wr) {
                 sh.wdot[k] = w;
                 sh.wT[k] = wt;
                 sh.U[k] = Wk * invrho;
@@ -270,8 +296,8 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, int lane, double
     return info;
 }
 
-// G = I/(h g) - J from the data of eval_rhs(..., jac = true).
-__device__ void build_matrix(const DevMech &m, const Slice &sh, int lane, const EvalInfo &in, double h) {
+// G = I/(h g) - J from the data of eval_rhs(..., jac = true), built by one warp.
+__device__ void build_matrix_warp(const DevMech &m, const Slice &sh, int lane, const EvalInfo &in, double h) {
     const int N = m.N, n = N + 1;
     double *G = sh.G;
     for (int s = 0; s < 2; ++s) {            // zero the species block (column owners)
@@ -360,8 +386,17 @@ __device__ void build_matrix(const DevMech &m, const Slice &sh, int lane, const 
     __syncwarp();
 }
 
+template <int W>
+__device__ void build_matrix(const DevMech &m, const Slice &sh, Team<W> tm, int lane, const EvalInfo &in, double h) {
+    if (tm.lead()) build_matrix_warp(m, sh, lane, in, h);
+    tm.sync();
+}
+
 // In-place LU with partial pivoting; false for a zero or non-finite pivot column.
-__device__ bool lu_factor(const Slice &sh, int lane, int n) {
+// In a team every warp searches the pivot (same data, same choice), the first
+// warp swaps and scales, and the trailing update splits the rows over the warps.
+template <int W>
+__device__ bool lu_factor(const Slice &sh, Team<W> tm, int lane, int n) {
     double *G = sh.G;
     for (int k = 0; k < n; ++k) {
         double best = -1.0;
@@ -380,55 +415,60 @@ __device__ bool lu_factor(const Slice &sh, int lane, int n) {
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
         if (!(best > 0.0) || bi >= n) return false;
-        if (lane == 0) sh.piv[k] = bi;
-        if (bi != k) {
-            for (int s = 0; s < 2; ++s) {
-                const int c = lane + 32 * s;
-                if (c < n) {
-                    const double t = G[k * n + c];
-                    G[k * n + c] = G[bi * n + c];
-                    G[bi * n + c] = t;
+        if (tm.lead()) {
+            if (lane == 0) sh.piv[k] = bi;
+            if (bi != k) {
+                for (int s = 0; s < 2; ++s) {
+                    const int c = lane + 32 * s;
+                    if (c < n) {
+                        const double t = G[k * n + c];
+                        G[k * n + c] = G[bi * n + c];
+                        G[bi * n + c] = t;
+                    }
                 }
             }
         }
-        __syncwarp();
+        tm.sync();
         const double rp = 1.0 / G[k * n + k];
-        if (lane == 0) sh.invd[k] = rp;
-        for (int s = 0; s < 2; ++s) {
-            const int i = lane + 32 * s;
-            if (i > k && i < n) G[i * n + k] *= rp;
+        if (tm.lead()) {
+            if (lane == 0) sh.invd[k] = rp;
+            for (int s = 0; s < 2; ++s) {
+                const int i = lane + 32 * s;
+                if (i > k && i < n) G[i * n + k] *= rp;
+            }
         }
-        __syncwarp();
+        tm.sync();
         for (int s = 0; s < 2; ++s) {
             const int c = lane + 32 * s;
             if (c > k && c < n) {
                 const double akc = G[k * n + c];
-                for (int i = k + 1; i < n; ++i) G[i * n + c] -= G[i * n + k] * akc;
+                for (int i = k + 1 + tm.wt; i < n; i += W) G[i * n + c] -= G[i * n + k] * akc;
             }
         }
-        __syncwarp();
+        tm.sync();
     }
     return true;
 }
 
-// b <- G^-1 b with the stored factors; b is lane-distributed.
-__device__ void lu_solve(const Slice &sh, int lane, int n, double b[2]) {
+// b <- G^-1 b with the stored factors; b is lane-distributed. bsw is this
+// warp's own permutation buffer (every warp of a team solves on its own).
+__device__ void lu_solve(const Slice &sh, double *bsw, int lane, int n, double b[2]) {
     const double *G = sh.G;
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
-        if (c < n) sh.bsw[c] = b[s];
+        if (c < n) bsw[c] = b[s];
     }
     __syncwarp();
     if (lane == 0) {
         for (int k = 0; k < n; ++k) {
             const int p = sh.piv[k];
-            if (p != k) { const double t = sh.bsw[k]; sh.bsw[k] = sh.bsw[p]; sh.bsw[p] = t; }
+            if (p != k) { const double t = bsw[k]; bsw[k] = bsw[p]; bsw[p] = t; }
         }
     }
     __syncwarp();
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
-        b[s] = (c < n) ? sh.bsw[c] : 0.0;
+        b[s] = (c < n) ? bsw[c] : 0.0;
     }
     for (int k = 0; k < n - 1; ++k) {
         const double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
@@ -451,28 +491,33 @@ __device__ void lu_solve(const Slice &sh, int lane, int n, double b[2]) {
     __syncwarp();
 }
 
-// Cells 0..ncells-1, or (list != null) the *list_count cells list[0..) of a
-// device-built queue; status of a successful cell = ok_status.
-__global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t ncells, int64_t ld, double dt,
-                                                             chem_ode_opts o, double *__restrict__ Tg,
-                                                             const double *__restrict__ pg, double *__restrict__ Yg,
-                                                             int32_t *__restrict__ status,
-                                                             int32_t *__restrict__ nsteps_out,
-                                                             unsigned int *__restrict__ queue,
-                                                             const int32_t *__restrict__ list,
-                                                             const unsigned int *__restrict__ list_count,
-                                                             int ok_status) {
-    extern __shared__ __align__(16) char smem[];
+// Integrates cells popped from the work queue until it is exhausted; W warps per cell.
+template <int W>
+__device__ void integrate_cells(const DevMech &m, char *smem, int *blk_pos, int64_t limit, int64_t ld, double dt,
+                                const chem_ode_opts &o, double *__restrict__ Tg, const double *__restrict__ pg,
+                                double *__restrict__ Yg, int32_t *__restrict__ status,
+                                int32_t *__restrict__ nsteps_out, unsigned int *__restrict__ queue,
+                                const int32_t *__restrict__ list, int ok_status) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int N = m.N, n = N + 1;
-    Slice sh = make_slice(smem + (size_t)warp * slice_bytes(N, m.R), N, m.R);
-    const int64_t limit = list ? (int64_t)(*list_count < (unsigned int)ncells ? *list_count : (unsigned int)ncells)
-                               : ncells;
+    const size_t sb = slice_bytes(N, m.R);
+    Team<W> tm{W == 1 ? 0 : warp};
+    // the team's shared data live in its first warp's slice; every warp keeps its own permutation buffer
+    Slice sh = make_slice(smem + (size_t)(W == 1 ? warp : 0) * sb, N, m.R);
+    double *bsw = make_slice(smem + (size_t)warp * sb, N, m.R).bsw;
     for (;;) {
         unsigned int pos = 0;
-        if (lane == 0) pos = atomicAdd(queue, 1u);
-        pos = __shfl_sync(kFull, pos, 0);
+        if (W == 1) {
+            if (lane == 0) pos = atomicAdd(queue, 1u);
+            pos = __shfl_sync(kFull, pos, 0);
+        } else {
+            if (tm.lead() && lane == 0) *blk_pos = (int)atomicAdd(queue, 1u);
+            tm.sync();
+            pos = (unsigned int)*blk_pos;
+            // the next write of *blk_pos comes after this cell's evaluations, whose barriers
+            // order it after every warp's read above
+        }
         if ((int64_t)pos >= limit) break;
         const int64_t cell = list ? (int64_t)list[pos] : (int64_t)pos;
         double y[2], yn[2], f0[2], K1[2], K2[2], K3[2], K4[2], ys[2], fs[2];
@@ -489,34 +534,34 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
             const double rem = dt - t;
             bool last = false;
             if (h >= rem) { h = rem; last = true; }
-            EvalInfo info = eval_rhs(m, sh, lane, p, y, f0, true);
+            EvalInfo info = eval_rhs<W>(m, sh, tm, lane, p, y, f0, true);
             bool bad = false;
             for (int s = 0; s < 2; ++s)
                 if (lane + 32 * s < n && !isfinite(f0[s])) bad = true;
             if (__any_sync(kFull, bad)) { stat = CHEM_CELL_NONFINITE; break; }
-            build_matrix(m, sh, lane, info, h);
+            build_matrix<W>(m, sh, tm, lane, info, h);
             ++nst;
-            if (!lu_factor(sh, lane, n)) { h *= 0.2; rejected_last = 1; continue; }
+            if (!lu_factor<W>(sh, tm, lane, n)) { h *= 0.2; rejected_last = 1; continue; }
             const double ih = 1.0 / h;
             // stage 1
             for (int s = 0; s < 2; ++s) K1[s] = f0[s];
-            lu_solve(sh, lane, n, K1);
+            lu_solve(sh, bsw, lane, n, K1);
             // stage 2: the stage point is y itself (a21 = 0)
             for (int s = 0; s < 2; ++s) K2[s] = f0[s] + (kC21 * ih) * K1[s];
-            lu_solve(sh, lane, n, K2);
+            lu_solve(sh, bsw, lane, n, K2);
             // stage 3: y + 2 K1
             for (int s = 0; s < 2; ++s) ys[s] = y[s] + kA31 * K1[s];
-            eval_rhs(m, sh, lane, p, ys, fs, false);
+            eval_rhs<W>(m, sh, tm, lane, p, ys, fs, false);
             for (int s = 0; s < 2; ++s) {
                 double v = fs[s];
                 v += (kC31 * ih) * K1[s];
                 v += (kC32 * ih) * K2[s];
                 K3[s] = v;
             }
-            lu_solve(sh, lane, n, K3);
+            lu_solve(sh, bsw, lane, n, K3);
             // stage 4: y + 2 K1 + K3
             for (int s = 0; s < 2; ++s) ys[s] = y[s] + kA41 * K1[s] + kA43 * K3[s];
-            eval_rhs(m, sh, lane, p, ys, fs, false);
+            eval_rhs<W>(m, sh, tm, lane, p, ys, fs, false);
             for (int s = 0; s < 2; ++s) {
                 double v = fs[s];
                 v += (kC41 * ih) * K1[s];
@@ -524,7 +569,7 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
                 v += (kC43 * ih) * K3[s];
                 K4[s] = v;
             }
-            lu_solve(sh, lane, n, K4);
+            lu_solve(sh, bsw, lane, n, K4);
             // y_new = y + 2 K1 + K3 + K4, error = K4
             double acc = 0.0;
             bool nonfinite = false;
@@ -569,15 +614,50 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
                 rejected_last = 1;
             }
         }
-        for (int s = 0; s < 2; ++s) {
-            int c = lane + 32 * s;
-            if (c == 0) Tg[cell] = y[s];
-            else if (c < n) Yg[(int64_t)(c - 1) * ld + cell] = y[s];
+        if (tm.lead()) {
+            for (int s = 0; s < 2; ++s) {
+                int c = lane + 32 * s;
+                if (c == 0) Tg[cell] = y[s];
+                else if (c < n) Yg[(int64_t)(c - 1) * ld + cell] = y[s];
+            }
+            if (lane == 0) {
+                status[cell] = (stat == CHEM_CELL_OK) ? ok_status : stat;
+                if (nsteps_out) nsteps_out[cell] = nst;
+            }
         }
-        if (lane == 0) {
-            status[cell] = (stat == CHEM_CELL_OK) ? ok_status : stat;
-            if (nsteps_out) nsteps_out[cell] = nst;
-        }
+    }
+}
+
+// Blocks that take a cell each in team mode: one per SM (the first blocks of a
+// grid are spread over the SMs), at most the grid.
+inline int team_blocks(int sms, int blocks) { return sms < blocks ? sms : blocks; }
+
+// Cells 0..ncells-1, or (list != null) the *list_count cells list[0..) of a
+// device-built queue; status of a successful cell = ok_status. When the cells
+// number at most team_blocks, the first team_blocks blocks integrate them with
+// all kWarps warps per cell and the other blocks return at once; otherwise
+// every warp takes cells of its own.
+__global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t ncells, int64_t ld, double dt,
+                                                             chem_ode_opts o, double *__restrict__ Tg,
+                                                             const double *__restrict__ pg, double *__restrict__ Yg,
+                                                             int32_t *__restrict__ status,
+                                                             int32_t *__restrict__ nsteps_out,
+                                                             unsigned int *__restrict__ queue,
+                                                             const int32_t *__restrict__ list,
+                                                             const unsigned int *__restrict__ list_count,
+                                                             int ok_status, int team_blocks) {
+    extern __shared__ __align__(16) char smem_raw[];
+    int *blk_pos = reinterpret_cast<int *>(smem_raw);
+    char *smem = smem_raw + kSmemHeader;
+    const int64_t limit = list ? (int64_t)(*list_count < (unsigned int)ncells ? *list_count : (unsigned int)ncells)
+                               : ncells;
+    if (limit <= (int64_t)team_blocks) {
+        if ((int)blockIdx.x >= team_blocks) return;
+        integrate_cells<kWarps>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue, list,
+                                ok_status);
+    } else {
+        integrate_cells<1>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue, list,
+                           ok_status);
     }
 }
 
@@ -607,7 +687,7 @@ extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, d
     std::string why;
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff: " + why);
     size_t per_warp = slice_bytes(m->N, m->R);
-    size_t smem = per_warp * kWarps;
+    size_t smem = kSmemHeader + per_warp * kWarps;
     if (smem > 227 * 1024) return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff: mechanism too large for shared memory");
     static size_t configured = 0;
     if (smem > configured) {
@@ -623,13 +703,14 @@ extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, d
     if (per_sm < 1) per_sm = 1;
     int64_t need = (ncells + kWarps - 1) / kWarps;
     int blocks = (int)((int64_t)sms * per_sm < need ? (int64_t)sms * per_sm : need);
+    if (ncells <= sms) blocks = (int)ncells;      // one block (a team of warps) per cell
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     unsigned int *queue = m->dev.counters;
     int rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "chem_step_stiff: queue reset");
     if (rc) return rc;
     void *pb = prof_begin(st);
     stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue, nullptr,
-                                                    nullptr, CHEM_CELL_OK);
+                                                    nullptr, CHEM_CELL_OK, team_blocks(sms, blocks));
     prof_end(pb, st, "stiff_kernel", 0.0, 0.0);
     return check_cuda(cudaGetLastError(), "chem_step_stiff launch");
 }
@@ -642,7 +723,7 @@ int launch_stiff_list(const chem_mech *m, int64_t capacity, int64_t ld, double d
                       const double *p, double *Y, int32_t *status, const int32_t *list, const unsigned int *count,
                       int ok_status, cudaStream_t st) {
     if (m->N > 63) return set_error(CHEM_EUNSUPPORTED, "fallback: at most 63 species");
-    size_t smem = slice_bytes(m->N, m->R) * kWarps;
+    size_t smem = kSmemHeader + slice_bytes(m->N, m->R) * kWarps;
     if (smem > 227 * 1024) return set_error(CHEM_EUNSUPPORTED, "fallback: mechanism too large for shared memory");
     int rc = check_cuda(cudaFuncSetAttribute(stiff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
                         "fallback: smem attribute");
@@ -659,7 +740,7 @@ int launch_stiff_list(const chem_mech *m, int64_t capacity, int64_t ld, double d
     rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "fallback: queue reset");
     if (rc) return rc;
     stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, capacity, ld, dt, o, T, p, Y, status, nullptr, queue, list,
-                                                    count, ok_status);
+                                                    count, ok_status, team_blocks(sms, blocks));
     return check_cuda(cudaGetLastError(), "fallback launch");
 }
 }  // namespace chemgb
@@ -736,7 +817,7 @@ extern "C" int chem_step_stiff_noalloc(const chem_mech *m, int64_t ncells, int64
     unsigned int *queue = nullptr;
     int rc = noalloc_scratch(&queue);
     if (rc) return rc;
-    size_t smem = slice_bytes(m->N, m->R) * kWarps;
+    size_t smem = kSmemHeader + slice_bytes(m->N, m->R) * kWarps;
     if (smem > 227 * 1024)
         return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff_noalloc: mechanism too large for shared memory");
     rc = check_cuda(cudaFuncSetAttribute(stiff_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
@@ -749,10 +830,11 @@ extern "C" int chem_step_stiff_noalloc(const chem_mech *m, int64_t ncells, int64
     if (per_sm < 1) per_sm = 1;
     int64_t need = (ncells + kWarps - 1) / kWarps;
     int blocks = (int)((int64_t)sms * per_sm < need ? (int64_t)sms * per_sm : need);
+    if (ncells <= sms) blocks = (int)ncells;      // one block (a team of warps) per cell
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     rc = check_cuda(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st), "chem_step_stiff_noalloc: clear queue");
     if (rc) return rc;
     stiff_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, dt, o, T, p, Y, status, nsteps, queue, nullptr,
-                                                    nullptr, CHEM_CELL_OK);
+                                                    nullptr, CHEM_CELL_OK, team_blocks(sms, blocks));
     return check_cuda(cudaGetLastError(), "chem_step_stiff_noalloc launch");
 }

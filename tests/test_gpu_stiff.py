@@ -103,3 +103,20 @@ def test_full_size_sampled(oracle):
     assert np.mean(same) > 0.8
     close = (np.abs(Tg[idx] - To) <= 1e-6 * To) & np.all(np.abs(Yg[:, idx] - Yo) <= 1e-6 * np.abs(Yo) + 1e-12, axis=0)
     assert np.mean(close[same]) > 0.9
+
+
+@pytest.mark.parametrize("name", ["c2", "c5"])
+def test_team_mode_is_bitwise_warp_mode(name):
+    # up to one cell per SM, a team of warps integrates each cell; the results are bitwise those
+    # of one warp per cell (the same operations in the same order), for every status and step count
+    m = synth.get_mech(name)
+    n_big = 2000
+    T, p, Y = synth.states_profiles(m, n_big, 31, synth.padded_ld(n_big))
+    for opts in (PARITY, dict(rtol=1e-2, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000),
+                 dict(rtol=1e-6, atol_Y=1e-12, atol_T=1e-6, h0=1e-9, max_steps=3)):
+        Tw, Yw, sw, nw = _gpu(name, T, p, Y, n_big, T.shape[0], **opts)        # warps
+        n = 100
+        Tt, Yt, st, nt = _gpu(name, T, p, Y, n, T.shape[0], **opts)            # teams
+        assert np.array_equal(st[:n], sw[:n]) and np.array_equal(nt[:n], nw[:n])
+        assert np.array_equal(Tt[:n], Tw[:n]) and np.array_equal(Yt[:, :n], Yw[:, :n])
+        assert np.array_equal(Tt[n:], T[n:])                                   # cells past n untouched
