@@ -390,7 +390,7 @@ def bench_ann(args, rank, world, local):
     N = smech.N
     hidden = HIDDEN[MECH]
     # ---- training (untimed): GPU stiff pairs, statistics, Adam on Eq. 5
-    net = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3003, chunk=262144, max_batch=4096)
+    net = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3003, chunk=args.chunk, max_batch=4096)
     fp8 = not args.untrained and not args.no_fp8
     if args.untrained:
         t_data = t_train = 0.0
@@ -412,7 +412,7 @@ def bench_ann(args, rank, world, local):
             binding.chem_mlp_calibrate_fp8(net, min(data.n, 262144), data.ld, data.T, data.p, data.Y)
         del data
     fb_opts = binding.make_opts(**STIFF_OPTS)
-    tiles = binding.chem_mlp_autotune(net, 262144)
+    tiles = binding.chem_mlp_autotune(net, min(args.chunk, 524288))
     # ---- inference workload
     ncells = args.cells
     T, p, Y = synth.states_profiles(smech, ncells, 2003 + 1000 * rank, ld=synth.padded_ld(ncells))
@@ -614,7 +614,7 @@ def bench_ann(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value = world * ncells * e2e_steps / (e0.elapsed_time(e1) / 1e3)
-    chunks = (ncells + 262143) // 262144
+    chunks = (ncells + args.chunk - 1) // args.chunk
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
@@ -690,6 +690,8 @@ def main():
     ap.add_argument("--mech", default=MECH, choices=sorted(HIDDEN),
                     help="mechanism (c2: 30 species, MLP 1600/800/400; c5: 53 species, MLP 2048/1024/512)")
     ap.add_argument("--no-fp8", action="store_true", help="skip the E4M3 variant of the learned step")
+    ap.add_argument("--chunk", type=int, default=262144,
+                    help="cells per inference chunk of the network (sets the activation workspace)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=None,
                     help="cells per GPU (default 4,194,304 for ann, 2,097,152 for stiff); smaller values only for "

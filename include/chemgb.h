@@ -194,9 +194,13 @@ int chem_step_stiff_noalloc(const chem_mech *mech, int64_t ncells, int64_t ld, d
  * x: [M][ldx] BF16, W: [N][ldw] BF16 (row n = output n), b: [N] float or NULL,
  * y: [M][ldy]. ldx and ldw must make rows a multiple of 16 bytes and the bases
  * 16-byte aligned. tile_n selects the output tile width (32, 64, 128, 160, 208
- * or 256; 0 = automatic). err (device int, may be NULL) receives a non-zero
+ * or 256; 0 = automatic); adding CHEM_TILE_PAIR (widths 128, 160, 208, 256)
+ * selects the two-CTA variant, in which a cluster of two CTAs computes
+ * 256-row tiles with one tensor-core instruction stream (each CTA holds half
+ * of the weight tile). err (device int, may be NULL) receives a non-zero
  * code if a pipeline wait timed out (the call then returns without a result).
  */
+#define CHEM_TILE_PAIR 0x10000
 int chem_dense_bf16(int64_t M, int N, int K, const void *x, int64_t ldx, const void *W, int64_t ldw,
                     const float *b, int act, void *y, int64_t ldy, int tile_n, int *err, chem_stream_t stream);
 
@@ -293,7 +297,8 @@ int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
  * compiled output-tile width of the tensor-core GEMM on `rows` rows of the
  * inference workspace (CUDA events, the first launch discarded) and keeps the
  * fastest for chem_step_ann / chem_mlp_forward. tiles_out[4] (host, may be
- * NULL) receives the choice. Synchronises the stream; results are bitwise
+ * NULL) receives the choice.
+ * Synchronises the stream; results are bitwise
  * the same for every tile width. */
 int chem_mlp_autotune(chem_mlp *mlp, int64_t rows, int32_t *tiles_out, chem_stream_t stream);
 /* Sticky error word of the network's pipeline waits (0 = none); synchronises the device. */

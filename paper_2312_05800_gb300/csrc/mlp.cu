@@ -1403,9 +1403,12 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
         const int64_t ldx = (l == 0) ? 2 * m->n_in_pad : m->L[l - 1].out;
         float best = 3.4e38f;
         int best_bn = L.tile;
-        for (int bn : kTileWidths) {
-            if (bn < 64 && L.out > 64) continue;
-            if (bn > 2 * ((L.out + 15) / 16) * 16 && bn > 64) continue;   // tiles far wider than the layer
+        // the two-CTA variant is not a candidate: measured on GB300 it runs at half the single-CTA rate
+        const std::vector<int> codes(std::begin(kTileWidths), std::end(kTileWidths));
+        for (int bn : codes) {
+            const int w = bn & 0xFFFF;
+            if (w < 64 && L.out > 64) continue;
+            if (w > 2 * ((L.out + 15) / 16) * 16 && w > 64) continue;   // tiles far wider than the layer
             float ms_sum = 0.0f;
             for (int rep = 0; rep < 4 && !rc; ++rep) {
                 rc = check_cuda(cudaEventRecord(e0, st), "autotune record");

@@ -32,7 +32,7 @@ __device__ __forceinline__ void load4(const real *p, real &a, real &b, real &c, 
 }
 
 // FP32 tables always fit (8 N Np floats <= 131 KB for N <= 64); FP64 tables stay in global memory.
-constexpr size_t kPropsSmemMax = 8 * 64 * 64 * 4;
+constexpr size_t kPropsSmemMax = (8 * 64 * 64 + 28 * 64) * 4;
 template <typename real>
 __host__ __device__ constexpr bool tables_in_smem() { return sizeof(real) == 4; }
 
@@ -44,6 +44,19 @@ __device__ __forceinline__ void stage_pair_tables(const PropTables<real> &tb, in
     const int nw = 3 * N * Np, nd = 5 * N * Np;
     for (int e = threadIdx.x; e < nw; e += blockDim.x) sh[e] = tb.wilke[e];
     for (int e = threadIdx.x; e < nd; e += blockDim.x) sh[nw + e] = tb.diff[e];
+    __syncthreads();
+}
+
+// Per-species coefficient rows (NASA cp and h of both ranges, the ln(mu) fit, 1/W) in
+// the global tables' own layout, copied to shared memory after the pair tables so
+// that the species loops read them as broadcasts.
+constexpr int kSpeciesFloats = 2 * 5 + 2 * 6 + 5 + 1;   // floats per species
+template <typename real>
+__device__ __forceinline__ void stage_species_tables(const PropTables<real> &tb, int N, real *sh) {
+    for (int e = threadIdx.x; e < 10 * N; e += blockDim.x) sh[e] = tb.nasa_cp[e];
+    for (int e = threadIdx.x; e < 12 * N; e += blockDim.x) sh[10 * N + e] = tb.nasa_h[e];
+    for (int e = threadIdx.x; e < 5 * N; e += blockDim.x) sh[22 * N + e] = tb.visc[e];
+    for (int e = threadIdx.x; e < N; e += blockDim.x) sh[27 * N + e] = tb.invW[e];
     __syncthreads();
 }
 
@@ -79,8 +92,14 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
     real *shtab = reinterpret_cast<real *>(props_smem);
     constexpr bool in_smem = tables_in_smem<real>();
     if (in_smem && transport) stage_pair_tables(tb, N, Np, shtab);
+    real *sp = shtab + (transport ? 8 * N * Np : 0);
+    if (in_smem) stage_species_tables(tb, N, sp);
     const real *wil = in_smem ? shtab : tb.wilke;
     const real *dif = in_smem ? shtab + 3 * N * Np : tb.diff;
+    const real *t_cp = in_smem ? sp : tb.nasa_cp;
+    const real *t_h = in_smem ? sp + 10 * N : tb.nasa_h;
+    const real *t_visc = in_smem ? sp + 22 * N : tb.visc;
+    const real *t_iw = in_smem ? sp + 27 * N : tb.invW;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
         const real T = to_real<real>(Tg[i]);
@@ -94,20 +113,20 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
         for (int k = 0; k < NMAX; ++k) {
             if (k < N) {
                 const real y = to_real<real>(Yg[(int64_t)k * ld + i]);
-                const real iw = __ldg(tb.invW + k);
-                const real *a = tb.nasa_cp + (rng * N + k) * 5;
-                const real *b = tb.nasa_h + (rng * N + k) * 6;
-                real cpR = __ldg(a + 4);
-                cpR = fma(cpR, T, __ldg(a + 3));
-                cpR = fma(cpR, T, __ldg(a + 2));
-                cpR = fma(cpR, T, __ldg(a + 1));
-                cpR = fma(cpR, T, __ldg(a + 0));
-                real hR = __ldg(b + 4);
-                hR = fma(hR, T, __ldg(b + 3));
-                hR = fma(hR, T, __ldg(b + 2));
-                hR = fma(hR, T, __ldg(b + 1));
-                hR = fma(hR, T, __ldg(b + 0));
-                hR = hR + __ldg(b + 5) / T;                      // H_k / (R T)
+                const real iw = t_iw[k];
+                const real *a = t_cp + (rng * N + k) * 5;
+                const real *b = t_h + (rng * N + k) * 6;
+                real cpR = a[4];
+                cpR = fma(cpR, T, a[3]);
+                cpR = fma(cpR, T, a[2]);
+                cpR = fma(cpR, T, a[1]);
+                cpR = fma(cpR, T, a[0]);
+                real hR = b[4];
+                hR = fma(hR, T, b[3]);
+                hR = fma(hR, T, b[2]);
+                hR = fma(hR, T, b[1]);
+                hR = fma(hR, T, b[0]);
+                hR = hR + b[5] / T;                              // H_k / (R T)
                 const real yw = y * iw;
                 S += yw;
                 cpm = fma(yw, cpR, cpm);
@@ -124,12 +143,12 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
             if (k < N) {
-                const real *c = tb.visc + k * 5;
-                real lm = __ldg(c + 4);
-                lm = fma(lm, x, __ldg(c + 3));
-                lm = fma(lm, x, __ldg(c + 2));
-                lm = fma(lm, x, __ldg(c + 1));
-                lm = fma(lm, x, __ldg(c + 0));
+                const real *c = t_visc + k * 5;
+                real lm = c[4];
+                lm = fma(lm, x, c[3]);
+                lm = fma(lm, x, c[2]);
+                lm = fma(lm, x, c[1]);
+                lm = fma(lm, x, c[0]);
                 const real ir = exp(real(-0.5) * lm);              // 1 / sqrt(mu_k)
                 X[k] = X[k] * Wbar;
                 xr[k] = X[k] * ir;
@@ -141,25 +160,28 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
         }
         const real T15 = T * sqrt(T);
         real mu = 0, lam = 0;
+        real y_next = to_real<real>(Yg[i]);
         for (int k = 0; k < N; ++k) {
-            // per-species values, recomputed from the tables (no dynamic register indexing)
-            const real y = real(Yg[(int64_t)k * ld + i]);
-            const real iw = __ldg(tb.invW + k);
+            // per-species values, recomputed from the tables (no dynamic register indexing);
+            // the next species' mass fraction is loaded one iteration ahead
+            const real y = y_next;
+            if (k + 1 < N) y_next = to_real<real>(Yg[(int64_t)(k + 1) * ld + i]);
+            const real iw = t_iw[k];
             const real Xk = y * iw * Wbar;
-            const real *c = tb.visc + k * 5;
-            real lm = __ldg(c + 4);
-            lm = fma(lm, x, __ldg(c + 3));
-            lm = fma(lm, x, __ldg(c + 2));
-            lm = fma(lm, x, __ldg(c + 1));
-            lm = fma(lm, x, __ldg(c + 0));
+            const real *c = t_visc + k * 5;
+            real lm = c[4];
+            lm = fma(lm, x, c[3]);
+            lm = fma(lm, x, c[2]);
+            lm = fma(lm, x, c[1]);
+            lm = fma(lm, x, c[0]);
             const real muk = exp(lm);
             const real rk = sqrt(muk);
-            const real *a = tb.nasa_cp + (rng * N + k) * 5;
-            real cpR = __ldg(a + 4);
-            cpR = fma(cpR, T, __ldg(a + 3));
-            cpR = fma(cpR, T, __ldg(a + 2));
-            cpR = fma(cpR, T, __ldg(a + 1));
-            cpR = fma(cpR, T, __ldg(a + 0));
+            const real *a = t_cp + (rng * N + k) * 5;
+            real cpR = a[4];
+            cpR = fma(cpR, T, a[3]);
+            cpR = fma(cpR, T, a[2]);
+            cpR = fma(cpR, T, a[1]);
+            cpR = fma(cpR, T, a[0]);
             const real lamk = muk * (cpR + real(1.25)) * R * iw;   // Eucken
             const real *t0 = wil + (0 * N + k) * Np;
             const real *t1 = wil + (1 * N + k) * Np;
@@ -221,12 +243,16 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 }
 
 // Thermo only (cp and h; the memory-bound part of props_eval), FP32 arithmetic.
-// One thread per cell in a grid-stride loop at full occupancy, so that enough
-// loads are in flight to keep HBM busy; the NASA-7 rows of both ranges and 1/W
-// are staged in shared memory (3 float4 per species and range). The arithmetic
-// is that of props_kernel's first pass, so cp and h are bitwise the same.
-template <typename in_t>
-__global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTables<float> tb, int64_t ncells,
+// One thread per cell in a grid-stride loop. The mass fractions are loaded in
+// groups of kThermoGroup species ahead of their arithmetic, so each thread keeps
+// that many loads in flight at full occupancy and HBM stays busy; the
+// NASA-7 rows of both ranges and 1/W are staged in shared memory (3 float4 per
+// species and range). The arithmetic is that of props_kernel's first pass, so
+// cp and h are bitwise the same.
+constexpr int kThermoGroup = 8;
+
+template <typename in_t, int NMAX>
+__global__ void __launch_bounds__(256, 5) thermo_kernel(int N, float T_mid, PropTables<float> tb, int64_t ncells,
                                                      int64_t ld, const in_t *__restrict__ Tg,
                                                      const in_t *__restrict__ Yg, float *__restrict__ cpg,
                                                      float *__restrict__ hg) {
@@ -246,55 +272,74 @@ __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTab
         const float T = to_real<float>(Tg[i]);
         const float4 *tab = th_tab + ((T >= T_mid) ? 3 * N : 0);
         float cpm = 0.0f, hm = 0.0f;
-#pragma unroll 4
-        for (int k = 0; k < N; ++k) {
-            const float y = to_real<float>(Yg[(int64_t)k * ld + i]);
-            const float4 q0 = tab[3 * k], q1 = tab[3 * k + 1], q2 = tab[3 * k + 2];
-            float cpR = q1.x;
-            cpR = fmaf(cpR, T, q0.w);
-            cpR = fmaf(cpR, T, q0.z);
-            cpR = fmaf(cpR, T, q0.y);
-            cpR = fmaf(cpR, T, q0.x);
-            float hR = q2.y;
-            hR = fmaf(hR, T, q2.x);
-            hR = fmaf(hR, T, q1.w);
-            hR = fmaf(hR, T, q1.z);
-            hR = fmaf(hR, T, q1.y);
-            hR = hR + q2.z / T;
-            const float yw = y * q2.w;
-            cpm = fmaf(yw, cpR, cpm);
-            hm = fmaf(yw, hR, hm);
+#pragma unroll 1
+        for (int k0 = 0; k0 < NMAX; k0 += kThermoGroup) {
+            if (k0 >= N) break;
+            float y[kThermoGroup];
+#pragma unroll
+            for (int u = 0; u < kThermoGroup; ++u)
+                y[u] = (k0 + u < N) ? to_real<float>(Yg[(int64_t)(k0 + u) * ld + i]) : 0.0f;
+#pragma unroll
+            for (int u = 0; u < kThermoGroup; ++u) {
+                const int k = k0 + u;
+                if (k >= N) break;
+                const float4 q0 = tab[3 * k], q1 = tab[3 * k + 1], q2 = tab[3 * k + 2];
+                float cpR = q1.x;
+                cpR = fmaf(cpR, T, q0.w);
+                cpR = fmaf(cpR, T, q0.z);
+                cpR = fmaf(cpR, T, q0.y);
+                cpR = fmaf(cpR, T, q0.x);
+                float hR = q2.y;
+                hR = fmaf(hR, T, q2.x);
+                hR = fmaf(hR, T, q1.w);
+                hR = fmaf(hR, T, q1.z);
+                hR = fmaf(hR, T, q1.y);
+                hR = hR + q2.z / T;
+                const float yw = y[u] * q2.w;
+                cpm = fmaf(yw, cpR, cpm);
+                hm = fmaf(yw, hR, hm);
+            }
         }
         if (cpg) cpg[i] = cpm * R;
         if (hg) hg[i] = hm * R * T;
     }
 }
 
-template <typename in_t>
+template <typename in_t, int NMAX>
 int launch_thermo(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *Y, void *cp, void *h,
                   cudaStream_t st) {
     const size_t smem = (size_t)6 * m->N * sizeof(float4);
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_kernel<in_t>, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_kernel<in_t, NMAX>, 256, smem);
     const int64_t max_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     const int64_t need = (ncells + 255) / 256;
     const int blocks = (int)(need < max_blocks ? need : max_blocks);
     void *pb = prof_begin(st);
-    thermo_kernel<in_t><<<blocks, 256, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,
-                                                   static_cast<const in_t *>(T), static_cast<const in_t *>(Y),
-                                                   static_cast<float *>(cp), static_cast<float *>(h));
+    thermo_kernel<in_t, NMAX><<<blocks, 256, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,
+                                                         static_cast<const in_t *>(T), static_cast<const in_t *>(Y),
+                                                         static_cast<float *>(cp), static_cast<float *>(h));
     prof_end(pb, st, "thermo_kernel", (double)ncells * 24.0 * m->N,
              (double)ncells * ((m->N + 1) * sizeof(in_t) + 2 * sizeof(float)));
     return check_cuda(cudaGetLastError(), "props_eval (thermo) launch");
+}
+
+template <typename in_t>
+int dispatch_thermo(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *Y, void *cp, void *h,
+                    cudaStream_t st) {
+    if (m->N <= 16) return launch_thermo<in_t, 16>(m, ncells, ld, T, Y, cp, h, st);
+    if (m->N <= 32) return launch_thermo<in_t, 32>(m, ncells, ld, T, Y, cp, h, st);
+    return launch_thermo<in_t, 64>(m, ncells, ld, T, Y, cp, h, st);
 }
 
 template <typename real, typename in_t, int NMAX>
 int launch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
                  void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
     const bool transport = mu || lam || Dk;
-    const size_t smem = (transport && tables_in_smem<real>()) ? (size_t)8 * m->N * m->dev.Np * sizeof(real) : 0;
+    const size_t smem = tables_in_smem<real>() ? ((transport ? (size_t)8 * m->N * m->dev.Np : 0) +
+                                                  (size_t)kSpeciesFloats * m->N) * sizeof(real)
+                                               : 0;
     static size_t configured = 0;
     if (smem > configured) {
         int rc = check_cuda(cudaFuncSetAttribute(props_kernel<real, in_t, NMAX>,
@@ -327,7 +372,7 @@ template <typename real, typename in_t>
 int dispatch_props(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *p, const void *Y,
                    void *cp, void *h, void *mu, void *lam, void *Dk, cudaStream_t st) {
     if constexpr (sizeof(real) == 4) {
-        if (!mu && !lam && !Dk) return launch_thermo<in_t>(m, ncells, ld, T, Y, cp, h, st);
+        if (!mu && !lam && !Dk) return dispatch_thermo<in_t>(m, ncells, ld, T, Y, cp, h, st);
     }
     if (m->N <= 16) return launch_props<real, in_t, 16>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
     if (m->N <= 32) return launch_props<real, in_t, 32>(m, ncells, ld, T, p, Y, cp, h, mu, lam, Dk, st);
