@@ -446,8 +446,8 @@ def bench_ann(args, rank, world, local):
     def step(st=stream, prec=binding.CHEM_PREC_BF16):
         Tw.copy_(T0)
         Yw.copy_(Y0)
-        binding.chem_step_ann(dm, net, ncells, ld, DT, prec, fb_opts, Tw, p0, Yw, status, st)
-        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, st)
+        binding.chem_step_ann_props(dm, net, ncells, ld, DT, prec, fb_opts, Tw, p0, Yw, status, cp, hh, mu, lam, Dk,
+                                    st)
 
     for _ in range(args.warmup):
         step()
@@ -564,8 +564,8 @@ def bench_ann(args, rank, world, local):
     torch.cuda.synchronize()
     binding.chem_prof_enable(True)
     e0.record(stream)
-    binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, stream)
-    binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+    binding.chem_step_ann_props(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, cp, hh,
+                                mu, lam, Dk, stream)
     e1.record(stream)
     torch.cuda.synchronize()
     prof4 = binding.chem_prof_read()
@@ -603,8 +603,8 @@ def bench_ann(args, rank, world, local):
         Tw.copy_(Th, non_blocking=True)
         p0.copy_(ph, non_blocking=True)
         Yw.copy_(Yh, non_blocking=True)
-        binding.chem_step_ann(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, stream)
-        binding.props_eval(dm, ncells, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
+        binding.chem_step_ann_props(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, cp,
+                                    hh, mu, lam, Dk, stream)
         Tout.copy_(Tw, non_blocking=True)
         Yout.copy_(Yw, non_blocking=True)
         sout.copy_(status, non_blocking=True)
@@ -619,8 +619,9 @@ def bench_ann(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": ann_workload(smech),
-                       "path": "chem_step_ann (BF16 tcgen05 GEMMs, FP32 accumulation; out-of-distribution cells to "
-                               "the FP64 stiff integrator) + props_eval (FP32)",
+                       "path": "chem_step_ann_props: BF16 tcgen05 GEMMs (FP32 accumulation); out-of-distribution "
+                               "cells to the FP64 stiff integrator; FP32 properties of the advanced state, run "
+                               "beside the fallback",
                        "cells_per_gpu": ncells, "l2": "inputs larger than L2 (1 GB FP64 state)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_throughput_setting_vs_tight_stiff": acc_stiff,
@@ -652,7 +653,7 @@ def bench_ann(args, rank, world, local):
             "fp8": fp8_line,
             "props_thermo": props_thermo,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (chunks * 6 + 1),
+            "gpu_launches": args.steps * (chunks * 6 + 3),
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ann(smech, T, p, Y)
@@ -690,7 +691,7 @@ def main():
     ap.add_argument("--mech", default=MECH, choices=sorted(HIDDEN),
                     help="mechanism (c2: 30 species, MLP 1600/800/400; c5: 53 species, MLP 2048/1024/512)")
     ap.add_argument("--no-fp8", action="store_true", help="skip the E4M3 variant of the learned step")
-    ap.add_argument("--chunk", type=int, default=262144,
+    ap.add_argument("--chunk", type=int, default=2097152,
                     help="cells per inference chunk of the network (sets the activation workspace)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=None,

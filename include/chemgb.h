@@ -352,6 +352,16 @@ int chem_step_ann(const chem_mech *mech, const chem_mlp *mlp, int64_t ncells, in
                   const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
                   chem_stream_t stream);
 
+/* chem_step_ann followed by the properties of the advanced state (Sec. 2: the
+ * per-cell thermal and transport properties the flow solver needs next), with
+ * the same results as chem_step_ann then props_eval(CHEM_F64_IN_F32): cp, h,
+ * mu, lambda [ld] and Dk [N][ld] (float, device, each may be NULL; 16-byte
+ * aligned), in one call on the caller's stream. Errors as chem_step_ann and
+ * props_eval. */
+int chem_step_ann_props(const chem_mech *mech, const chem_mlp *mlp, int64_t ncells, int64_t ld, double dt, int prec,
+                        const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
+                        float *cp, float *h, float *mu, float *lambda, float *Dk, chem_stream_t stream);
+
 /* ---------------------------------------------------------------------------
  * mlp_train_step -- one Adam step on the L1 loss of Eq. 5
  * ---------------------------------------------------------------------------

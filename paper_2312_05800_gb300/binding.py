@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_save.argtypes = [vp, ctypes.c_char_p]
     L.chem_mlp_load.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
     L.chem_step_ann.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp]
+    L.chem_step_ann_props.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp,
+                                      vp, vp, vp, vp, vp, vp]
     L.mlp_train_step.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, ctypes.c_float, vp, vp]
     L.chem_prof_enable.argtypes = [i32]
     L.chem_prof_read.argtypes = [ctypes.c_char_p, i64]
@@ -359,6 +361,14 @@ def chem_step_ann(mech: Mech, mlp: Mlp, ncells: int, ld: int, dt: float, prec: i
     _check(lib().chem_step_ann(mech.handle, mlp.handle, ncells, ld, float(dt), prec,
                                ctypes.byref(fallback) if fallback is not None else None, _ptr(T), _ptr(p), _ptr(Y),
                                _ptr(status), _stream(stream)))
+
+
+def chem_step_ann_props(mech: Mech, mlp: Mlp, ncells: int, ld: int, dt: float, prec: int, fallback, T, p, Y,
+                        status=None, cp=None, h=None, mu=None, lam=None, Dk=None, stream=None):
+    _check(lib().chem_step_ann_props(mech.handle, mlp.handle, ncells, ld, float(dt), prec,
+                                     ctypes.byref(fallback) if fallback is not None else None, _ptr(T), _ptr(p),
+                                     _ptr(Y), _ptr(status), _ptr(cp), _ptr(h), _ptr(mu), _ptr(lam), _ptr(Dk),
+                                     _stream(stream)))
 
 
 def mlp_train_step(mlp: Mlp, batch: int, idx, ld: int, T, p, Y, Y1, lr: float, loss=None, stream=None):

@@ -18,6 +18,8 @@ namespace chemgb {
 int launch_stiff_list(const chem_mech *m, int64_t capacity, int64_t ld, double dt, const chem_ode_opts &o, double *T,
                       const double *p, double *Y, int32_t *status, const int32_t *list, const unsigned int *count,
                       int ok_status, cudaStream_t st);
+int props_f64_in_f32(const chem_mech *m, int64_t ncells, int64_t ld, const double *T, const double *p,
+                     const double *Y, float *cp, float *h, float *mu, float *lam, float *Dk, cudaStream_t st);
 }
 
 namespace chemgb {
@@ -691,6 +693,8 @@ int check_prec(const chem_mlp *m, int prec, const char *who) {
 
 using namespace chemgb;
 
+extern "C" int chem_mlp_free(chem_mlp *m);
+
 extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc, uint64_t seed, chem_mlp **out) {
     if (!mech || !desc || !out) return set_error(CHEM_EINVAL, "chem_mlp_create: null argument");
     *out = nullptr;
@@ -816,7 +820,10 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     if (!rc) rc = upload_norm(m);
     if (!rc) rc = refresh_bf16(m, 0);
     if (!rc) rc = check_cuda(cudaDeviceSynchronize(), "chem_mlp_create");
-    if (rc) { cudaFree(blob); delete m; return rc; }
+    if (rc) {
+        chem_mlp_free(m);
+        return rc;
+    }
     *out = m;
     return CHEM_OK;
 }
@@ -1005,26 +1012,37 @@ extern "C" int chem_mlp_get_fp8_weights(const chem_mlp *m, int layer, uint8_t *W
     return rc;
 }
 
-extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int64_t ld, double dt, int prec,
-                             const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
-                             chem_stream_t stream) {
-    (void)fallback;
-    if (!mech || !m) return set_error(CHEM_EINVAL, "chem_step_ann: null handle");
+namespace chemgb {
+namespace {
+
+// FP32 property outputs of the fused entry point (all null: none)
+struct PropsOut {
+    float *cp, *h, *mu, *lam, *Dk;
+    bool any() const { return cp || h || mu || lam || Dk; }
+};
+
+int step_ann_impl(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int64_t ld, double dt, int prec,
+                  const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
+                  const PropsOut &po, chem_stream_t stream, const char *who) {
+    if (!mech || !m) return set_error(CHEM_EINVAL, std::string(who) + ": null handle");
     if (mech->N != m->N || mech->bath != m->bath)
-        return set_error(CHEM_EINVAL, "chem_step_ann: network and mechanism disagree on the species");
+        return set_error(CHEM_EINVAL, std::string(who) + ": network and mechanism disagree on the species");
     if (!(std::fabs(dt - m->dt) <= 1e-12 * m->dt))
-        return set_error(CHEM_EINVAL, "chem_step_ann: dt differs from the step the network was trained for");
-    int rc = check_state_args(ncells, ld, T, p, Y, "chem_step_ann");
+        return set_error(CHEM_EINVAL, std::string(who) + ": dt differs from the step the network was trained for");
+    int rc = check_state_args(ncells, ld, T, p, Y, who);
     if (rc) return rc;
-    if ((rc = check_prec(m, prec, "chem_step_ann"))) return rc;
+    if ((rc = check_prec(m, prec, who))) return rc;
     if (ncells == 0) return CHEM_OK;
-    if (status && !aligned16(status)) return set_error(CHEM_EINVAL, "chem_step_ann: status must be 16-byte aligned");
+    if (status && !aligned16(status)) return set_error(CHEM_EINVAL, std::string(who) + ": status must be 16-byte aligned");
+    const void *outs[] = {po.cp, po.h, po.mu, po.lam, po.Dk};
+    for (const void *q : outs)
+        if (q && !aligned16(q)) return set_error(CHEM_EINVAL, std::string(who) + ": outputs must be 16-byte aligned");
     std::string why;
-    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_step_ann: " + why);
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, std::string(who) + ": " + why);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (m->ood_enabled && !status && ncells > m->chunk)
-        return set_error(CHEM_EINVAL, "chem_step_ann: with the out-of-distribution guard, calls of more than one "
-                                      "chunk need a status array");
+        return set_error(CHEM_EINVAL, std::string(who) + ": with the out-of-distribution guard, calls of more than "
+                                                          "one chunk need a status array");
     const int64_t qcap = m->chunk > kFallbackQueue ? m->chunk : kFallbackQueue;
     chem_ode_opts fo;
     chem_ode_opts_default(&fo);
@@ -1078,7 +1096,30 @@ extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t n
         rc = check_cuda(cudaGetLastError(), "chem_step_ann epilogue");
         if (rc) return rc;
     }
-    return flush(flush_base);
+    rc = flush(flush_base);
+    if (rc || !po.any()) return rc;
+    // the properties of the advanced state, after the fallback. (Run beside the fallback on a
+    // second stream, they took the issue slots its latency-bound FP64 warps need: measured on
+    // GB300, the fallback slowed from 5.5 to 10.8 ms while the properties saved 4 ms.)
+    return props_f64_in_f32(mech, ncells, ld, T, p, Y, po.cp, po.h, po.mu, po.lam, po.Dk, st);
+}
+
+}  // namespace
+}  // namespace chemgb
+
+extern "C" int chem_step_ann(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int64_t ld, double dt, int prec,
+                             const chem_ode_opts *fallback, double *T, const double *p, double *Y, int32_t *status,
+                             chem_stream_t stream) {
+    return step_ann_impl(mech, m, ncells, ld, dt, prec, fallback, T, p, Y, status,
+                         PropsOut{nullptr, nullptr, nullptr, nullptr, nullptr}, stream, "chem_step_ann");
+}
+
+extern "C" int chem_step_ann_props(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int64_t ld, double dt,
+                                   int prec, const chem_ode_opts *fallback, double *T, const double *p, double *Y,
+                                   int32_t *status, float *cp, float *h, float *mu, float *lambda, float *Dk,
+                                   chem_stream_t stream) {
+    return step_ann_impl(mech, m, ncells, ld, dt, prec, fallback, T, p, Y, status,
+                         PropsOut{cp, h, mu, lambda, Dk}, stream, "chem_step_ann_props");
 }
 
 extern "C" int chem_mlp_fit_ood(chem_mlp *m, const chem_mech *mech, int64_t n, int64_t ld, const double *T,

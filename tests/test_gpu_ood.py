@@ -76,3 +76,38 @@ def test_fallback_cells_take_the_stiff_result(oracle):
                                  atol_Y=1e-13, atol_T=1e-6, max_steps=20000)
     assert np.all(np.abs(Tg[idx] - To) <= 1e-4 * To)
     net.free()
+
+
+@pytest.mark.parametrize("transport", [True, False])
+def test_fused_step_and_properties(transport):
+    # chem_step_ann_props == chem_step_ann then props_eval(CHEM_F64_IN_F32), bitwise: the state, the
+    # status and every property, with fallback cells integrated while the other cells' properties run
+    # (several chunks, the fallback queue spanning them, ragged tail)
+    import torch
+    from paper_2312_05800_gb300 import binding
+    m, net, _, (T2, pe, Y2, ne, moved) = _setup(ntr=60000, ne=20001)
+    ld = T2.shape[0]
+    opts = binding.make_opts(rtol=1e-2, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000)
+    dm = dev_mech("c2")
+    res = []
+    for fused in (False, True):
+        Td, pd, Yd = to_dev(T2), to_dev(pe), to_dev(Y2)
+        st = torch.full((ld,), -1, dtype=torch.int32, device="cuda")
+        outs = [torch.full((ld,), float("nan"), dtype=torch.float32, device="cuda") for _ in range(4)]
+        Dk = torch.full((m.N, ld), float("nan"), dtype=torch.float32, device="cuda")
+        if not transport:
+            outs[2] = outs[3] = Dk = None
+        args = outs + [Dk]
+        if fused:
+            binding.chem_step_ann_props(dm, net, ne, ld, 1e-6, binding.CHEM_PREC_BF16, opts, Td, pd, Yd, st, *args)
+        else:
+            binding.chem_step_ann(dm, net, ne, ld, 1e-6, binding.CHEM_PREC_BF16, opts, Td, pd, Yd, st)
+            binding.props_eval(dm, ne, ld, binding.CHEM_F64_IN_F32, Td, pd, Yd, *args)
+        torch.cuda.synchronize()
+        res.append([x.cpu().numpy() if x is not None else None for x in [Td, Yd, st] + args])
+    s = res[0][2][:ne]
+    assert (s == binding.CELL_FALLBACK).sum() > 20 and np.all((s == 0) | (s == binding.CELL_FALLBACK))
+    for a, b in zip(res[0], res[1]):
+        if a is not None:
+            assert np.array_equal(a, b, equal_nan=True)
+    net.free()
