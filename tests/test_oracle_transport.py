@@ -2,7 +2,9 @@
 properties per cell; Sec. 3.1 names the Hirschfelder-Curtiss model).
 
 Wilke's mixing rule reduces to the pure-species value; two species with equal
-W and viscosity mix to that viscosity; the binary mixture-averaged diffusion
+W and viscosity mix to that viscosity; the off-diagonal Wilke weights, recovered
+from binary-mixture viscosities, obey Wilke's reciprocity and reproduce the
+conductivity, which mixes with the same weights; the binary mixture-averaged diffusion
 coefficient has a closed form in the binary coefficient; D scales as 1/p while
 mu and lambda do not depend on p; and the fitted species values stay within the
 fit residual of the raw Chapman-Enskog expressions the fits were made from.
@@ -92,3 +94,27 @@ def test_fits_follow_chapman_enskog(oracle):
         P * np.pi * sjk ** 2 * synth._omega11(Ts / ejk))
     Dfit = Ts ** 1.5 / (P * _polyval(m.diff_fit[j, k], np.log(Ts / 1000.0)))
     assert np.all(np.abs(Dfit - Draw) <= 0.02 * Draw)
+
+
+def test_wilke_off_diagonal_weights(oracle):
+    # For a binary mixture, mu = X1 mu1 / (X1 + X2 P12) + X2 mu2 / (X1 P21 + X2) with the two
+    # off-diagonal Wilke weights P12, P21. Recovered from the oracle's mixture viscosity at two
+    # compositions (and checked at a third), they must satisfy Wilke's reciprocity
+    # P21 / P12 = (mu2 / mu1) (W1 / W2), a property of the weights, not their formula; the
+    # conductivity, which mixes with the same weights, must give the same pair.
+    from scipy.optimize import fsolve
+    m = tiny_mech([(3.5, 0.0, 20.0), (4.0, 0.0, 22.0)], [dict(reac=[0], prod=[1], A=1.0)], W=[0.004, 0.032])
+    m.visc_fit = np.array([[-11.3, 0.7, 0.0, 0.0, 0.0], [-10.4, 0.62, 0.01, 0.0, 0.0]])
+    T = 1300.0
+    Y1 = np.array([1.0, 0.0, 0.2, 0.55, 0.85])
+    Y = np.stack([Y1, 1 - Y1])
+    cp, h, mu, lam, Dk = oracle.props(m, np.full(5, T), np.full(5, P), Y)
+    X1 = (Y1 / 0.004) / (Y1 / 0.004 + (1 - Y1) / 0.032)
+    X2 = 1 - X1
+    mix = lambda prop, phi, i: (X1[i] * prop[0] / (X1[i] + X2[i] * phi[0]) +
+                                X2[i] * prop[1] / (X1[i] * phi[1] + X2[i]))   # prop[0], prop[1]: pure values
+    phi = fsolve(lambda f: [mix(mu, f, 2) - mu[2], mix(mu, f, 3) - mu[3]], [1.0, 1.0], xtol=1e-14)
+    assert abs(mix(mu, phi, 4) - mu[4]) <= 1e-10 * mu[4]
+    assert abs(phi[1] / phi[0] - (mu[1] / mu[0]) * (0.004 / 0.032)) <= 1e-8 * phi[1] / phi[0]
+    for i in (2, 3, 4):
+        assert abs(mix(lam, phi, i) - lam[i]) <= 1e-10 * lam[i]
