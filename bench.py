@@ -635,9 +635,11 @@ def bench_ann(args, rank, world, local):
                          "train_s": t_train},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": GEMM_CHUNK_TRAFFIC.get(MECH),
+                         "traffic": (GEMM_CHUNK_TRAFFIC[MECH] * args.chunk / 262144
+                                     if MECH in GEMM_CHUNK_TRAFFIC else None),
                          "traffic_unit": "DRAM bytes (read + write) of the four GEMM launches of one chunk of "
-                                         "262,144 cells, from one ncu capture of this configuration",
+                                         "%d cells: one ncu capture of a 262,144-cell chunk, scaled by the "
+                                         "cells (every activation makes one DRAM round trip)" % args.chunk,
                          "kernel": "gemm_tn_kernel (all four layers; logical 2MNK flops)", "peak_source": src,
                          "per_shape": {k: {"launches": v[0], "ms": v[1],
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
