@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 1); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 32 * kEpiWarps); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], kEpiWarps); }
         tc::mbar_init(drain, 1);
         tc::fence_barrier_init();
     }
@@ -393,7 +393,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
             const int acc = t & 1;
             const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-            if (!tc::mbar_wait(&tfull[acc], aph)) { atomicExch(err, tc::kErrTimeoutTmemFull); break; }
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[acc], aph))) {   // warp-uniform outcome
+                if (lane == 0) atomicExch(err, tc::kErrTimeoutTmemFull);
+                break;
+            }
             tc::tc_fence_after();
             const int m_blk = tile / n_tiles, n_blk = tile % n_tiles;
             const int row0 = m_blk * kBM + quad * 32;
@@ -425,8 +428,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     epi(row0 + lane, col0, v);
                 }
             }
+            // one arrival per warp once all its lanes' TMEM reads are done
             tc::tc_fence_before();
-            tc::mbar_arrive(&tempty[acc]);
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&tempty[acc]);
         }
         if (tma && lane == 0) tc::bulk_wait<0>();    // stores complete before the CTA exits
         __syncwarp();
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 2); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 2 * 32 * kEpiWarps); }
+        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 2 * kEpiWarps); }
         tc::mbar_init(drain, 1);
         tc::fence_barrier_init();
     }
@@ -585,7 +590,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int tile = pair; tile < tiles; tile += npairs, ++t) {
             const int acc = t & 1;
             const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-            if (!tc::mbar_wait_cluster(&tfull[acc], aph)) { atomicExch(err, tc::kErrTimeoutTmemFull); break; }
+            if (!__all_sync(0xffffffffu, tc::mbar_wait_cluster(&tfull[acc], aph))) {
+                if (lane == 0) atomicExch(err, tc::kErrTimeoutTmemFull);
+                break;
+            }
             tc::tc_fence_after();
             const int m_pair = tile / n_tiles, n_blk = tile % n_tiles;
             const int row0 = (2 * m_pair + (int)rank) * kBM + quad * 32;
@@ -618,7 +626,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 }
             }
             tc::tc_fence_before();
-            tc::mbar_arrive_cluster(acc ? tempty1 : tempty0);
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive_cluster(acc ? tempty1 : tempty0);
         }
         if (tma && lane == 0) tc::bulk_wait<0>();
         __syncwarp();
