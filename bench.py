@@ -405,8 +405,8 @@ def bench_ann(args, rank, world, local):
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         # out-of-distribution guard fitted on the training states; off-grid cells fall back to stiff
-        binding.chem_mlp_fit_ood(net, dm, data.n, data.ld, data.T, data.p, data.Y, smech.roles["oxidizer"], 64,
-                                 args.ood_kmin)
+        binding.chem_mlp_fit_ood_multi(net, dm, data.n, data.ld, data.T, data.p, data.Y,
+                                       [smech.roles[r] for r in args.ood_species.split(",")], 64, args.ood_kmin)
         if fp8:
             # E4M3 activation scales from the BF16 forward of training states
             binding.chem_mlp_calibrate_fp8(net, min(data.n, 262144), data.ld, data.T, data.p, data.Y)
@@ -645,8 +645,9 @@ def bench_ann(args, rank, world, local):
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
                                        for k, v in gemm.items()}},
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
-            "guard": {"ood": not args.untrained, "grid": "64^3 over (T, h/R, Y_oxidizer), neighbourhood >= %d"
-                      % args.ood_kmin, "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
+            "guard": {"ood": not args.untrained,
+                      "grid": "64^3 over (T, h/R, Y_s) for s in %s, neighbourhood >= %d; outside any grid -> fallback"
+                      % (args.ood_species, args.ood_kmin), "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
                       "fallback_rtol": STIFF_OPTS["rtol"]},
             "autotuned_tiles": tiles,
             "graph": {"ms_per_step": graph_ms, "cells_per_s": world * ncells / (graph_ms / 1e3),
@@ -693,6 +694,8 @@ def main():
     ap.add_argument("--mech", default=MECH, choices=sorted(HIDDEN),
                     help="mechanism (c2: 30 species, MLP 1600/800/400; c5: 53 species, MLP 2048/1024/512)")
     ap.add_argument("--no-fp8", action="store_true", help="skip the E4M3 variant of the learned step")
+    ap.add_argument("--ood-species", default="oxidizer,co2",
+                    help="comma-separated species roles of the guard's grids (one grid per role, at most two)")
     ap.add_argument("--chunk", type=int, default=2097152,
                     help="cells per inference chunk of the network (sets the activation workspace)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -704,7 +707,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-cells", type=int, default=32768)
     ap.add_argument("--stiff-sample", type=int, default=262144)
-    ap.add_argument("--ood-kmin", type=int, default=2,
+    ap.add_argument("--ood-kmin", type=int, default=1,
                     help="training states the 3x3x3 neighbourhood of a cell's bin must hold for the network")
     ap.add_argument("--untrained", action="store_true",
                     help="profiling captures only: skip training and the accuracy check (kernel times do not "

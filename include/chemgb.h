@@ -324,14 +324,23 @@ int chem_mlp_error(const chem_mlp *mlp, int *host_err);
  */
 int chem_mlp_fit_ood(chem_mlp *mlp, const chem_mech *mech, int64_t n, int64_t ld, const double *T, const double *p,
                      const double *Y, int32_t species, int32_t nbins, int32_t min_count, chem_stream_t stream);
+/* The same test with ngrids (1 or 2) grids, one per feature species
+ * species[0..ngrids): a cell stays with the network only if every grid holds
+ * it, which catches off-manifold cells that one feature species alone
+ * misses. chem_mlp_fit_ood is this call with one grid. */
+int chem_mlp_fit_ood_multi(chem_mlp *mlp, const chem_mech *mech, int64_t n, int64_t ld, const double *T,
+                           const double *p, const double *Y, const int32_t *species, int32_t ngrids, int32_t nbins,
+                           int32_t min_count, chem_stream_t stream);
 /* Turns the test on or off (on requires a fitted grid). */
 int chem_mlp_set_ood(chem_mlp *mlp, int enable);
 /* flags[i] (uint8, device) = 1 when cell i is outside the training distribution. */
 int chem_mlp_ood_flags(const chem_mlp *mlp, const chem_mech *mech, int64_t ncells, int64_t ld, const double *T,
                        const double *p, const double *Y, uint8_t *flags, chem_stream_t stream);
-/* The fitted grid's feature ranges lo3[3], hi3[3] (host floats) and settings. */
+/* The first fitted grid's feature ranges lo3[3], hi3[3] (host floats) and settings. */
 int chem_mlp_get_ood(const chem_mlp *mlp, float *lo3, float *hi3, int32_t *nbins, int32_t *species,
                      int32_t *min_count);
+/* Feature ranges and species of fitted grid `grid` (0 or 1). */
+int chem_mlp_get_ood_grid(const chem_mlp *mlp, int32_t grid, float *lo3, float *hi3, int32_t *species);
 
 /* ---------------------------------------------------------------------------
  * chem_step_ann -- the learned method: advance every cell by the network

@@ -188,3 +188,11 @@ def ood_flags(fit, features):
     outside = ~np.all((u >= 0) & (u < nb), axis=1)
     b = np.clip(np.floor(u).astype(np.int64), 0, nb - 1)
     return outside | ~fit["mask"][b[:, 0], b[:, 1], b[:, 2]]
+
+
+def ood_flags_multi(fits, features):
+    """Several grids (one per feature species): a cell is outside if any grid puts it outside."""
+    out = np.zeros(features[0].shape[0], bool)
+    for fit, f in zip(fits, features):
+        out |= ood_flags(fit, f)
+    return out

@@ -85,6 +85,8 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_get_fp8_weights.argtypes = [vp, i32, vp, vp]
     L.chem_mlp_error.argtypes = [vp, vp]
     L.chem_mlp_fit_ood.argtypes = [vp, vp, i64, i64, vp, vp, vp, i32, i32, i32, vp]
+    L.chem_mlp_fit_ood_multi.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, i32, i32, i32, vp]
+    L.chem_mlp_get_ood_grid.argtypes = [vp, i32, vp, vp, vp]
     L.chem_mlp_set_ood.argtypes = [vp, i32]
     L.chem_mlp_ood_flags.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, vp]
     L.chem_mlp_get_ood.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -288,6 +290,22 @@ def chem_mlp_fit_ood(mlp: Mlp, mech: Mech, n: int, ld: int, T, p, Y, species: in
                      min_count: int = 4, stream=None):
     _check(lib().chem_mlp_fit_ood(mlp.handle, mech.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), species, nbins,
                                   min_count, _stream(stream)))
+
+
+def chem_mlp_fit_ood_multi(mlp: Mlp, mech: Mech, n: int, ld: int, T, p, Y, species, nbins: int = 64,
+                           min_count: int = 4, stream=None):
+    import numpy as np
+    sp = np.ascontiguousarray(species, dtype=np.int32)
+    _check(lib().chem_mlp_fit_ood_multi(mlp.handle, mech.handle, n, ld, _ptr(T), _ptr(p), _ptr(Y), sp.ctypes.data,
+                                        int(sp.size), nbins, min_count, _stream(stream)))
+
+
+def chem_mlp_get_ood_grid(mlp: Mlp, grid: int):
+    import numpy as np
+    lo, hi = np.zeros(3, np.float32), np.zeros(3, np.float32)
+    sp = ctypes.c_int32()
+    _check(lib().chem_mlp_get_ood_grid(mlp.handle, grid, lo.ctypes.data, hi.ctypes.data, ctypes.byref(sp)))
+    return lo, hi, sp.value
 
 
 def chem_mlp_set_ood(mlp: Mlp, enable: bool):

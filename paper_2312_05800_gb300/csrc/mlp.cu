@@ -27,6 +27,7 @@ namespace {
 
 constexpr int kLayers = 4;
 constexpr int kOodMaxBins = 64;
+constexpr int kOodMaxGrids = 2;     // grids of the out-of-distribution test (a cell must pass all)
 constexpr int kOodBlocks = 512;
 constexpr int64_t kFallbackQueue = 8388608;   // cells queued for the stiff fallback before a flush
 constexpr float kLambdaBC = 0.1f;     // Box-Cox lambda (Sec. 3.2)
@@ -79,11 +80,12 @@ struct chem_mlp {
     float *tz[3], *tout, *loss_part;
     int *err;
     // out-of-distribution grid over (T, h/R, Y_s) and the fallback queue
-    uint32_t *ood_counts;                   // [64^3]
-    uint8_t *ood_mask;                      // [64^3]
-    float *ood_range_dev;                   // lo[3], inv_width[3]
-    float ood_lo[3], ood_hi[3];
-    int ood_nb, ood_kmin, ood_species, ood_fitted, ood_enabled;
+    uint32_t *ood_counts[chemgb::kOodMaxGrids];    // [64^3] each
+    uint8_t *ood_mask[chemgb::kOodMaxGrids];       // [64^3] each
+    float *ood_range_dev;                          // per grid: lo[3], inv_width[3]
+    float ood_lo[chemgb::kOodMaxGrids][3], ood_hi[chemgb::kOodMaxGrids][3];
+    int ood_species[chemgb::kOodMaxGrids];
+    int ood_nb, ood_kmin, ood_ngrids, ood_fitted, ood_enabled;
     int32_t *fb_queue;                      // [chunk]
     unsigned int *fb_count;
     int32_t *fb_status;                     // [chunk] when the caller passes no status array
@@ -176,13 +178,25 @@ __device__ __forceinline__ int ood_bin(const float f[3], const float *range, int
 // the compile-time bound NMAX) for the enthalpy Newton iteration; the final
 // clamp and renormalisation are FP64 so that sum Y' = 1 to FP64 round-off.
 struct OodRoute {
-    const float *range;      // null: no test
-    const uint8_t *mask;
-    int nb, species;
+    const float *range;      // per grid lo[3], inv_width[3]; null: no test
+    const uint8_t *mask[kOodMaxGrids];
+    int species[kOodMaxGrids];
+    int ngrids, nb;
     int32_t *queue;          // absolute cell indices (the call's first cell is 0)
     unsigned int *count;
     int64_t base;            // index of this chunk's first cell within the call
 };
+
+// true when a cell with features (T, h/R) and the state Y is outside any grid's distribution
+__device__ __forceinline__ bool ood_outside(const OodRoute &ood, float T, float h, const double *Y, int64_t ld,
+                                            int64_t i) {
+    for (int g = 0; g < ood.ngrids; ++g) {
+        const float f[3] = {T, h, f64_to_f32_trunc(Y[(int64_t)ood.species[g] * ld + i])};
+        const int b = ood_bin(f, ood.range + 6 * g, ood.nb);
+        if (b < 0 || ood.mask[g][b] == 0) return true;
+    }
+    return false;
+}
 
 template <int NMAX>
 __global__ void __launch_bounds__(128, (NMAX <= 32 ? 8 : 4)) epilogue_kernel(int64_t n, int64_t ld, const float *__restrict__ u, int ldu,
@@ -235,9 +249,7 @@ __global__ void __launch_bounds__(128, (NMAX <= 32 ? 8 : 4)) epilogue_kernel(int
     }
     if (ood.range) {
         // a cell outside the training distribution keeps its state and goes to the stiff integrator
-        const float f[3] = {T0, h0, f64_to_f32_trunc(Y[(int64_t)ood.species * ld + i])};
-        const int b = ood_bin(f, ood.range, ood.nb);
-        if (b < 0 || ood.mask[b] == 0) {
+        if (ood_outside(ood, T0, h0, Y, ld, i)) {
             const unsigned int q = atomicAdd(ood.count, 1u);
             ood.queue[q] = (int32_t)(ood.base + i);
             return;
@@ -350,13 +362,12 @@ __global__ void ood_mask_kernel(int nb, int kmin, const uint32_t *counts, uint8_
 }
 
 __global__ void ood_flags_kernel(int64_t n, int64_t ld, const double *T, const double *Y, PropTables<float> tb, int N,
-                                 float T_mid, int s, const float *range, int nb, const uint8_t *mask, uint8_t *out) {
+                                 float T_mid, OodRoute ood, uint8_t *out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float f[3];
-    ood_features(tb, N, T_mid, ld, i, T, Y, s, f);
-    const int b = ood_bin(f, range, nb);
-    out[i] = (b < 0 || mask[b] == 0) ? 1 : 0;
+    ood_features(tb, N, T_mid, ld, i, T, Y, ood.species[0], f);
+    out[i] = ood_outside(ood, f[0], f[1], Y, ld, i) ? 1 : 0;
 }
 
 // L1 loss of Eq. 5 on normalised outputs; dL/du = sign(u - u*)/B written as BF16.
@@ -679,6 +690,19 @@ int quantize_fp8(chem_mlp *m, cudaStream_t st) {
     return check_cuda(cudaGetLastError(), "quantize_fp8");
 }
 
+// the fitted grids as the epilogue and flag kernels take them (queue fields unset)
+OodRoute ood_route(const chem_mlp *m) {
+    OodRoute r{};
+    r.range = m->ood_range_dev;
+    for (int g = 0; g < kOodMaxGrids; ++g) {
+        r.mask[g] = m->ood_mask[g];
+        r.species[g] = m->ood_species[g];
+    }
+    r.ngrids = m->ood_ngrids;
+    r.nb = m->ood_nb;
+    return r;
+}
+
 int check_prec(const chem_mlp *m, int prec, const char *who) {
     if (prec == CHEM_PREC_BF16) return CHEM_OK;
     if (prec != CHEM_PREC_FP8) return set_error(CHEM_EINVAL, std::string(who) + ": unknown precision");
@@ -779,9 +803,11 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->tT0, (size_t)B * maxw * 2});
     parts.push_back({(void **)&m->tT1, (size_t)B * maxw * 2});
     parts.push_back({(void **)&m->loss_part, (size_t)B * 4});
-    parts.push_back({(void **)&m->ood_counts, (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins * 4});
-    parts.push_back({(void **)&m->ood_mask, (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins});
-    parts.push_back({(void **)&m->ood_range_dev, 64});
+    for (int g = 0; g < kOodMaxGrids; ++g) {
+        parts.push_back({(void **)&m->ood_counts[g], (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins * 4});
+        parts.push_back({(void **)&m->ood_mask[g], (size_t)kOodMaxBins * kOodMaxBins * kOodMaxBins});
+    }
+    parts.push_back({(void **)&m->ood_range_dev, 6 * 4 * kOodMaxGrids});
     parts.push_back({(void **)&m->fb_queue, (size_t)(C > kFallbackQueue ? C : kFallbackQueue) * 4});
     parts.push_back({(void **)&m->fb_count, 64});
     parts.push_back({(void **)&m->fb_status, (size_t)C * 4});
@@ -1066,7 +1092,7 @@ int step_ann_impl(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int6
         }
         rc = forward_chunk(m, n, ld, T + c0, p + c0, Y + c0, st, prec);
         if (rc) return rc;
-        OodRoute route{nullptr, nullptr, 0, 0, nullptr, nullptr, 0};
+        OodRoute route{};
         int32_t *st_chunk = status ? status + c0 : m->fb_status;
         if (m->ood_enabled) {
             if (queued == 0) {
@@ -1074,8 +1100,10 @@ int step_ann_impl(const chem_mech *mech, const chem_mlp *m, int64_t ncells, int6
                 rc = check_cuda(cudaMemsetAsync(m->fb_count, 0, sizeof(unsigned int), st), "chem_step_ann: queue reset");
                 if (rc) return rc;
             }
-            route = OodRoute{m->ood_range_dev, m->ood_mask, m->ood_nb, m->ood_species, m->fb_queue, m->fb_count,
-                             c0 - flush_base};
+            route = ood_route(m);
+            route.queue = m->fb_queue;
+            route.count = m->fb_count;
+            route.base = c0 - flush_base;
             queued += n;
         }
         void *pb = prof_begin(st);
@@ -1122,51 +1150,72 @@ extern "C" int chem_step_ann_props(const chem_mech *mech, const chem_mlp *m, int
                          PropsOut{cp, h, mu, lambda, Dk}, stream, "chem_step_ann_props");
 }
 
-extern "C" int chem_mlp_fit_ood(chem_mlp *m, const chem_mech *mech, int64_t n, int64_t ld, const double *T,
-                                const double *p, const double *Y, int32_t species, int32_t nbins, int32_t min_count,
-                                chem_stream_t stream) {
-    if (!m || !mech) return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: null handle");
+extern "C" int chem_mlp_fit_ood_multi(chem_mlp *m, const chem_mech *mech, int64_t n, int64_t ld, const double *T,
+                                      const double *p, const double *Y, const int32_t *species, int32_t ngrids,
+                                      int32_t nbins, int32_t min_count, chem_stream_t stream) {
+    if (!m || !mech || !species) return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: null argument");
     int rc = check_state_args(n, ld, T, p, Y, "chem_mlp_fit_ood");
     if (rc) return rc;
-    if (n < 1 || species < 0 || species >= m->N || nbins < 2 || nbins > kOodMaxBins || min_count < 1)
-        return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: need n >= 1, a valid species, 2 <= nbins <= 64, min_count >= 1");
+    if (ngrids < 1 || ngrids > kOodMaxGrids)
+        return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: 1 or 2 grids (feature species)");
+    for (int g = 0; g < ngrids; ++g)
+        if (species[g] < 0 || species[g] >= m->N) return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: bad species");
+    if (n < 1 || nbins < 2 || nbins > kOodMaxBins || min_count < 1)
+        return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: need n >= 1, 2 <= nbins <= 64, min_count >= 1");
     if (mech->N != m->N) return set_error(CHEM_EINVAL, "chem_mlp_fit_ood: network and mechanism disagree");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_fit_ood: " + why);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const float Tmid = (float)mech->T_mid;
-    ood_extrema_kernel<<<kOodBlocks, 256, 0, st>>>(n, ld, T, Y, mech->dev.f32, m->N, Tmid, species, m->ood_part);
-    std::vector<float> part(kOodBlocks * 6);
-    rc = check_cuda(cudaMemcpyAsync(part.data(), m->ood_part, part.size() * 4, cudaMemcpyDeviceToHost, st),
-                    "chem_mlp_fit_ood extrema");
-    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_ood sync");
-    if (rc) return rc;
-    float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
-    for (int b = 0; b < kOodBlocks; ++b)
-        for (int d = 0; d < 3; ++d) { lo[d] = std::fmin(lo[d], part[b * 6 + d]); hi[d] = std::fmax(hi[d], part[b * 6 + 3 + d]); }
-    float range[6];
-    for (int d = 0; d < 3; ++d) {
-        float w = hi[d] - lo[d];
-        if (!(w > 0.0f)) w = std::fmax(std::fabs(lo[d]) * 1e-3f, 1e-30f);
-        m->ood_lo[d] = lo[d] - 0.05f * w;                 // 5 % margin on both sides
-        m->ood_hi[d] = hi[d] + 0.05f * w;
-        range[d] = m->ood_lo[d];
-        range[3 + d] = (float)nbins / (m->ood_hi[d] - m->ood_lo[d]);
+    float range[6 * kOodMaxGrids];
+    for (int g = 0; g < ngrids; ++g) {
+        ood_extrema_kernel<<<kOodBlocks, 256, 0, st>>>(n, ld, T, Y, mech->dev.f32, m->N, Tmid, species[g], m->ood_part);
+        std::vector<float> part(kOodBlocks * 6);
+        rc = check_cuda(cudaMemcpyAsync(part.data(), m->ood_part, part.size() * 4, cudaMemcpyDeviceToHost, st),
+                        "chem_mlp_fit_ood extrema");
+        if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_ood sync");
+        if (rc) return rc;
+        float lo[3] = {3.4e38f, 3.4e38f, 3.4e38f}, hi[3] = {-3.4e38f, -3.4e38f, -3.4e38f};
+        for (int b = 0; b < kOodBlocks; ++b)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::fmin(lo[d], part[b * 6 + d]);
+                hi[d] = std::fmax(hi[d], part[b * 6 + 3 + d]);
+            }
+        for (int d = 0; d < 3; ++d) {
+            float w = hi[d] - lo[d];
+            if (!(w > 0.0f)) w = std::fmax(std::fabs(lo[d]) * 1e-3f, 1e-30f);
+            m->ood_lo[g][d] = lo[d] - 0.05f * w;                 // 5 % margin on both sides
+            m->ood_hi[g][d] = hi[d] + 0.05f * w;
+            range[6 * g + d] = m->ood_lo[g][d];
+            range[6 * g + 3 + d] = (float)nbins / (m->ood_hi[g][d] - m->ood_lo[g][d]);
+        }
     }
-    rc = check_cuda(cudaMemcpyAsync(m->ood_range_dev, range, sizeof(range), cudaMemcpyHostToDevice, st), "ood range");
-    if (!rc) rc = check_cuda(cudaMemsetAsync(m->ood_counts, 0, (size_t)nbins * nbins * nbins * 4, st), "ood reset");
-    if (rc) return rc;
-    ood_hist_kernel<<<kOodBlocks, 256, 0, st>>>(n, ld, T, Y, mech->dev.f32, m->N, Tmid, species, m->ood_range_dev,
-                                                nbins, m->ood_counts);
+    rc = check_cuda(cudaMemcpyAsync(m->ood_range_dev, range, sizeof(float) * 6 * ngrids, cudaMemcpyHostToDevice, st),
+                    "ood range");
     const int nbins3 = nbins * nbins * nbins;
-    ood_mask_kernel<<<(nbins3 + 255) / 256, 256, 0, st>>>(nbins, min_count, m->ood_counts, m->ood_mask);
-    rc = check_cuda(cudaGetLastError(), "chem_mlp_fit_ood");
+    for (int g = 0; g < ngrids && !rc; ++g) {
+        rc = check_cuda(cudaMemsetAsync(m->ood_counts[g], 0, (size_t)nbins3 * 4, st), "ood reset");
+        if (rc) break;
+        ood_hist_kernel<<<kOodBlocks, 256, 0, st>>>(n, ld, T, Y, mech->dev.f32, m->N, Tmid, species[g],
+                                                    m->ood_range_dev + 6 * g, nbins, m->ood_counts[g]);
+        ood_mask_kernel<<<(nbins3 + 255) / 256, 256, 0, st>>>(nbins, min_count, m->ood_counts[g], m->ood_mask[g]);
+        rc = check_cuda(cudaGetLastError(), "chem_mlp_fit_ood");
+    }
     if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_ood sync");
     if (rc) return rc;
     m->ood_nb = nbins;
     m->ood_kmin = min_count;
-    m->ood_species = species;
+    m->ood_ngrids = ngrids;
+    for (int g = 0; g < ngrids; ++g) m->ood_species[g] = species[g];
     m->ood_fitted = 1;
     m->ood_enabled = 1;
     return CHEM_OK;
+}
+
+extern "C" int chem_mlp_fit_ood(chem_mlp *m, const chem_mech *mech, int64_t n, int64_t ld, const double *T,
+                                const double *p, const double *Y, int32_t species, int32_t nbins, int32_t min_count,
+                                chem_stream_t stream) {
+    return chem_mlp_fit_ood_multi(m, mech, n, ld, T, p, Y, &species, 1, nbins, min_count, stream);
 }
 
 extern "C" int chem_mlp_set_ood(chem_mlp *m, int enable) {
@@ -1187,8 +1236,7 @@ extern "C" int chem_mlp_ood_flags(const chem_mlp *m, const chem_mech *mech, int6
     if (!flags) return set_error(CHEM_EINVAL, "chem_mlp_ood_flags: null flags");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     ood_flags_kernel<<<(unsigned)((ncells + 255) / 256), 256, 0, st>>>(ncells, ld, T, Y, mech->dev.f32, m->N,
-                                                                        (float)mech->T_mid, m->ood_species,
-                                                                        m->ood_range_dev, m->ood_nb, m->ood_mask, flags);
+                                                                        (float)mech->T_mid, ood_route(m), flags);
     return check_cuda(cudaGetLastError(), "chem_mlp_ood_flags");
 }
 
@@ -1196,10 +1244,19 @@ extern "C" int chem_mlp_get_ood(const chem_mlp *m, float *lo3, float *hi3, int32
                                 int32_t *min_count) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_ood: null handle");
     if (!m->ood_fitted) return set_error(CHEM_EINVAL, "chem_mlp_get_ood: the grid is not fitted");
-    for (int d = 0; d < 3; ++d) { if (lo3) lo3[d] = m->ood_lo[d]; if (hi3) hi3[d] = m->ood_hi[d]; }
+    for (int d = 0; d < 3; ++d) { if (lo3) lo3[d] = m->ood_lo[0][d]; if (hi3) hi3[d] = m->ood_hi[0][d]; }
     if (nbins) *nbins = m->ood_nb;
-    if (species) *species = m->ood_species;
+    if (species) *species = m->ood_species[0];
     if (min_count) *min_count = m->ood_kmin;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_get_ood_grid(const chem_mlp *m, int32_t grid, float *lo3, float *hi3, int32_t *species) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_ood_grid: null handle");
+    if (!m->ood_fitted || grid < 0 || grid >= m->ood_ngrids)
+        return set_error(CHEM_EINVAL, "chem_mlp_get_ood_grid: no such fitted grid");
+    for (int d = 0; d < 3; ++d) { if (lo3) lo3[d] = m->ood_lo[grid][d]; if (hi3) hi3[d] = m->ood_hi[grid][d]; }
+    if (species) *species = m->ood_species[grid];
     return CHEM_OK;
 }
 

@@ -111,3 +111,36 @@ def test_fused_step_and_properties(transport):
         if a is not None:
             assert np.array_equal(a, b, equal_nan=True)
     net.free()
+
+
+def test_two_grids_match_oracle(oracle):
+    import torch
+    from paper_2312_05800_gb300 import binding
+    m = synth.mech_c2()
+    ntr, ne = 100000, 40000
+    T, p, Y = synth.states_profiles(m, ntr, 2103)
+    Te, pe, Ye = synth.states_profiles(m, ne, 2003)
+    T2, Y2, moved = synth.perturb_off_manifold(Te, Ye, ne, 0.02, 2004)
+    net = binding.Mlp(dev_mech("c2"), hidden=(64, 64, 64), chunk=8192)
+    sps = [m.roles["oxidizer"], m.roles["water"]]
+    binding.chem_mlp_fit_ood_multi(net, dev_mech("c2"), ntr, T.shape[0], to_dev(T), to_dev(p), to_dev(Y), sps, 64, 2)
+    fits, feats = [], []
+    for g, sp in enumerate(sps):
+        lo, hi, s = binding.chem_mlp_get_ood_grid(net, g)
+        assert s == sp
+        F = A.ood_features(m, T[:ntr], p[:ntr], Y[:, :ntr], sp)
+        fit = A.ood_fit(F, nbins=64, kmin=2)
+        assert np.allclose(lo, fit["lo"], rtol=1e-5, atol=1e-6 * np.abs(fit["hi"] - fit["lo"]))
+        assert np.allclose(hi, fit["hi"], rtol=1e-5, atol=1e-6 * np.abs(fit["hi"] - fit["lo"]))
+        fits.append(fit)
+        feats.append(A.ood_features(m, T2[:ne], pe[:ne], Y2[:, :ne], sp))
+    flags = torch.zeros(T2.shape[0], dtype=torch.uint8, device="cuda")
+    binding.chem_mlp_ood_flags(net, dev_mech("c2"), ne, T2.shape[0], to_dev(T2), to_dev(pe), to_dev(Y2), flags)
+    torch.cuda.synchronize()
+    g = flags.cpu().numpy()[:ne].astype(bool)
+    o = A.ood_flags_multi(fits, feats)
+    assert np.mean(g == o) >= 0.999
+    mv = moved[:ne]
+    assert abs(g[mv].mean() - o[mv].mean()) <= 0.002 + 1.0 / mv.sum()
+    assert abs(g[~mv].mean() - o[~mv].mean()) <= 0.002
+    net.free()

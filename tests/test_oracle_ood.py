@@ -40,3 +40,23 @@ def test_perturbed_cells_are_flagged(oracle):
     flags = A.ood_flags(fit, A.ood_features(m, T2[:ne], pe[:ne], Y2[:, :ne], m.roles["water"]))
     assert flags[moved[:ne]].mean() > 0.7
     assert flags[~moved[:ne]].mean() < 0.01
+
+
+def test_two_grids_flag_the_union(oracle):
+    # a cell is outside two grids' distribution when either grid puts it outside: the flags are
+    # the union, so recall never drops and the false positives stay within the sum of both
+    m = synth.mech_c2()
+    ntr, ne = 100000, 40000
+    T, p, Y = synth.states_profiles(m, ntr, 2103)
+    Te, pe, Ye = synth.states_profiles(m, ne, 2003)
+    T2, Y2, moved = synth.perturb_off_manifold(Te, Ye, ne, 0.02, 2004)
+    fits, feats = [], []
+    for sp in (m.roles["oxidizer"], m.roles["water"]):
+        fits.append(A.ood_fit(A.ood_features(m, T[:ntr], p[:ntr], Y[:, :ntr], sp)))
+        feats.append(A.ood_features(m, T2[:ne], pe[:ne], Y2[:, :ne], sp))
+    single = [A.ood_flags(f, x) for f, x in zip(fits, feats)]
+    both = A.ood_flags_multi(fits, feats)
+    assert np.array_equal(both, single[0] | single[1])
+    mv = moved[:ne]
+    assert both[mv].mean() >= max(s[mv].mean() for s in single)
+    assert both[~mv].mean() <= single[0][~mv].mean() + single[1][~mv].mean()
