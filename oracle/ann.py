@@ -117,21 +117,33 @@ def network(layers, z, round_bf16=False, fp8_scales=None):
     return h
 
 
-def forward_u(mech, layers, stats, T, p, Y, round_bf16=False, fp8_scales=None):
+def network_ensemble(nets, z, round_bf16=False):
+    """The per-species model of Sec. 3.2 (each species mass fraction has a network of its own):
+    nets[g] holds the (W, b) layers of output g's network (widths n_in -> h1 -> h2 -> h3 -> 1), all
+    reading the same input z. Column g of the result is network g's output."""
+    return np.concatenate([network(layers, z, round_bf16) for layers in nets], axis=1)
+
+
+def forward_u(mech, layers, stats, T, p, Y, round_bf16=False, fp8_scales=None, ensemble=False):
+    """ensemble: layers is a list of per-output networks (network_ensemble)."""
     mu_x, sd_x, mu_u, sd_u = stats
     x = M.features(T, p, Y)
     z = (x - mu_x) / sd_x
     if round_bf16 or fp8_scales is not None:
         # the device forms z in FP32
         z = np.asarray(z, np.float32).astype(np.float64)
+    if ensemble:
+        if fp8_scales is not None:
+            raise ValueError("the per-species ensemble has no E4M3 variant")
+        return network_ensemble(layers, z, round_bf16)
     return network(layers, z, round_bf16, fp8_scales)
 
 
-def step_ann(mech, layers, stats, T, p, Y, round_bf16=False, fp8_scales=None):
+def step_ann(mech, layers, stats, T, p, Y, round_bf16=False, fp8_scales=None, ensemble=False):
     """Returns (T', Y') for SoA inputs T[n], p[n], Y[N, n]."""
     import oracle as O
     mu_x, sd_x, mu_u, sd_u = stats
-    u = forward_u(mech, layers, stats, T, p, Y, round_bf16, fp8_scales)
+    u = forward_u(mech, layers, stats, T, p, Y, round_bf16, fp8_scales, ensemble)
     dY = u * sd_u + mu_u
     Yn = np.array(Y, dtype=np.float64)
     sp = out_species(mech)

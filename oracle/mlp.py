@@ -99,6 +99,22 @@ def backward(layers, cache, dout, act_last: bool = False):
     return grads
 
 
+def ensemble_grads(nets, z, target, sign_from=None):
+    """Sec. 3.2 trains each species' network on its own output: network g's loss is Eq. 5 on
+    column g alone, and since no parameter is shared its gradient is that loss's gradient.
+    nets[g] = [{'W', 'b'}] layers of network g. Returns (sum over g of the losses, per-network
+    gradients). sign_from (optional, [B, G]): outputs on which the L1 subgradient sign is taken."""
+    total, grads = 0.0, []
+    for g, layers in enumerate(nets):
+        out, cache = forward(layers, z)
+        loss, dout = l1_loss(out, target[:, g:g + 1])
+        if sign_from is not None:
+            _, dout = l1_loss(sign_from[:, g:g + 1], target[:, g:g + 1])
+        total += loss
+        grads.append(backward(layers, cache, dout))
+    return total, grads
+
+
 def adam_init(layers):
     return {"t": 0, "m": [{k: np.zeros_like(v) for k, v in L.items()} for L in layers],
             "v": [{k: np.zeros_like(v) for k, v in L.items()} for L in layers]}

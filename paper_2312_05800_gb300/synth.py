@@ -571,6 +571,30 @@ def mlp_layers(widths, seed: int):
     return out
 
 
+def mlp_ensemble(widths, seed: int):
+    """G = widths[-1] networks of widths [n_in, h1, h2, h3, 1] (one per output, the per-species
+    model), network g drawn as mlp_layers draws a network with seed + g."""
+    return [mlp_layers(list(widths[:-1]) + [1], seed + g) for g in range(widths[-1])]
+
+
+def stack_ensemble(nets):
+    """Per-output networks in the C ABI's ensemble layout: per layer, the networks' weight
+    matrices stacked row-wise (network g's rows follow network g - 1's) and their biases
+    concatenated."""
+    return [(np.concatenate([net[l][0] for net in nets], axis=0), np.concatenate([net[l][1] for net in nets]))
+            for l in range(len(nets[0]))]
+
+
+def unstack_ensemble(layers, G: int):
+    """The inverse of stack_ensemble for G networks."""
+    out = [[] for _ in range(G)]
+    for W, b in layers:
+        r = W.shape[0] // G
+        for g in range(G):
+            out[g].append((W[g * r:(g + 1) * r], b[g * r:(g + 1) * r]))
+    return out
+
+
 def flatten_layers(layers):
     """Layer-by-layer W (row-major) then b, as float32 (the C ABI's parameter layout)."""
     return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in layers]).astype(np.float32)
