@@ -211,18 +211,29 @@ int chem_dense_bf16(int64_t M, int N, int K, const void *x, int64_t ldx, const v
  * (the Box-Cox map; negative Y clamp to 0), Z-score normalised with training
  * statistics, through three GELU hidden layers (1600, 800, 400 in the paper)
  * to the Z-scored change u*(t) = Y(t + dt) - Y(t) of the N - 1 species other
- * than the bath species (ascending species index). One multi-output network
- * stands in for the paper's one-network-per-species ensemble. Layers run on
- * the tensor cores in BF16 with FP32 accumulation; parameters are kept in FP32.
- * The bath species is closed by mass conservation (dY_bath = -sum dY_k).
+ * than the bath species (ascending species index). Two forms:
+ *  - one multi-output network (ensemble = 0), the default;
+ *  - the paper's form (ensemble = 1): one network per output species, each
+ *    with the three hidden layers and a single output unit, trained on its own
+ *    output (Sec. 3.2, "individual training and prediction ... for each
+ *    species"). The G = N - 1 networks run side by side: the first layers as
+ *    one GEMM over their stacked weights, the hidden-to-hidden layers as
+ *    grouped GEMMs (one launch per layer), the output units as per-network
+ *    dot products. Its parameter layout stacks the networks per layer: W of
+ *    layer l is [G * out_l][in_l] (network g's rows after network g - 1's), b
+ *    is [G * out_l]; with out_3 = 1 the last layer is [G][h3], [G].
+ * Layers run on the tensor cores in BF16 with FP32 accumulation; parameters
+ * are kept in FP32. The bath species is closed by mass conservation
+ * (dY_bath = -sum dY_k).
  */
 typedef struct chem_mlp chem_mlp;
 
 typedef struct {
     int32_t n_hidden[3]; /* hidden widths, multiples of 8 (Sec. 3.2: 1600, 800, 400) */
-    int32_t chunk;       /* cells per inference chunk (0 = 262144): sets the activation workspace */
+    int32_t chunk;       /* cells per inference chunk (0 = 262144; 65536 for an ensemble): sets the
+                            activation workspace (an ensemble keeps G x (h1 + h2 + h3) BF16 per cell) */
     int32_t max_batch;   /* largest training batch (0 = 4096) */
-    int32_t _pad;
+    int32_t ensemble;    /* 0: one multi-output network; 1: one network per output species */
     double dt;           /* the flow step the network predicts, s (Sec. 3.1: 1e-6) */
 } chem_mlp_desc;
 
@@ -234,8 +245,10 @@ enum { CHEM_PREC_BF16 = 0, CHEM_PREC_FP8 = 1 };
  * inference and training workspaces). */
 int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc, uint64_t seed, chem_mlp **out);
 int chem_mlp_free(chem_mlp *mlp);
-/* widths[5] = {N + 2, h1, h2, h3, N - 1} */
+/* widths[5] = {N + 2, h1, h2, h3, N - 1} (per network for an ensemble) */
 int chem_mlp_dims(const chem_mlp *mlp, int32_t *widths);
+/* Number of networks: 1, or N - 1 for an ensemble; negative on a null handle. */
+int chem_mlp_groups(const chem_mlp *mlp);
 /* Number of parameters: sum over the 4 layers of out * in + out. */
 int64_t chem_mlp_nparams(const chem_mlp *mlp);
 /* Host float arrays of chem_mlp_nparams values, layer by layer: W[out][in]

@@ -34,7 +34,7 @@ class chem_ode_opts(ctypes.Structure):
 
 class chem_mlp_desc(ctypes.Structure):
     _fields_ = [("n_hidden", ctypes.c_int32 * 3), ("chunk", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("_pad", ctypes.c_int32), ("dt", ctypes.c_double)]
+                ("ensemble", ctypes.c_int32), ("dt", ctypes.c_double)]
 
 
 CHEM_PREC_BF16, CHEM_PREC_FP8 = 0, 1
@@ -69,6 +69,7 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_create.argtypes = [vp, ctypes.POINTER(chem_mlp_desc), ctypes.c_uint64, ctypes.POINTER(vp)]
     L.chem_mlp_free.argtypes = [vp]
     L.chem_mlp_dims.argtypes = [vp, vp]
+    L.chem_mlp_groups.argtypes = [vp]
     L.chem_mlp_nparams.argtypes = [vp]
     L.chem_mlp_nparams.restype = ctypes.c_int64
     L.chem_mlp_set_params.argtypes = [vp, vp]
@@ -209,19 +210,24 @@ def chem_dense_bf16(M: int, N: int, K: int, x, ldx: int, W, ldw: int, b, act: in
 class Mlp:
     """Library-owned network handle (chem_mlp_create / chem_mlp_free)."""
 
-    def __init__(self, mech: Mech, hidden=(1600, 800, 400), dt=1e-6, seed=0, chunk=0, max_batch=0):
-        import numpy as np
+    def __init__(self, mech: Mech, hidden=(1600, 800, 400), dt=1e-6, seed=0, chunk=0, max_batch=0, ensemble=False):
         d = chem_mlp_desc()
         for i in range(3):
             d.n_hidden[i] = int(hidden[i])
-        d.chunk, d.max_batch, d.dt = int(chunk), int(max_batch), float(dt)
+        d.chunk, d.max_batch, d.dt, d.ensemble = int(chunk), int(max_batch), float(dt), int(bool(ensemble))
         h = ctypes.c_void_p()
         _check(lib().chem_mlp_create(mech.handle, ctypes.byref(d), ctypes.c_uint64(seed), ctypes.byref(h)))
         self.handle = h.value
+        self._describe()
+
+    def _describe(self):
+        import numpy as np
         w = np.zeros(5, np.int32)
         _check(lib().chem_mlp_dims(self.handle, w.ctypes.data))
         self.widths = [int(v) for v in w]
         self.nparams = int(lib().chem_mlp_nparams(self.handle))
+        self.groups = int(lib().chem_mlp_groups(self.handle))
+        self.ensemble = self.groups > 1
 
     def set_params(self, flat):
         import numpy as np
@@ -263,10 +269,7 @@ class Mlp:
         _check(lib().chem_mlp_load(mech.handle, path.encode(), ctypes.byref(h)))
         self = cls.__new__(cls)
         self.handle = h.value
-        w = np.zeros(5, np.int32)
-        _check(lib().chem_mlp_dims(self.handle, w.ctypes.data))
-        self.widths = [int(v) for v in w]
-        self.nparams = int(lib().chem_mlp_nparams(self.handle))
+        self._describe()
         return self
 
     def error(self) -> int:

@@ -20,6 +20,14 @@
 // Ragged M, N and K: TMA fills out-of-range operand elements with zeros, TMA
 // stores clip at the tensor bounds, and direct stores mask rows >= M and
 // columns >= N.
+// Groups: one launch computes G independent products Y_g = epi_g(X_g W_g^T)
+// of the same M, N, K (the per-species networks of Sec. 3.2 side by side).
+// Each operand is either shared by all groups (a 2-D map) or a 3-D map whose
+// third coordinate picks the group: stacked rows (group g's rows follow group
+// g - 1's, as stacked weights) or side-by-side columns (group g's K columns
+// follow group g - 1's in every row, as the activations of G networks). The
+// 3-D box holds one group, so a ragged K or N clips at the group's own bound.
+// Tiles run group-major, so a wave of CTAs shares one group's weights.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -36,6 +44,26 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;                     // BF16 elements per k-block row (128 bytes)
 constexpr int kBK8 = 128;                   // E4M3 elements per k-block row (128 bytes)
 constexpr uint32_t kTmemCols = 512;
+
+// operand / output map kinds of a grouped launch
+enum : int { kMap2D = 0, kMapRowGrp = 1, kMapColGrp = 2 };
+struct GemmGroups {
+    int count;           // G >= 1
+    int a, b, c;         // map kinds of X, W and the TMA-store output
+};
+
+// load one box of a (k, row) tile of group g from a map of the given kind
+__device__ __forceinline__ void load_tile(void *dst, const CUtensorMap *map, uint64_t *bar, int kind, int k, int row,
+                                          int g) {
+    if (kind == kMap2D) tc::tma_load_2d(dst, map, bar, k, row);
+    else if (kind == kMapRowGrp) tc::tma_load_3d(dst, map, bar, k, row, g);
+    else tc::tma_load_3d(dst, map, bar, k, g, row);
+}
+__device__ __forceinline__ void store_tile(const CUtensorMap *map, const void *src, int kind, int col, int row, int g) {
+    if (kind == kMap2D) tc::tma_store_2d(map, src, col, row);
+    else if (kind == kMapRowGrp) tc::tma_store_3d(map, src, col, row, g);
+    else tc::tma_store_3d(map, src, col, g, row);
+}
 
 template <int BN, int STAGES>
 struct GemmSmem {
@@ -97,6 +125,14 @@ struct EpiGelu {
     int64_t ldo;
     float *pre;      // may be null
     int64_t ldp;
+    int64_t g_out = 0, g_bias = 0, g_pre = 0;   // element offsets of group g's out, bias, pre: g x these
+    __device__ __forceinline__ EpiGelu group(int g) const {
+        EpiGelu e = *this;
+        e.out += g * g_out;
+        if (bias) e.bias += g * g_bias;
+        if (pre) e.pre += g * g_pre;
+        return e;
+    }
     // TMA stores clip at 16-byte granularity in the row, so they are used only
     // when rows end on whole 16-column chunks (N % 16 == 0) with a 16-byte
     // aligned bias (read as float4)
@@ -160,6 +196,13 @@ struct EpiLinear {
     const float *bias;
     float *out;
     int64_t ldo;
+    int64_t g_out = 0, g_bias = 0;
+    __device__ __forceinline__ EpiLinear group(int g) const {
+        EpiLinear e = *this;
+        e.out += g * g_out;
+        if (bias) e.bias += g * g_bias;
+        return e;
+    }
     __host__ __device__ __forceinline__ bool tma_store() const { return false; }
     const void *tma_ptr() const { return nullptr; }
     __device__ __forceinline__ void compute(int, const float (&)[16], uint32_t (&)[8]) const {}
@@ -193,6 +236,13 @@ struct EpiGeluGrad {
     int64_t ldz;
     __nv_bfloat16 *out;
     int64_t ldo;
+    int64_t g_z = 0, g_out = 0;
+    __device__ __forceinline__ EpiGeluGrad group(int g) const {
+        EpiGeluGrad e = *this;
+        e.z += g * g_z;
+        e.out += g * g_out;
+        return e;
+    }
     __host__ __device__ __forceinline__ bool tma_store() const { return false; }
     const void *tma_ptr() const { return nullptr; }
     __device__ __forceinline__ void compute(int, const float (&)[16], uint32_t (&)[8]) const {}
@@ -220,6 +270,7 @@ struct EpiGeluQ {
     void *out;
     int64_t ldo;          // elements
     float inv_so;         // used when F8OUT
+    __device__ __forceinline__ EpiGeluQ group(int) const { return *this; }   // launched ungrouped
     __host__ __device__ __forceinline__ bool tma_store() const {
         return (N & 15) == 0 && (reinterpret_cast<uintptr_t>(bias) & 15) == 0 &&
                (!F8IN || (reinterpret_cast<uintptr_t>(cs) & 15) == 0);
@@ -287,7 +338,7 @@ struct EpiGeluQ {
 template <int BN, int STAGES, class Epi>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     gemm_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                   const __grid_constant__ CUtensorMap tmC, int M, int N, int K, Epi epi, int *err) {
+                   const __grid_constant__ CUtensorMap tmC, int M, int N, int K, GemmGroups grp, Epi epi, int *err) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "UMMA N for M = 128");
     using L = GemmSmem<BN, STAGES>;
     extern __shared__ uint8_t smem_raw[];
@@ -305,7 +356,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m_tiles = (M + kBM - 1) / kBM, n_tiles = (N + BN - 1) / BN;
-    const int tiles = m_tiles * n_tiles;
+    const int group_tiles = m_tiles * n_tiles;
+    const int tiles = group_tiles * grp.count;
     constexpr int kBKe = Epi::kF8 ? kBK8 : kBK;   // elements of K per k-block
     const int kblocks = (K + kBKe - 1) / kBKe;
 
@@ -331,14 +383,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             int it = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
-                const int m_blk = tile / n_tiles, n_blk = tile % n_tiles;
+                const int g = tile / group_tiles, r = tile - g * group_tiles;
+                const int m_blk = r / n_tiles, n_blk = r % n_tiles;
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
                     if (!tc::mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, tc::kErrTimeoutEmpty); ok = false; break; }
                     tc::mbar_arrive_expect_tx(&full[s], L::kABytes + L::kBBytes);
-                    tc::tma_load_2d(sA + s * L::kABytes, &tmA, &full[s], kb * kBKe, m_blk * kBM);
-                    tc::tma_load_2d(sB + s * L::kBBytes, &tmB, &full[s], kb * kBKe, n_blk * BN);
+                    load_tile(sA + s * L::kABytes, &tmA, &full[s], grp.a, kb * kBKe, m_blk * kBM, g);
+                    load_tile(sB + s * L::kBBytes, &tmB, &full[s], grp.b, kb * kBKe, n_blk * BN, g);
                 }
             }
             // every issued load lands before the CTA may exit (bounded)
@@ -398,7 +451,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             tc::tc_fence_after();
-            const int m_blk = tile / n_tiles, n_blk = tile % n_tiles;
+            const int g = tile / group_tiles, r = tile - g * group_tiles;
+            const int m_blk = r / n_tiles, n_blk = r % n_tiles;
+            const Epi ge = epi.group(g);
             const int row0 = m_blk * kBM + quad * 32;
             const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u;
 #pragma unroll 1
@@ -410,7 +465,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 if (tma) {
                     if (row0 >= M) continue;            // warp-uniform: nothing of this slice is in range
                     uint32_t w[8];
-                    epi.compute(col0, v, w);
+                    ge.compute(col0, v, w);
                     uint8_t *buf = my_stage + (nstore & 1) * kStageBytesPerWarp;
                     if (nstore >= 2 && lane == 0) tc::bulk_wait_read<1>();   // this buffer's previous store has read it
                     __syncwarp();
@@ -420,12 +475,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     tc::fence_proxy_async_smem();
                     __syncwarp();
                     if (lane == 0) {
-                        tc::tma_store_2d(&tmC, buf, col0, row0);
+                        store_tile(&tmC, buf, grp.c, col0, row0, g);
                         tc::bulk_commit();
                     }
                     ++nstore;
                 } else {
-                    epi(row0 + lane, col0, v);
+                    ge(row0 + lane, col0, v);
                 }
             }
             // one arrival per warp once all its lanes' TMEM reads are done

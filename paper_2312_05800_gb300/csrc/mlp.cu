@@ -44,7 +44,8 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 struct Layer {
-    int in, out;          // logical widths
+    int in, out;          // logical widths (an ensemble: in per network, out over all networks)
+    int gout;             // output width of one network (out / G)
     int kin;              // padded input width (row length of W, multiple of 8)
     int kx;               // forward GEMM K and row length of Wb: 2 kin for the first layer, whose
                           // input is carried as two BF16 terms (hi + lo), else kin
@@ -64,6 +65,7 @@ struct Layer {
 
 struct chem_mlp {
     int N, bath, n_in, n_in_pad, n_out, n_out_pad;
+    int ens, G;                             // one network per output (G = n_out networks) or one (G = 1)
     int widths[5];
     int out_species[64];
     double dt;
@@ -570,6 +572,68 @@ __global__ void amax_bf16_kernel(int64_t rows, int cols, int64_t ld, const __nv_
 }
 
 // ---------------------------------------------------------------------------
+// output units of the per-species ensemble (Sec. 3.2: each network ends in one
+// unit). Network g's last hidden layer is columns [g K, (g + 1) K) of h.
+// ---------------------------------------------------------------------------
+
+// u[i][g] = b[g] + sum_k W[g][k] h[i][g K + k]: one warp per (row, network), BF16 operands as the
+// tensor-core layers store them, FP32 lane sums over 8-element slices, then a fixed butterfly.
+// K % 8 == 0 and 16-byte aligned rows (K, ldh, ldw multiples of 8).
+__global__ void group_dot_kernel(int64_t rows, int G, int K, const __nv_bfloat16 *__restrict__ h, int64_t ldh,
+                                 const __nv_bfloat16 *__restrict__ W, int ldw, const float *__restrict__ b,
+                                 float *__restrict__ u, int ldu) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= rows * G) return;                     // warp-uniform
+    const int64_t i = w / G;
+    const int g = (int)(w - i * G);
+    const __nv_bfloat16 *hr = h + i * ldh + (int64_t)g * K;
+    const __nv_bfloat16 *wr = W + (int64_t)g * ldw;
+    float s = 0.0f;
+    for (int k = lane * 8; k < K; k += 256) {
+        const uint4 hv = *reinterpret_cast<const uint4 *>(hr + k);
+        const uint4 wv = __ldg(reinterpret_cast<const uint4 *>(wr + k));
+        const __nv_bfloat162 *hp = reinterpret_cast<const __nv_bfloat162 *>(&hv);
+        const __nv_bfloat162 *wp = reinterpret_cast<const __nv_bfloat162 *>(&wv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float2 a = __bfloat1622float2(hp[j]), c = __bfloat1622float2(wp[j]);
+            s = fmaf(a.x, c.x, s);
+            s = fmaf(a.y, c.y, s);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) u[i * ldu + g] = s + __ldg(b + g);
+}
+
+// backward of the output units: dz[i][g K + k] = bf16(dout[i][g] W[g][k] GELU'(z[i][g K + k]))
+__global__ void group_dot_back_kernel(int64_t rows, int G, int K, const __nv_bfloat16 *__restrict__ dout, int lddo,
+                                      const __nv_bfloat16 *__restrict__ W, int ldw, const float *__restrict__ z,
+                                      int64_t ldz, __nv_bfloat16 *__restrict__ dz, int64_t lddz) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cols = (int64_t)G * K;
+    if (t >= rows * cols) return;
+    const int64_t i = t / cols;
+    const int c = (int)(t - i * cols);
+    const int g = c / K, k = c - g * K;
+    const float d = __bfloat162float(dout[i * lddo + g]) * __bfloat162float(W[(int64_t)g * ldw + k]);
+    dz[i * lddz + c] = __float2bfloat16_rn(d * gelu_grad(z[i * ldz + c]));
+}
+
+// weight gradient of the output units: gW[g][k] = sum_i dout[i][g] h[i][g K + k], rows in order
+__global__ void group_dot_wgrad_kernel(int64_t rows, int G, int K, const __nv_bfloat16 *__restrict__ dout, int lddo,
+                                       const __nv_bfloat16 *__restrict__ h, int64_t ldh, float *__restrict__ gW,
+                                       int ldgw) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= G * K) return;
+    const int g = c / K, k = c - g * K;
+    float s = 0.0f;
+    for (int64_t i = 0; i < rows; ++i)
+        s = fmaf(__bfloat162float(dout[i * lddo + g]), __bfloat162float(h[i * ldh + c]), s);
+    gW[(int64_t)g * ldgw + k] = s;
+}
+
+// ---------------------------------------------------------------------------
 // host helpers
 // ---------------------------------------------------------------------------
 
@@ -643,6 +707,29 @@ int check_state_args(int64_t ncells, int64_t ld, const void *T, const void *p, c
     return CHEM_OK;
 }
 
+// Hidden layer l >= 1 of the ensemble on n rows: G grouped products, network g's input columns
+// [g in, (g + 1) in) of x (row stride G in), its stacked weight rows [g gout, (g + 1) gout),
+// output columns [g gout, (g + 1) gout) of y; pre (optional) the FP32 pre-activations.
+int ens_hidden(const chem_mlp *m, int l, int bn, int n, const __nv_bfloat16 *x, __nv_bfloat16 *y, float *pre,
+               cudaStream_t st) {
+    const Layer &L = m->L[l];
+    const GemmOperand X{x, (int64_t)m->G * L.in, kMapColGrp, L.in};
+    const GemmOperand W{L.Wb, L.kx, kMapRowGrp, (int64_t)L.gout * L.kx};
+    return gemm_gelu_grouped(bn, X, W, m->G, n, L.gout, L.in, L.b, L.gout, y, L.out, L.gout, pre, L.out, L.gout,
+                             m->err, st);
+}
+
+// the ensemble's output units on n rows of h (the last hidden layer of every network)
+int ens_output(const chem_mlp *m, int64_t n, const __nv_bfloat16 *h, float *u, cudaStream_t st) {
+    const Layer &L = m->L[kLayers - 1];
+    const int64_t threads = n * m->G * 32;
+    void *pb = prof_begin(st);
+    group_dot_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(n, m->G, L.in, h, (int64_t)m->G * L.in, L.Wb,
+                                                                        L.kx, L.b, u, m->n_out_pad);
+    prof_end(pb, st, "group_dot_kernel", 2.0 * n * m->G * L.in, (double)n * (m->G * L.in * 2 + m->G * 4));
+    return check_cuda(cudaGetLastError(), "ensemble output units");
+}
+
 // prologue + the first nlayers layers on cells [0, n) of the given SoA pointers; with all four,
 // the normalised outputs are in m->out. prec CHEM_PREC_FP8 runs the hidden-to-hidden layers on
 // E4M3 operands: h1 and h2 are stored as E4M3 (scales act_scale) in the buffers of h[0] and h[1],
@@ -657,6 +744,16 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
     if (rc) return rc;
     const void *x = m->a0;
     int64_t ldx = 2 * m->n_in_pad;
+    if (m->ens) {
+        // the G first layers read the same input: one GEMM over their stacked weights
+        const Layer &L0 = m->L[0];
+        rc = gemm_gelu(L0.tile, x, ldx, L0.Wb, L0.kx, (int)n, L0.out, L0.kx, L0.b, m->h[0], L0.out, nullptr, 0, m->err,
+                       st);
+        for (int l = 1; l < 3 && l < nlayers && !rc; ++l)
+            rc = ens_hidden(m, l, m->L[l].tile, (int)n, m->h[l - 1], m->h[l], nullptr, st);
+        if (rc || nlayers < kLayers) return rc;
+        return ens_output(m, n, m->h[2], m->out, st);
+    }
     for (int l = 0; l < 3 && l < nlayers; ++l) {
         const Layer &L = m->L[l];
         if (prec == CHEM_PREC_FP8) {
@@ -706,6 +803,7 @@ OodRoute ood_route(const chem_mlp *m) {
 int check_prec(const chem_mlp *m, int prec, const char *who) {
     if (prec == CHEM_PREC_BF16) return CHEM_OK;
     if (prec != CHEM_PREC_FP8) return set_error(CHEM_EINVAL, std::string(who) + ": unknown precision");
+    if (m->ens) return set_error(CHEM_EUNSUPPORTED, std::string(who) + ": the per-species ensemble runs in BF16 only");
     if (!m->fp8_ready)
         return set_error(CHEM_EINVAL, std::string(who) + ": no E4M3 scales for the current parameters (call "
                                                          "chem_mlp_calibrate_fp8 or chem_mlp_set_fp8_scales)");
@@ -739,7 +837,13 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     for (int k = 0, j = 0; k < mech->N; ++k)
         if (k != mech->bath) m->out_species[j++] = k;
     m->dt = desc->dt;
-    m->chunk = desc->chunk > 0 ? desc->chunk : 262144;
+    if (desc->ensemble != 0 && desc->ensemble != 1) {
+        delete m;
+        return set_error(CHEM_EINVAL, "chem_mlp_create: ensemble must be 0 or 1");
+    }
+    m->ens = desc->ensemble;
+    m->G = m->ens ? m->n_out : 1;
+    m->chunk = desc->chunk > 0 ? desc->chunk : (m->ens ? 65536 : 262144);
     m->chunk = (m->chunk + 127) / 128 * 128;
     m->max_batch = desc->max_batch > 0 ? (desc->max_batch + 7) / 8 * 8 : 4096;
     m->seed = seed;
@@ -749,12 +853,16 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     for (int l = 0; l < kLayers; ++l) {
         Layer &L = m->L[l];
         L.in = m->widths[l];
-        L.out = m->widths[l + 1];
+        // an ensemble's layer l stacks G networks' layers: out = G x (one network's out), and a
+        // network's output layer has one unit
+        L.gout = (m->ens && l == kLayers - 1) ? 1 : m->widths[l + 1];
+        L.out = m->ens ? m->G * L.gout : L.gout;
         L.kin = (int)pad8(L.in);
         L.kx = (l == 0) ? 2 * L.kin : L.kin;
         L.outp = (int)pad8(L.out);
         L.kin8 = (int)pad16(L.in);
-        L.tile = default_tile_width(L.out);
+        // an ensemble's grouped layers tile one network's width
+        L.tile = default_tile_width((m->ens && l > 0) ? L.gout : L.out);
     }
     for (int j = 0; j < m->n_in; ++j) { m->h_mu_x[j] = 0.0; m->h_sd_x[j] = 1.0; }
     for (int j = 0; j < m->n_out; ++j) { m->h_mu_u[j] = 0.0; m->h_sd_u[j] = 1.0; }
@@ -773,7 +881,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
         parts.push_back({(void **)&L.vb, o * 4});
         parts.push_back({(void **)&L.gW, w * 4});
         parts.push_back({(void **)&L.gb, o * 4});
-        if (fp8_layer(l)) {
+        if (fp8_layer(l) && !m->ens) {
             parts.push_back({(void **)&L.Wq, (size_t)L.out * L.kin8});
             parts.push_back({(void **)&L.sw, (size_t)pad16(L.out) * 4});
             parts.push_back({(void **)&L.cs, (size_t)pad16(L.out) * 4});
@@ -788,15 +896,15 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->err, 64});
     const int64_t C = m->chunk, B = m->max_batch;
     parts.push_back({(void **)&m->a0, (size_t)C * m->n_in_pad * 4});
-    for (int i = 0; i < 3; ++i) parts.push_back({(void **)&m->h[i], (size_t)C * desc->n_hidden[i] * 2});
+    for (int i = 0; i < 3; ++i) parts.push_back({(void **)&m->h[i], (size_t)C * m->L[i].out * 2});
     parts.push_back({(void **)&m->out, (size_t)C * m->n_out_pad * 4});
     int maxw = m->n_in_pad > m->n_out_pad ? m->n_in_pad : m->n_out_pad;
-    for (int i = 0; i < 3; ++i) maxw = desc->n_hidden[i] > maxw ? desc->n_hidden[i] : maxw;
+    for (int i = 0; i < 3; ++i) maxw = m->L[i].out > maxw ? m->L[i].out : maxw;
     parts.push_back({(void **)&m->tx0, (size_t)B * m->n_in_pad * 4});
     for (int i = 0; i < 3; ++i) {
-        parts.push_back({(void **)&m->th[i], (size_t)B * desc->n_hidden[i] * 2});
-        parts.push_back({(void **)&m->tz[i], (size_t)B * desc->n_hidden[i] * 4});
-        parts.push_back({(void **)&m->tdz[i], (size_t)B * desc->n_hidden[i] * 2});
+        parts.push_back({(void **)&m->th[i], (size_t)B * m->L[i].out * 2});
+        parts.push_back({(void **)&m->tz[i], (size_t)B * m->L[i].out * 4});
+        parts.push_back({(void **)&m->tdz[i], (size_t)B * m->L[i].out * 2});
     }
     parts.push_back({(void **)&m->tout, (size_t)B * m->n_out_pad * 4});
     parts.push_back({(void **)&m->tdout, (size_t)B * m->n_out_pad * 2});
@@ -869,6 +977,11 @@ extern "C" int chem_mlp_dims(const chem_mlp *m, int32_t *widths) {
 }
 
 extern "C" int64_t chem_mlp_nparams(const chem_mlp *m) { return m ? param_count(m) : -1; }
+
+extern "C" int chem_mlp_groups(const chem_mlp *m) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_groups: null handle");
+    return m->G;
+}
 
 extern "C" int chem_mlp_set_params(chem_mlp *m, const float *host) {
     if (!m || !host) return set_error(CHEM_EINVAL, "chem_mlp_set_params: null argument");
@@ -970,6 +1083,7 @@ extern "C" int chem_mlp_forward(const chem_mlp *m, int64_t ncells, int64_t ld, c
 
 extern "C" int chem_mlp_set_fp8_scales(chem_mlp *m, const float *act_scale) {
     if (!m || !act_scale) return set_error(CHEM_EINVAL, "chem_mlp_set_fp8_scales: null argument");
+    if (m->ens) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_set_fp8_scales: the ensemble runs in BF16 only");
     for (int i = 0; i < 2; ++i)
         if (!(act_scale[i] > 0.0f) || !std::isfinite(act_scale[i]))
             return set_error(CHEM_EINVAL, "chem_mlp_set_fp8_scales: scales must be positive and finite");
@@ -994,6 +1108,7 @@ extern "C" int chem_mlp_get_fp8_scales(const chem_mlp *m, float *act_scale) {
 extern "C" int chem_mlp_calibrate_fp8(chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p,
                                       const double *Y, chem_stream_t stream) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_calibrate_fp8: null handle");
+    if (m->ens) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_calibrate_fp8: the ensemble runs in BF16 only");
     int rc = check_state_args(n, ld, T, p, Y, "chem_mlp_calibrate_fp8");
     if (rc) return rc;
     if (n == 0) return set_error(CHEM_EINVAL, "chem_mlp_calibrate_fp8: no cells");
@@ -1027,6 +1142,7 @@ extern "C" int chem_mlp_calibrate_fp8(chem_mlp *m, int64_t n, int64_t ld, const 
 
 extern "C" int chem_mlp_get_fp8_weights(const chem_mlp *m, int layer, uint8_t *Wq, float *sw) {
     if (!m || !Wq || !sw) return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_weights: null argument");
+    if (m->ens) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_get_fp8_weights: the ensemble runs in BF16 only");
     if (layer < 0 || layer >= kLayers || !fp8_layer(layer))
         return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_weights: layer has no E4M3 weights (layers 1 and 2 have)");
     if (!m->fp8_ready) return set_error(CHEM_EINVAL, "chem_mlp_get_fp8_weights: not calibrated");
@@ -1260,6 +1376,74 @@ extern "C" int chem_mlp_get_ood_grid(const chem_mlp *m, int32_t grid, float *lo3
     return CHEM_OK;
 }
 
+namespace chemgb {
+namespace {
+
+// Forward (saving pre-activations), Eq. 5 loss and backward of the per-species ensemble on the B
+// rows already in tx0. Each network's loss is its own output's term of the summed L1 loss, so the
+// gradients are those of G independent trainings. The stacked layers' gradients land in the
+// layers' gW, gb like a single network's.
+int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const double *Y, const double *Y1,
+                     float *loss_dev, cudaStream_t st) {
+    const int G = m->G;
+    const Layer &L0 = m->L[0];
+    int rc = gemm_gelu(L0.tile, m->tx0, 2 * m->n_in_pad, L0.Wb, L0.kx, B, L0.out, L0.kx, L0.b, m->th[0], L0.out,
+                       m->tz[0], L0.out, m->err, st);
+    for (int l = 1; l < 3 && !rc; ++l) rc = ens_hidden(m, l, m->L[l].tile, B, m->th[l - 1], m->th[l], m->tz[l], st);
+    if (!rc) rc = ens_output(m, B, m->th[2], m->tout, st);
+    if (rc) return rc;
+    l1_loss_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, m->tout, m->n_out_pad, idx, ld, Y, Y1, m->n_out, m->out_sp_dev,
+                                                     m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part);
+    if (loss_dev) loss_reduce_kernel<<<1, 256, 0, st>>>(B, m->loss_part, loss_dev);
+    if ((rc = check_cuda(cudaGetLastError(), "ensemble loss"))) return rc;
+    // output units
+    {
+        const Layer &L = m->L[3];
+        const int64_t ldh = (int64_t)G * L.in;
+        group_dot_wgrad_kernel<<<(G * L.in + 127) / 128, 128, 0, st>>>(B, G, L.in, m->tdout, m->n_out_pad, m->th[2],
+                                                                        ldh, L.gW, L.kin);
+        colsum_kernel<<<(G + 127) / 128, 128, 0, st>>>(B, G, m->tdout, m->n_out_pad, L.gb);
+        const int64_t ne = (int64_t)B * ldh;
+        group_dot_back_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(B, G, L.in, m->tdout, m->n_out_pad, L.Wb,
+                                                                            L.kx, m->tz[2], ldh, m->tdz[2], ldh);
+        if ((rc = check_cuda(cudaGetLastError(), "ensemble output backward"))) return rc;
+    }
+    dim3 tb(32, 8);
+    // grouped hidden layers: dW_g = dZ_g^T H_g (stacked rows of the transposes), dZ_{l-1} = (dZ_g W_g) GELU'
+    for (int l = 2; l >= 1; --l) {
+        const Layer &L = m->L[l];
+        const int64_t ldz = (int64_t)G * L.gout, ldh = (int64_t)G * L.in;
+        transpose_kernel<<<dim3((unsigned)((ldz + 31) / 32), (B + 31) / 32), tb, 0, st>>>(B, (int)ldz, m->tdz[l], ldz,
+                                                                                         m->tT0, B);
+        transpose_kernel<<<dim3((unsigned)((ldh + 31) / 32), (B + 31) / 32), tb, 0, st>>>(B, (int)ldh, m->th[l - 1],
+                                                                                         ldh, m->tT1, B);
+        if ((rc = check_cuda(cudaGetLastError(), "ensemble transpose"))) return rc;
+        rc = gemm_linear_grouped(default_tile_width(L.in), GemmOperand{m->tT0, B, kMapRowGrp, (int64_t)L.gout * B},
+                                 GemmOperand{m->tT1, B, kMapRowGrp, (int64_t)L.in * B}, G, L.gout, L.in, B, nullptr, 0,
+                                 L.gW, L.kin, (int64_t)L.gout * L.kin, m->err, st);
+        if (rc) return rc;
+        colsum_kernel<<<(unsigned)((ldz + 127) / 128), 128, 0, st>>>(B, (int)ldz, m->tdz[l], (int)ldz, L.gb);
+        if ((rc = check_cuda(cudaGetLastError(), "ensemble bias grad"))) return rc;
+        rc = gemm_gelu_grad_grouped(default_tile_width(L.in), GemmOperand{m->tdz[l], ldz, kMapColGrp, L.gout},
+                                    GemmOperand{L.Wt, L.outp, kMapColGrp, L.gout}, G, B, L.in, L.gout, m->tz[l - 1],
+                                    ldh, L.in, m->tdz[l - 1], ldh, L.in, m->err, st);
+        if (rc) return rc;
+    }
+    // the stacked first layers: one product over all networks (their input is shared)
+    transpose_kernel<<<dim3((L0.out + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, L0.out, m->tdz[0], L0.out, m->tT0, B);
+    transpose_kernel<<<dim3((m->n_in_pad + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, m->n_in_pad, m->tx0,
+                                                                                  2 * m->n_in_pad, m->tT1, B);
+    if ((rc = check_cuda(cudaGetLastError(), "ensemble transpose"))) return rc;
+    rc = gemm_linear(default_tile_width(L0.kin), m->tT0, B, m->tT1, B, L0.out, L0.kin, B, nullptr, L0.gW, L0.kin,
+                     m->err, st);
+    if (rc) return rc;
+    colsum_kernel<<<(L0.out + 127) / 128, 128, 0, st>>>(B, L0.out, m->tdz[0], L0.out, L0.gb);
+    return check_cuda(cudaGetLastError(), "ensemble bias grad");
+}
+
+}  // namespace
+}  // namespace chemgb
+
 extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, int64_t ld, const double *T,
                               const double *p, const double *Y, const double *Y1, float lr, float *loss_dev,
                               chem_stream_t stream) {
@@ -1277,50 +1461,55 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     // forward with saved pre-activations
     prologue_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, ld, T, p, Y, idx, m->N, m->n_in_pad, m->mu_x, m->isd_x, m->tx0);
     if ((rc = check_cuda(cudaGetLastError(), "train prologue"))) return rc;
-    const __nv_bfloat16 *x = m->tx0;
-    int64_t ldx = 2 * m->n_in_pad;
-    for (int l = 0; l < 3; ++l) {
-        const Layer &L = m->L[l];
-        rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->th[l], L.out, m->tz[l], L.out, m->err, st);
+    if (m->ens) {
+        rc = ens_train_passes(m, B, idx, ld, Y, Y1, loss_dev, st);
         if (rc) return rc;
-        x = m->th[l];
-        ldx = L.out;
-    }
-    {
-        const Layer &L = m->L[3];
-        rc = gemm_linear(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->tout, m->n_out_pad, m->err, st);
-        if (rc) return rc;
-    }
-    // loss and dL/du
-    l1_loss_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, m->tout, m->n_out_pad, idx, ld, Y, Y1, m->n_out, m->out_sp_dev,
-                                                     m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part);
-    if (loss_dev) loss_reduce_kernel<<<1, 256, 0, st>>>(B, m->loss_part, loss_dev);
-    if ((rc = check_cuda(cudaGetLastError(), "train loss"))) return rc;
-    // backward, top layer down: dW_l = dZ_l^T H_{l-1}, db_l = colsum dZ_l, dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
-    const __nv_bfloat16 *dz = m->tdout;
-    int lddz = m->n_out_pad;
-    for (int l = 3; l >= 0; --l) {
-        const Layer &L = m->L[l];
-        // the first layer's weight gradient takes the hi input term (BF16 precision suffices for a gradient)
-        const __nv_bfloat16 *hin = (l == 0) ? m->tx0 : m->th[l - 1];
-        const int wh = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
-        const int ldh = (l == 0) ? 2 * m->n_in_pad : wh;
-        dim3 tb(32, 8);
-        transpose_kernel<<<dim3((lddz + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, lddz, dz, lddz, m->tT0, B);
-        transpose_kernel<<<dim3((wh + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, wh, hin, ldh, m->tT1, B);
-        if ((rc = check_cuda(cudaGetLastError(), "train transpose"))) return rc;
-        rc = gemm_linear(default_tile_width(L.kin), m->tT0, B, m->tT1, B, L.out, L.kin, B, nullptr, L.gW, L.kin, m->err,
-                         st);
-        if (rc) return rc;
-        colsum_kernel<<<(L.out + 127) / 128, 128, 0, st>>>(B, L.out, dz, lddz, L.gb);
-        if ((rc = check_cuda(cudaGetLastError(), "train bias grad"))) return rc;
-        if (l > 0) {
-            const Layer &Lb = m->L[l - 1];
-            rc = gemm_gelu_grad(default_tile_width(Lb.out), dz, lddz, L.Wt, L.outp, B, Lb.out, L.outp, m->tz[l - 1],
-                                Lb.out, m->tdz[l - 1], Lb.out, m->err, st);
+    } else {
+        const __nv_bfloat16 *x = m->tx0;
+        int64_t ldx = 2 * m->n_in_pad;
+        for (int l = 0; l < 3; ++l) {
+            const Layer &L = m->L[l];
+            rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->th[l], L.out, m->tz[l], L.out, m->err, st);
             if (rc) return rc;
-            dz = m->tdz[l - 1];
-            lddz = Lb.out;
+            x = m->th[l];
+            ldx = L.out;
+        }
+        {
+            const Layer &L = m->L[3];
+            rc = gemm_linear(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->tout, m->n_out_pad, m->err, st);
+            if (rc) return rc;
+        }
+        // loss and dL/du
+        l1_loss_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, m->tout, m->n_out_pad, idx, ld, Y, Y1, m->n_out, m->out_sp_dev,
+                                                         m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part);
+        if (loss_dev) loss_reduce_kernel<<<1, 256, 0, st>>>(B, m->loss_part, loss_dev);
+        if ((rc = check_cuda(cudaGetLastError(), "train loss"))) return rc;
+        // backward, top layer down: dW_l = dZ_l^T H_{l-1}, db_l = colsum dZ_l, dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
+        const __nv_bfloat16 *dz = m->tdout;
+        int lddz = m->n_out_pad;
+        for (int l = 3; l >= 0; --l) {
+            const Layer &L = m->L[l];
+            // the first layer's weight gradient takes the hi input term (BF16 precision suffices for a gradient)
+            const __nv_bfloat16 *hin = (l == 0) ? m->tx0 : m->th[l - 1];
+            const int wh = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
+            const int ldh = (l == 0) ? 2 * m->n_in_pad : wh;
+            dim3 tb(32, 8);
+            transpose_kernel<<<dim3((lddz + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, lddz, dz, lddz, m->tT0, B);
+            transpose_kernel<<<dim3((wh + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, wh, hin, ldh, m->tT1, B);
+            if ((rc = check_cuda(cudaGetLastError(), "train transpose"))) return rc;
+            rc = gemm_linear(default_tile_width(L.kin), m->tT0, B, m->tT1, B, L.out, L.kin, B, nullptr, L.gW, L.kin, m->err,
+                             st);
+            if (rc) return rc;
+            colsum_kernel<<<(L.out + 127) / 128, 128, 0, st>>>(B, L.out, dz, lddz, L.gb);
+            if ((rc = check_cuda(cudaGetLastError(), "train bias grad"))) return rc;
+            if (l > 0) {
+                const Layer &Lb = m->L[l - 1];
+                rc = gemm_gelu_grad(default_tile_width(Lb.out), dz, lddz, L.Wt, L.outp, B, Lb.out, L.outp, m->tz[l - 1],
+                                    Lb.out, m->tdz[l - 1], Lb.out, m->err, st);
+                if (rc) return rc;
+                dz = m->tdz[l - 1];
+                lddz = Lb.out;
+            }
         }
     }
     // Adam
@@ -1392,8 +1581,14 @@ extern "C" int chem_mlp_save(const chem_mlp *m, const char *path) {
         const uint8_t *b = static_cast<const uint8_t *>(p);
         body.insert(body.end(), b, b + n);
     };
-    int32_t hdr[8] = {1, m->N, m->bath, m->widths[0], m->widths[1], m->widths[2], m->widths[3], m->widths[4]};
+    // version 1: one multi-output network; version 2: followed by {ensemble flag, 0}
+    int32_t hdr[8] = {m->ens ? 2 : 1, m->N, m->bath, m->widths[0], m->widths[1], m->widths[2], m->widths[3],
+                      m->widths[4]};
     put(hdr, sizeof(hdr));
+    if (m->ens) {
+        const int32_t ext[2] = {1, 0};
+        put(ext, sizeof(ext));
+    }
     put(&m->dt, 8);
     put(&m->adam_t, 8);
     put(m->h_mu_x, 8 * m->n_in);
@@ -1435,13 +1630,21 @@ extern "C" int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp *
     if (fnv1a(body, blen) != sum) return set_error(CHEM_EIO, "chem_mlp_load: checksum mismatch");
     int32_t hdr[8];
     std::memcpy(hdr, body, sizeof(hdr));
-    if (hdr[0] != 1) return set_error(CHEM_EIO, "chem_mlp_load: unknown checkpoint version");
+    if (hdr[0] != 1 && hdr[0] != 2) return set_error(CHEM_EIO, "chem_mlp_load: unknown checkpoint version");
     if (hdr[1] != mech->N || hdr[2] != mech->bath)
         return set_error(CHEM_EINVAL, "chem_mlp_load: checkpoint species do not match the mechanism");
     chem_mlp_desc d;
     std::memset(&d, 0, sizeof(d));
     for (int i = 0; i < 3; ++i) d.n_hidden[i] = hdr[4 + i];
     size_t off = sizeof(hdr);
+    if (hdr[0] == 2) {
+        int32_t ext[2];
+        if (blen < off + sizeof(ext)) return set_error(CHEM_EIO, "chem_mlp_load: truncated checkpoint");
+        std::memcpy(ext, body + off, sizeof(ext));
+        if (ext[0] != 0 && ext[0] != 1) return set_error(CHEM_EIO, "chem_mlp_load: bad ensemble flag");
+        d.ensemble = ext[0];
+        off += sizeof(ext);
+    }
     std::memcpy(&d.dt, body + off, 8);
     off += 8;
     int64_t adam_t;
@@ -1497,21 +1700,28 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
     if (rc) { cudaEventDestroy(e0); return rc; }
     for (int l = 0; l < kLayers && !rc; ++l) {
         Layer &L = m->L[l];
+        if (m->ens && l == kLayers - 1) {           // the ensemble's output units are not a GEMM
+            if (tiles_out) tiles_out[l] = 0;
+            continue;
+        }
         const __nv_bfloat16 *x = (l == 0) ? m->a0 : m->h[l - 1];
         const int64_t ldx = (l == 0) ? 2 * m->n_in_pad : m->L[l - 1].out;
+        const int width = (m->ens && l > 0) ? L.gout : L.out;    // output columns of one product
         float best = 3.4e38f;
         int best_bn = L.tile;
         // the two-CTA variant is not a candidate: measured on GB300 it runs at half the single-CTA rate
         const std::vector<int> codes(std::begin(kTileWidths), std::end(kTileWidths));
         for (int bn : codes) {
             const int w = bn & 0xFFFF;
-            if (w < 64 && L.out > 64) continue;
-            if (w > 2 * ((L.out + 15) / 16) * 16 && w > 64) continue;   // tiles far wider than the layer
+            if (w < 64 && width > 64) continue;
+            if (w > 2 * ((width + 15) / 16) * 16 && w > 64) continue;   // tiles far wider than the layer
             float ms_sum = 0.0f;
             for (int rep = 0; rep < 4 && !rc; ++rep) {
                 rc = check_cuda(cudaEventRecord(e0, st), "autotune record");
                 if (rc) break;
-                if (l < 3)
+                if (m->ens && l > 0)
+                    rc = ens_hidden(m, l, bn, (int)rows, m->h[l - 1], m->h[l], nullptr, st);
+                else if (l < 3)
                     rc = gemm_gelu(bn, x, ldx, L.Wb, L.kx, (int)rows, L.out, L.kx, L.b, m->h[l], L.out, nullptr, 0,
                                    m->err, st);
                 else
