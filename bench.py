@@ -410,6 +410,25 @@ def bench_ann(args, rank, world, local):
         if fp8:
             # E4M3 activation scales from the BF16 forward of training states
             binding.chem_mlp_calibrate_fp8(net, min(data.n, 262144), data.ld, data.T, data.p, data.Y)
+    # ---- the paper's model form: one network per species (Sec. 3.2), trained on the same pairs
+    ens = None
+    ens_train = None
+    if args.ens_epochs > 0:
+        ens = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3004, chunk=args.ens_chunk, max_batch=4096, ensemble=True)
+        if args.untrained:
+            ens_train = {"epochs": 0}
+        else:
+            train.fit_norm(ens, data)
+            t0 = time.perf_counter()
+            ens_hist = train.train(ens, data, epochs=args.ens_epochs, batch=4096, lr0=args.lr)
+            torch.cuda.synchronize()
+            ens_train = {"pairs": args.train_pairs, "epochs": args.ens_epochs, "batch": 4096,
+                         "loss_first_epoch": ens_hist[0], "loss_last_epoch": ens_hist[-1],
+                         "train_s": time.perf_counter() - t0}
+            binding.chem_mlp_fit_ood_multi(ens, dm, data.n, data.ld, data.T, data.p, data.Y,
+                                           [smech.roles[r] for r in args.ood_species.split(",")], 64, args.ood_kmin)
+        ens_tiles = binding.chem_mlp_autotune(ens, min(args.ens_chunk, 262144))
+    if not args.untrained:
         del data
     fb_opts = binding.make_opts(**STIFF_OPTS)
     tiles = binding.chem_mlp_autotune(net, min(args.chunk, 524288))
@@ -436,12 +455,16 @@ def bench_ann(args, rank, world, local):
     T8, Y8 = T0.clone(), Y0.clone()
     if fp8:
         binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_FP8, fb_opts, T8, p0, Y8, status)
+    Te, Ye = T0.clone(), Y0.clone()
+    if ens is not None:
+        binding.chem_step_ann(dm, ens, ne, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Te, p0, Ye, status)
     torch.cuda.synchronize()
-    Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8 = [x.cpu().numpy() for x in (Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8)]
+    Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8, Te, Ye = [x.cpu().numpy() for x in (Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8, Te, Ye)]
     acc_ann = accuracy(smech, T, Y, Ta, Ya, Tr, Yr, ne)
     acc_stiff = accuracy(smech, T, Y, Ts, Ys, Tr, Yr, ne)
     acc_fp8 = accuracy(smech, T, Y, T8, Y8, Tr, Yr, ne) if fp8 else None
-    del Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8
+    acc_ens = accuracy(smech, T, Y, Te, Ye, Tr, Yr, ne) if ens is not None else None
+    del Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8, Te, Ye
 
     def step(st=stream, prec=binding.CHEM_PREC_BF16):
         Tw.copy_(T0)
@@ -531,6 +554,50 @@ def bench_ann(args, rank, world, local):
                     "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof8.items()},
                     "layers": "h1 -> h2 and h2 -> h3 on E4M3 operands (per-row weight scales, per-tensor "
                               "activation scales), first and output layers BF16"}
+    # ---- the per-species ensemble through the same call
+    ens_line = None
+    if ens is not None:
+        def ens_step():
+            Tw.copy_(T0)
+            Yw.copy_(Y0)
+            binding.chem_step_ann_props(dm, ens, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status,
+                                        cp, hh, mu, lam, Dk, stream)
+
+        ens_steps = max(1, min(args.steps, 5))
+        for _ in range(min(args.warmup, 2)):
+            ens_step()
+        torch.cuda.synchronize()
+        assert ens.error() == 0
+        binding.chem_prof_enable(True)
+        g0.record(stream)
+        for _ in range(ens_steps):
+            ens_step()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        profe = binding.chem_prof_read()
+        binding.chem_prof_enable(False)
+        e_ms = g0.elapsed_time(g1) / ens_steps
+        ge = {k: v for k, v in profe.items() if k.startswith("gemm_tn")}
+        ge_ms, ge_fl = sum(v[1] for v in ge.values()), sum(v[2] for v in ge.values())
+        bf_peak = measured_peak("bf16_tflops", 1900.0)[0]
+        ens_line = {"value": world * ncells / (e_ms / 1e3), "unit": "cells/s", "ms_per_step": e_ms,
+                    "steps": ens_steps,
+                    "model": "%d networks %d-%s-1 (one per non-bath species), BF16 tcgen05 grouped GEMMs"
+                             % (N - 1, N + 2, "-".join(str(h) for h in hidden)),
+                    "mflop_per_cell": 2.0 * (N - 1) * ((N + 2) * hidden[0] + hidden[0] * hidden[1] +
+                                                       hidden[1] * hidden[2] + hidden[2]) / 1e6,
+                    "accuracy_vs_tight_stiff": acc_ens, "training": ens_train, "autotuned_tiles": ens_tiles,
+                    "fallback_cells_per_step": int((status[:ncells] == binding.CELL_FALLBACK).sum().item()),
+                    "gemm_roofline": {"bound": "tensor", "achieved": ge_fl / (ge_ms / 1e3) / 1e12 if ge_ms else None,
+                                      "peak": bf_peak, "unit": "TFLOP/s",
+                                      "frac": (ge_fl / (ge_ms / 1e3) / 1e12 / bf_peak) if ge_ms else None,
+                                      "peak_source": "measured",
+                                      "per_shape": {k: {"launches": v[0], "ms": v[1],
+                                                        "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
+                                                    for k, v in ge.items()}},
+                    "kernels_ms_per_step": {k: v[1] / ens_steps for k, v in profe.items()},
+                    "chunk": args.ens_chunk}
+        ens.free()
     if world > 1:
         torch.distributed.barrier()
     total_s = ev[0].elapsed_time(ev[1]) / 1e3
@@ -654,6 +721,7 @@ def bench_ann(args, rank, world, local):
                       "note": "the whole step captured once as a CUDA graph and replayed"},
             "batched_fallback": batched,
             "fp8": fp8_line,
+            "ensemble": ens_line,
             "props_thermo": props_thermo,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks * 6 + 3),
@@ -709,6 +777,10 @@ def main():
     ap.add_argument("--stiff-sample", type=int, default=262144)
     ap.add_argument("--ood-kmin", type=int, default=1,
                     help="training states the 3x3x3 neighbourhood of a cell's bin must hold for the network")
+    ap.add_argument("--ens-epochs", type=int, default=30,
+                    help="epochs of the per-species ensemble's training (0: no ensemble line)")
+    ap.add_argument("--ens-chunk", type=int, default=262144,
+                    help="cells per inference chunk of the ensemble (G x 2800 BF16 activations per cell)")
     ap.add_argument("--untrained", action="store_true",
                     help="profiling captures only: skip training and the accuracy check (kernel times do not "
                          "depend on the weights)")

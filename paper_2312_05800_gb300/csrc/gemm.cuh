@@ -76,40 +76,104 @@ struct GemmSmem {
     static_assert(kBBytes % 1024 == 0, "B tile must keep 1024-byte alignment");
 };
 
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
 __device__ __forceinline__ float ex2_approx(float x) {
     float r;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
 
-// erf by Abramowitz and Stegun (1964) formula 7.1.26: for x >= 0,
-// erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-x^2), t = 1 / (1 + p x),
-// absolute error <= 1.5e-7; odd in x. The reciprocal and the exponential use
-// the hardware approximations (relative error ~2^-22), which keeps the total
-// error near 2e-7, far below the BF16 rounding of the activations.
-__device__ __forceinline__ float erf_as(float x) {
-    const float ax = fabsf(x);
-    const float t = rcp_approx(fmaf(0.3275911f, ax, 1.0f));
-    float y = fmaf(1.061405429f, t, -1.453152027f);
-    y = fmaf(y, t, 1.421413741f);
-    y = fmaf(y, t, -0.284496736f);
-    y = fmaf(y, t, 0.254829592f);
-    const float e = ex2_approx(ax * (ax * -1.4426950408889634f));   // exp(-x^2)
-    const float r = fmaf(-y * t, e, 1.0f);
-    return copysignf(r, x);
+// ---- packed FP32x2 arithmetic (each lane one IEEE operation, round to nearest) ----
+__device__ __forceinline__ uint64_t pk2(float a, float b) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
 }
-// GELU(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 and its derivative Phi(z) + z phi(z)
+__device__ __forceinline__ void upk2(uint64_t r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---- GELU (Sec. 3.2) ---------------------------------------------------------
+// GELU(z) = z Phi(z) = h + |h| erf(sqrt(2) |h|) with h = z / 2. For a >= 0,
+// erf(a) = 1 - erfcx(a) exp(-a^2), erfcx(a) = exp(a^2) erfc(a) (smooth, from 1 at 0
+// down to about 1 / (sqrt(pi) a)). exp(-2 h^2) comes from the hardware exp2
+// approximation, the one special-function operation per value; erfcx(sqrt(2) x),
+// x = min(|h|, 4.5 / sqrt 2), from a degree-11 polynomial fitted by fit_erfcx.py
+// (error of erf at most 1.0e-7 in FP32 Horner evaluation; past the clamp
+// erfc < 4e-10). The coefficients are stored negated: the Horner sum is -erfcx.
+// The packed form runs two values per FP32x2 instruction with the same
+// operations in the same order as the scalar form, so both give the same bits.
+constexpr float kGeluXmax = 3.18198052f;     // 4.5 / sqrt 2
+constexpr float kNeg2Log2e = -2.88539008f;   // -2 log2(e): exp(-2 h^2) = exp2(h (h kNeg2Log2e))
+// -erfcx(sqrt(2) x) on [0, 4.5 / sqrt 2]: Horner form of the fitted polynomial (coefficients negated)
+__device__ __forceinline__ float neg_erfcx(float x) {
+    float y = fmaf(0.00129250193f, x, -0.0157879684f);
+    y = fmaf(y, x, 0.0868072212f);
+    y = fmaf(y, x, -0.288594484f);
+    y = fmaf(y, x, 0.663069665f);
+    y = fmaf(y, x, -1.15249884f);
+    y = fmaf(y, x, 1.63020039f);
+    y = fmaf(y, x, -1.98156738f);
+    y = fmaf(y, x, 2.12489295f);
+    y = fmaf(y, x, -1.99978065f);
+    y = fmaf(y, x, 1.59576237f);
+    y = fmaf(y, x, -0.99999994f);
+    return y;
+}
+__device__ __forceinline__ uint64_t neg_erfcx2(uint64_t x) {
+    uint64_t y = fma2(pk2(0.00129250193f, 0.00129250193f), x, pk2(-0.0157879684f, -0.0157879684f));
+    y = fma2(y, x, pk2(0.0868072212f, 0.0868072212f));
+    y = fma2(y, x, pk2(-0.288594484f, -0.288594484f));
+    y = fma2(y, x, pk2(0.663069665f, 0.663069665f));
+    y = fma2(y, x, pk2(-1.15249884f, -1.15249884f));
+    y = fma2(y, x, pk2(1.63020039f, 1.63020039f));
+    y = fma2(y, x, pk2(-1.98156738f, -1.98156738f));
+    y = fma2(y, x, pk2(2.12489295f, 2.12489295f));
+    y = fma2(y, x, pk2(-1.99978065f, -1.99978065f));
+    y = fma2(y, x, pk2(1.59576237f, 1.59576237f));
+    y = fma2(y, x, pk2(-0.99999994f, -0.99999994f));
+    return y;
+}
+
 __device__ __forceinline__ float gelu_exact(float z) {
-    const float hz = 0.5f * z;
-    return fmaf(hz, erf_as(z * 0.70710678118654752f), hz);
+    const float h = z * 0.5f;
+    const float y = neg_erfcx(fminf(fabsf(h), kGeluXmax));
+    const float e = ex2_approx((h * kNeg2Log2e) * h);
+    const float s = fmaf(y, e, 1.0f);                 // erf(sqrt(2) |h|)
+    return fmaf(fabsf(h), s, h);
 }
+// GELU(v0 + b0), GELU(v1 + b1): the scalar operations above, two lanes at a time
+__device__ __forceinline__ void gelu_pair(float v0, float v1, float b0, float b1, float &g0, float &g1) {
+    const uint64_t h = mul2(add2(pk2(v0, v1), pk2(b0, b1)), pk2(0.5f, 0.5f));
+    float h0, h1;
+    upk2(h, h0, h1);
+    const uint64_t y = neg_erfcx2(pk2(fminf(fabsf(h0), kGeluXmax), fminf(fabsf(h1), kGeluXmax)));
+    float m0, m1;
+    upk2(mul2(mul2(h, pk2(kNeg2Log2e, kNeg2Log2e)), h), m0, m1);
+    const uint64_t s = fma2(y, pk2(ex2_approx(m0), ex2_approx(m1)), pk2(1.0f, 1.0f));
+    upk2(fma2(pk2(fabsf(h0), fabsf(h1)), s, h), g0, g1);
+}
+// dGELU/dz = Phi(z) + z phi(z), with the same erf and exp(-z^2 / 2) = exp(-2 h^2)
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    const float h = z * 0.5f;
+    const float y = neg_erfcx(fminf(fabsf(h), kGeluXmax));
+    const float e = ex2_approx((h * kNeg2Log2e) * h);
+    const float s = fmaf(y, e, 1.0f);                 // erf(|z| / sqrt 2)
+    return fmaf(z * 0.39894228f, e, 0.5f + copysignf(0.5f * s, z));
 }
 
 // ---- epilogue functors: (row, first column, 16 accumulator values) --------
@@ -152,7 +216,9 @@ struct EpiGelu {
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(gelu_exact(v[2 * i] + b[2 * i]), gelu_exact(v[2 * i + 1] + b[2 * i + 1]));
+            float g0, g1;
+            gelu_pair(v[2 * i], v[2 * i + 1], b[2 * i], b[2 * i + 1], g0, g1);
+            __nv_bfloat162 h = __floats2bfloat162_rn(g0, g1);
             w[i] = *reinterpret_cast<uint32_t *>(&h);
         }
     }

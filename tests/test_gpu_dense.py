@@ -106,3 +106,54 @@ def test_pair_tiles_are_bitwise_single_tiles():
     torch.cuda.synchronize()
     assert int(err[0].item()) == 0
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def _bf16_round(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = a.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("tile_n", [256, 208])
+def test_gelu_epilogue_against_exact_gelu(tile_n):
+    # The epilogue's GELU on exactly known pre-activations: X row m holds z_m in column 0, W row n
+    # is the unit vector e_0, so the accumulator is z_m exactly and the epilogue sees
+    # z = fl32(z_m + b_n). The device stores BF16(d) of its FP32 GELU value d. Every output g must
+    # come from a d within the device GELU's error of the exact value (the erf polynomial's 1.0e-7
+    # and FP32 rounding: delta = 2e-7 (1 + |z|)): the exact GELU lies within delta of the set of
+    # FP32 values that round to g. Deep in the negative tail that set is near 0 and the test is
+    # absolute, which is the accuracy the next layer sees.
+    import torch
+    from paper_2312_05800_gb300 import binding
+    M, N, K = 8192, 512, 16
+    rng = np.random.default_rng(31)
+    zm = _bf16_round(np.concatenate([np.linspace(-12.0, 12.0, M - 2048), rng.normal(size=2048) * 2.0]))
+    bn = (rng.uniform(-0.05, 0.05, N)).astype(np.float32)
+    x = np.zeros((M, K), np.float32)
+    x[:, 0] = zm
+    W = np.zeros((N, K), np.float32)
+    W[:, 0] = 1.0
+    xd = torch.from_numpy(x).to(torch.bfloat16).cuda()
+    Wd = torch.from_numpy(W).to(torch.bfloat16).cuda()
+    bd = torch.from_numpy(bn).cuda()
+    y = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(4, dtype=torch.int32, device="cuda")
+    binding.chem_dense_bf16(M, N, K, xd, K, Wd, K, bd, 1, y, N, tile_n, err)
+    torch.cuda.synchronize()
+    assert int(err[0].item()) == 0
+    got = y.double().cpu().numpy()
+    z = (zm[:, None].astype(np.float32) + bn[None, :]).astype(np.float64)   # fl32(z_m + b_n)
+    exact = _gelu64(z)
+    # half a BF16 unit in the last place of g (8 significant bits); 0 for g = 0
+    _, ex = np.frexp(np.where(got != 0, np.abs(got), 1.0))
+    hu = np.where(got != 0, np.ldexp(1.0, ex - 9), 0.0)
+    dist = np.maximum(np.abs(exact - got) - hu, 0.0)
+    delta = 2e-7 * (1.0 + np.abs(z))
+    if not np.all(dist <= delta):
+        i, j = np.unravel_index(np.argmax(dist / delta), dist.shape)
+        raise AssertionError("%d of %d outside; worst z %.9g: device %.9g exact %.9g (delta %.3g)"
+                             % ((dist > delta).sum(), dist.size, z[i, j], got[i, j], exact[i, j], delta[i, j]))
+    # and the outputs are the correctly rounded ones almost everywhere the GELU is not tiny
+    big = np.abs(exact) > 0.05
+    assert np.mean(got[big] != _bf16_round(exact[big])) < 1e-3
