@@ -76,6 +76,12 @@ def stiff_flops_per_step(N: int, R: int, n_tb: int, n_troe: int) -> float:
     return 3 * rhs + jac + (2.0 / 3.0) * n ** 3 + 4 * 2 * n * n
 
 
+def pasr_rhs_flops(N: int, R: int, n_tb: int, n_troe: int) -> float:
+    """FP64 flops of one reactor right-hand side (the rhs term of stiff_flops_per_step) plus the
+    species times (a division and a comparison per species)."""
+    return 20 * N + R * (2 * 20 + 12) + n_tb * 2 * N + n_troe * (5 * 20 + 30) + 2 * N
+
+
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -554,6 +560,32 @@ def bench_ann(args, rank, world, local):
                     "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof8.items()},
                     "layers": "h1 -> h2 and h2 -> h3 on E4M3 operands (per-row weight scales, per-tensor "
                               "activation scales), first and output layers BF16"}
+    # ---- PaSR scaling (Sec. 4.1) of the learned step's result, timed alone
+    rng_t = np.random.default_rng(2071)
+    tt = torch.from_numpy(10.0 ** rng_t.uniform(-6, -2, ld)).to(dev)
+    tk = torch.from_numpy(10.0 ** rng_t.uniform(-7, -3, ld)).to(dev)
+    kap = torch.empty(ld, dtype=torch.float64, device=dev)
+    tcd = torch.empty_like(kap)
+    step()
+    Tp, Yp = Tw.clone(), Yw.clone()
+    binding.chem_pasr(dm, ncells, ld, 1e-6, T0, p0, Y0, tt, tk, Tp, Yp, tcd, kap, stream)
+    torch.cuda.synchronize()
+    kap_med = float(kap[:ncells].median().item())
+    g0.record(stream)
+    for _ in range(2):
+        binding.chem_pasr(dm, ncells, ld, 1e-6, T0, p0, Y0, tt, tk, Tp, Yp, tcd, kap, stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    pasr_ms = g0.elapsed_time(g1) / 2
+    rhs_fl = pasr_rhs_flops(smech.N, smech.R, int((smech.rtype != 0).sum()), int((smech.rtype == 2).sum()))
+    pasr_line = {"ms": pasr_ms, "cells_per_s": ncells / (pasr_ms / 1e3), "kappa_median": kap_med,
+                 "roofline": {"bound": "alu", "achieved": ncells * rhs_fl / (pasr_ms / 1e3) / 1e12,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": ncells * rhs_fl / (pasr_ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS,
+                              "flops_per_cell": rhs_fl},
+                 "workload": "chem_pasr on the learned step's result: FP64 reactor rates at the state before "
+                             "the step, tau_c, kappa with seeded Taylor / Kolmogorov times, scaled (T, Y)"}
+    del Tp, Yp, tt, tk, kap, tcd
     # ---- the per-species ensemble through the same call
     ens_line = None
     if ens is not None:
@@ -722,6 +754,7 @@ def bench_ann(args, rank, world, local):
             "batched_fallback": batched,
             "fp8": fp8_line,
             "ensemble": ens_line,
+            "pasr": pasr_line,
             "props_thermo": props_thermo,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * (chunks * 6 + 3),

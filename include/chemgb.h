@@ -184,6 +184,33 @@ int chem_step_stiff_noalloc(const chem_mech *mech, int64_t ncells, int64_t ld, d
                             chem_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * chem_pasr -- partially stirred reactor scaling of one chemistry step
+ * ---------------------------------------------------------------------------
+ * Sec. 4.1: the turbulence-chemistry interaction is the PaSR model, in which a
+ * cell's reaction rate is scaled by kappa = tau_c / (tau_c + tau_mix); the
+ * chemical time tau_c comes from the slowest formation rate of the species and
+ * the mixing time tau_mix is the geometric mean of the Taylor and Kolmogorov
+ * time scales. Per cell i < ncells (SoA, leading dimension ld):
+ *   dY_k/dt  the reactor right-hand side (Sec. 3.1) at (T0, p, Y0), in FP64;
+ *   tau_c    max over species k with Y0_k >= y_min and dY_k/dt != 0 of
+ *            Y0_k / |dY_k/dt|, or +inf when no species qualifies;
+ *   tau_mix  sqrt(tau_taylor * tau_kolmogorov);
+ *   kappa    tau_c / (tau_c + tau_mix), or 1 when tau_c is infinite.
+ * T0, p, Y0 [N][ld]: the state before the chemistry step (device, read only).
+ * tau_taylor, tau_kolmogorov [ncells] (s, device, read only).
+ * T, Y (device, may both be NULL): on entry the chemistry step's result at
+ * t + dt (chem_step_stiff or chem_step_ann), on exit T0 + kappa (T - T0) and
+ * Y0 + kappa (Y - Y0). They must not alias T0, Y0.
+ * tau_c, kappa [ncells] (device, FP64, may be NULL): outputs.
+ * y_min > 0 (e.g. 1e-6). Errors: CHEM_EINVAL for null inputs, only one of T
+ * and Y, misaligned arrays or ncells > ld; CHEM_EUNSUPPORTED for more than 63
+ * species or a non-sm_103 device. Asynchronous on stream; allocates nothing.
+ */
+int chem_pasr(const chem_mech *mech, int64_t ncells, int64_t ld, double y_min, const double *T0, const double *p,
+              const double *Y0, const double *tau_taylor, const double *tau_kolmogorov, double *T, double *Y,
+              double *tau_c, double *kappa, chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * chem_dense_bf16 -- one dense layer of the network on the tensor cores
  * ---------------------------------------------------------------------------
  * Sec. 3.2: each hidden layer applies GELU to an affine map of the layer below.

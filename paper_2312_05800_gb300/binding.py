@@ -65,6 +65,7 @@ def lib() -> ctypes.CDLL:
     L.chem_ode_opts_default.restype = None
     L.chem_step_stiff.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
     L.chem_step_stiff_noalloc.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
+    L.chem_pasr.argtypes = [vp, i64, i64, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.chem_dense_bf16.argtypes = [i64, i32, i32, vp, i64, vp, i64, vp, i32, vp, i64, i32, vp, vp]
     L.chem_mlp_create.argtypes = [vp, ctypes.POINTER(chem_mlp_desc), ctypes.c_uint64, ctypes.POINTER(vp)]
     L.chem_mlp_free.argtypes = [vp]
@@ -205,6 +206,12 @@ def chem_dense_bf16(M: int, N: int, K: int, x, ldx: int, W, ldw: int, b, act: in
                     err=None, stream=None):
     _check(lib().chem_dense_bf16(M, N, K, _ptr(x), ldx, _ptr(W), ldw, _ptr(b), act, _ptr(y), ldy, tile_n, _ptr(err),
                                  _stream(stream)))
+
+
+def chem_pasr(mech: Mech, ncells: int, ld: int, y_min: float, T0, p, Y0, tau_taylor, tau_kolmogorov, T=None, Y=None,
+              tau_c=None, kappa=None, stream=None):
+    _check(lib().chem_pasr(mech.handle, ncells, ld, float(y_min), _ptr(T0), _ptr(p), _ptr(Y0), _ptr(tau_taylor),
+                           _ptr(tau_kolmogorov), _ptr(T), _ptr(Y), _ptr(tau_c), _ptr(kappa), _stream(stream)))
 
 
 class Mlp:

@@ -26,6 +26,8 @@
 //      (I/(h g) - J) K_i = f(y + sum_j a_ij K_j) + sum_j (c_ij / h) K_j,
 //    y_new = y + sum_i m_i K_i, error estimate sum_i e_i K_i, with the
 //    step-size controller of chem_ode_opts. Everything is FP64.
+#include <math_constants.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -661,10 +663,105 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
     }
 }
 
+// PaSR scaling (Sec. 4.1), one warp per cell. The species times Y_k / |dY_k/dt| come from the
+// reactor right-hand side at the state before the step (the same FP64 evaluation as the
+// integrator's); tau_c is the largest over the species with Y_k >= y_min and a non-zero rate
+// (the slowest formation rate), +inf when none qualifies; tau_mix = sqrt(tau_T tau_K);
+// kappa = tau_c / (tau_c + tau_mix), 1 for an infinite tau_c. With T, Y given (the chemistry
+// step's result), they become T0 + kappa (T - T0), Y0 + kappa (Y - Y0).
+__global__ void __launch_bounds__(kWarps * 32) pasr_kernel(DevMech m, int64_t ncells, int64_t ld, double y_min,
+                                                            const double *__restrict__ T0,
+                                                            const double *__restrict__ pg,
+                                                            const double *__restrict__ Y0,
+                                                            const double *__restrict__ tau_t,
+                                                            const double *__restrict__ tau_k, double *__restrict__ T,
+                                                            double *__restrict__ Y, double *__restrict__ tau_c_out,
+                                                            double *__restrict__ kappa_out) {
+    extern __shared__ __align__(16) char smem_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = m.N, n = N + 1;
+    const Slice sh = make_slice(smem_raw + (size_t)warp * slice_bytes(N, m.R), N, m.R);
+    const Team<1> tm{0};
+    for (int64_t cell = (int64_t)blockIdx.x * kWarps + warp; cell < ncells; cell += (int64_t)gridDim.x * kWarps) {
+        double y[2], f[2];
+        for (int s = 0; s < 2; ++s) {
+            const int c = lane + 32 * s;
+            y[s] = (c == 0) ? T0[cell] : (c < n ? Y0[(int64_t)(c - 1) * ld + cell] : 0.0);
+        }
+        eval_rhs<1>(m, sh, tm, lane, pg[cell], y, f, false);
+        double tmax = -1.0;                       // species times are >= 0: -1 marks none
+        for (int s = 0; s < 2; ++s) {
+            const int c = lane + 32 * s;
+            if (c >= 1 && c < n) {
+                const double r = fabs(f[s]);
+                if (y[s] >= y_min && r > 0.0) tmax = fmax(tmax, y[s] / r);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tmax = fmax(tmax, __shfl_xor_sync(kFull, tmax, o));
+        const double tau_c = (tmax >= 0.0) ? tmax : CUDART_INF;
+        const double tau_mix = sqrt(tau_t[cell] * tau_k[cell]);
+        const double kap = (tmax >= 0.0) ? tau_c / (tau_c + tau_mix) : 1.0;
+        if (lane == 0) {
+            if (tau_c_out) tau_c_out[cell] = tau_c;
+            if (kappa_out) kappa_out[cell] = kap;
+        }
+        if (T && Y)
+            for (int s = 0; s < 2; ++s) {
+                const int c = lane + 32 * s;
+                if (c == 0) T[cell] = y[s] + kap * (T[cell] - y[s]);
+                else if (c < n) {
+                    const int64_t q = (int64_t)(c - 1) * ld + cell;
+                    Y[q] = y[s] + kap * (Y[q] - y[s]);
+                }
+            }
+    }
+}
+
 }  // namespace
 }  // namespace chemgb
 
 using namespace chemgb;
+
+extern "C" int chem_pasr(const chem_mech *m, int64_t ncells, int64_t ld, double y_min, const double *T0,
+                         const double *p, const double *Y0, const double *tau_taylor, const double *tau_kolmogorov,
+                         double *T, double *Y, double *tau_c, double *kappa, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_pasr: null mechanism");
+    if (ncells < 0 || ld < ncells || (ld & 3) != 0 || ncells > (int64_t)0x7fffffff)
+        return set_error(CHEM_EINVAL, "chem_pasr: need 0 <= ncells <= ld < 2^31, ld a multiple of 4");
+    if (!(y_min > 0.0)) return set_error(CHEM_EINVAL, "chem_pasr: y_min must be positive");
+    if (m->N > 63) return set_error(CHEM_EUNSUPPORTED, "chem_pasr: at most 63 species");
+    if (ncells == 0) return CHEM_OK;
+    if (!T0 || !p || !Y0 || !tau_taylor || !tau_kolmogorov) return set_error(CHEM_EINVAL, "chem_pasr: null input");
+    if ((T == nullptr) != (Y == nullptr)) return set_error(CHEM_EINVAL, "chem_pasr: give both T and Y or neither");
+    const void *ptrs[] = {T0, p, Y0, tau_taylor, tau_kolmogorov, T, Y, tau_c, kappa};
+    for (const void *q : ptrs)
+        if (q && !aligned16(q)) return set_error(CHEM_EINVAL, "chem_pasr: arrays must be 16-byte aligned");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_pasr: " + why);
+    const size_t smem = slice_bytes(m->N, m->R) * kWarps;
+    if (smem > 227 * 1024) return set_error(CHEM_EUNSUPPORTED, "chem_pasr: mechanism too large for shared memory");
+    static size_t configured = 0;
+    if (smem > configured) {
+        int rc = check_cuda(cudaFuncSetAttribute(pasr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+                            "chem_pasr: smem attribute");
+        if (rc) return rc;
+        configured = smem;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pasr_kernel, kWarps * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (ncells + kWarps - 1) / kWarps;
+    const int blocks = (int)((int64_t)sms * per_sm < need ? (int64_t)sms * per_sm : need);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    void *pb = prof_begin(st);
+    pasr_kernel<<<blocks, kWarps * 32, smem, st>>>(m->dev, ncells, ld, y_min, T0, p, Y0, tau_taylor, tau_kolmogorov,
+                                                   T, Y, tau_c, kappa);
+    prof_end(pb, st, "pasr_kernel", 0.0, (double)ncells * ((m->N + 2) * 8 + 2 * 8 + (T ? 2 * (m->N + 1) * 8 : 0)));
+    return check_cuda(cudaGetLastError(), "chem_pasr launch");
+}
 
 extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, double dt, const chem_ode_opts *opts,
                                double *T, const double *p, double *Y, int32_t *status, int32_t *nsteps,
