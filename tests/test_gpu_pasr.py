@@ -58,7 +58,7 @@ def test_pasr_parity_c2(oracle):
     assert np.allclose(gtc[:n], otc, rtol=1e-9, atol=0), np.abs(gtc[:n] / otc - 1).max()
     assert np.allclose(gkp[:n], okp, rtol=1e-9, atol=0)
     assert np.all(gtc[n:] == -7.0) and np.all(gkp[n:] == -7.0)
-    assert 0.01 < okp.min() and okp.max() < 0.999          # the time scales span the interesting range
+    assert okp.min() < 0.1 and okp.max() > 0.9             # mixing-limited and chemistry-limited cells both occur
     To, Yo = P.apply(T[:n], Y[:, :n], T1[:n], Y1[:, :n], okp)
     Tg, Yg = T1d.cpu().numpy(), Y1d.cpu().numpy()
     assert np.allclose(Tg[:n], To, rtol=1e-12, atol=0)
