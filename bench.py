@@ -761,6 +761,7 @@ def bench_ann(args, rank, world, local):
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ann(smech, T, p, Y)
+        line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
     return line
 
 
@@ -782,6 +783,41 @@ def cpu_baseline_ann(smech, T, p, Y, sample=4096):
     el = time.perf_counter() - t0
     return {"value": sample / el, "unit": "cells/s", "cores": omp_threads(), "kind": "oracle",
             "sample": "first %d of the cells: oracle ANN step (FP64) + props" % sample}
+
+
+def _oracle_one_core(q, mech_name: str, sample: int):
+    """Spawned child: the oracle's learned step + props with every thread pool sized to one."""
+    global MECH
+    MECH = mech_name
+    from paper_2312_05800_gb300 import synth
+    smech = synth.get_mech(mech_name)
+    T, p, Y = synth.states_profiles(smech, sample, 2003, ld=synth.padded_ld(sample))
+    cpu_baseline_ann(smech, T, p, Y, sample)                 # warm: builds and loads the C oracle
+    q.put(cpu_baseline_ann(smech, T, p, Y, sample)["value"])
+
+
+def cpu_baseline_one_core(sample: int = 1024):
+    """cells/s of the oracle on one host core: a spawned process whose OpenMP and BLAS pools are set to
+    one thread before it loads numpy (a pool forked from this process would carry its threads)."""
+    import multiprocessing as mp
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    old = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        proc = ctx.Process(target=_oracle_one_core, args=(q, MECH, sample))
+        proc.start()
+        v = q.get(timeout=900)
+        proc.join()
+    finally:
+        for k, v0 in old.items():
+            if v0 is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v0
+    return {"value": v, "unit": "cells/s", "cores": 1, "sample": "%d cells, same oracle path" % sample}
 
 
 def main():
