@@ -217,7 +217,7 @@ int chem_pasr(const chem_mech *mech, int64_t ncells, int64_t ld, double y_min, c
  * Computes, for i < M and n < N,
  *     acc[i][n] = sum_k x[i][k] W[n][k]      (BF16 operands, FP32 accumulation)
  *     act = 0:  y[i][n] = acc + b[n]         (float y)
- *     act = 1:  y[i][n] = GELU(acc + b[n])   (BF16 y, exact erf GELU)
+ *     act = 1:  y[i][n] = GELU(acc + b[n])   (BF16 y; GELU(z) = z Phi(z) to 2e-7 (1 + |z|))
  * x: [M][ldx] BF16, W: [N][ldw] BF16 (row n = output n), b: [N] float or NULL,
  * y: [M][ldy]. ldx and ldw must make rows a multiple of 16 bytes and the bases
  * 16-byte aligned. tile_n selects the output tile width (32, 64, 128, 160, 208
