@@ -271,7 +271,6 @@ class Mlp:
 
     @classmethod
     def load(cls, mech: Mech, path: str) -> "Mlp":
-        import numpy as np
         h = ctypes.c_void_p()
         _check(lib().chem_mlp_load(mech.handle, path.encode(), ctypes.byref(h)))
         self = cls.__new__(cls)
