@@ -64,6 +64,35 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def rank_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest x over the ranks (the slowest rank's time): an all-reduce on the process group's
+    device (CPU tensors under gloo, the rank's GPU under nccl)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = torch.device("cpu") if dist.get_backend() == "gloo" else torch.device("cuda", torch.cuda.current_device())
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time (weak scaling)."""
+    return world * units_per_rank / seconds
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Each rank draws its own cells (independent shards, no collective on the data path)."""
+    return base + 1000 * rank
+
+
 def stiff_flops_per_step(N: int, R: int, n_tb: int, n_troe: int) -> float:
     """Algorithmic FP64 flops of one Rodas3 step (exp/log counted as 20 flops):
     3 right-hand sides (species thermo 20N, per reaction 2 exp + 12, third-body
@@ -147,7 +176,7 @@ def ann_workload(mech) -> str:
 def make_inputs(rank: int, ncells: int = NCELLS):
     from paper_2312_05800_gb300 import synth
     mech = synth.get_mech(MECH)
-    T, p, Y = synth.states_profiles(mech, ncells, SEED + 1000 * rank, ld=synth.padded_ld(ncells))
+    T, p, Y = synth.states_profiles(mech, ncells, shard_seed(SEED, rank), ld=synth.padded_ld(ncells))
     return mech, T, p, Y
 
 
@@ -239,8 +268,7 @@ def bench_stiff(args, rank, world, local):
         step()
     torch.cuda.synchronize()
     assert int((status != 0).sum()) == 0, "cells failed in warm-up"
-    if world > 1:
-        torch.distributed.barrier()
+    rank_barrier(world)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     kev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
@@ -255,16 +283,12 @@ def bench_stiff(args, rank, world, local):
             binding.props_eval(dm, NCELLS, NCELLS, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
             ev[2 * i + 1].record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    rank_barrier(world)
+    torch.cuda.synchronize()
     step_ms = [ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps)]
     kern_ms = [kev[2 * i].elapsed_time(kev[2 * i + 1]) for i in range(args.steps)]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * NCELLS * args.steps / total_s
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world)
+    value = job_rate(NCELLS * args.steps, world, total_s)
     steps_total = float(nsteps.double().sum().item())
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -403,7 +427,7 @@ def bench_ann(args, rank, world, local):
         hist = [float("nan")]
     else:
         t0 = time.perf_counter()
-        data = train.make_training_set(dm, smech, args.train_pairs, seed=2103 + 1000 * rank)
+        data = train.make_training_set(dm, smech, args.train_pairs, seed=shard_seed(2103, rank))
         t_data = time.perf_counter() - t0
         train.fit_norm(net, data)
         t0 = time.perf_counter()
@@ -440,7 +464,7 @@ def bench_ann(args, rank, world, local):
     tiles = binding.chem_mlp_autotune(net, min(args.chunk, 524288))
     # ---- inference workload
     ncells = args.cells
-    T, p, Y = synth.states_profiles(smech, ncells, 2003 + 1000 * rank, ld=synth.padded_ld(ncells))
+    T, p, Y = synth.states_profiles(smech, ncells, shard_seed(2003, rank), ld=synth.padded_ld(ncells))
     ld = T.shape[0]
     T0 = torch.from_numpy(T).to(dev)
     p0 = torch.from_numpy(p).to(dev)
@@ -482,8 +506,7 @@ def bench_ann(args, rank, world, local):
         step()
     torch.cuda.synchronize()
     assert net.error() == 0
-    if world > 1:
-        torch.distributed.barrier()
+    rank_barrier(world)
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     binding.chem_prof_enable(True)
@@ -493,6 +516,8 @@ def bench_ann(args, rank, world, local):
         for _ in range(args.steps):
             step()
         ev[1].record(stream)
+        torch.cuda.synchronize()
+        rank_barrier(world)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
     prof = binding.chem_prof_read()
@@ -630,14 +655,8 @@ def bench_ann(args, rank, world, local):
                     "kernels_ms_per_step": {k: v[1] / ens_steps for k, v in profe.items()},
                     "chunk": args.ens_chunk}
         ens.free()
-    if world > 1:
-        torch.distributed.barrier()
-    total_s = ev[0].elapsed_time(ev[1]) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * ncells * args.steps / total_s
+    total_s = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, world)
+    value = job_rate(ncells * args.steps, world, total_s)
     gemm = {k: v for k, v in prof.items() if k.startswith("gemm_tn")}
     g_ms = sum(v[1] for v in gemm.values())
     g_fl = sum(v[2] for v in gemm.values())
@@ -656,7 +675,7 @@ def bench_ann(args, rank, world, local):
     torch.cuda.synchronize()
     stiff_value = ns / (e0.elapsed_time(e1) / 1e3)
     # ---- batched + fallback: the same cells with 2 % moved off the manifold (T +/- 300 K, Y noise 0.2)
-    T4, Y4, moved = synth.perturb_off_manifold(T, Y, ncells, 0.02, 2004 + 1000 * rank)
+    T4, Y4, moved = synth.perturb_off_manifold(T, Y, ncells, 0.02, shard_seed(2004, rank))
     T4d, Y4d = torch.from_numpy(T4).to(dev), torch.from_numpy(Y4).to(dev)
     Tw.copy_(T4d)
     Yw.copy_(Y4d)
