@@ -828,19 +828,36 @@ def cpu_baseline_one_core(sample: int = 1024):
     old = {k: os.environ.get(k) for k in keys}
     for k in keys:
         os.environ[k] = "1"
+    import queue as queue_mod
+    v, why = None, None
     try:
         ctx = mp.get_context("spawn")
         q = ctx.Queue()
         proc = ctx.Process(target=_oracle_one_core, args=(q, MECH, sample))
         proc.start()
-        v = q.get(timeout=900)
-        proc.join()
+        t_end = time.time() + 600
+        while v is None and time.time() < t_end:
+            try:
+                v = q.get(timeout=2)
+            except queue_mod.Empty:
+                if not proc.is_alive():
+                    why = "the one-core oracle process exited with code %s" % proc.exitcode
+                    break
+        if v is None and why is None:
+            why = "the one-core oracle run exceeded 600 s"
+        proc.join(timeout=30)
+        if proc.is_alive():
+            proc.terminate()
+    except Exception as e:          # the baseline is reported, never allowed to end the run
+        why = "one-core oracle run failed: %s" % e
     finally:
         for k, v0 in old.items():
             if v0 is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v0
+    if v is None:
+        return {"value": None, "unit": "cells/s", "cores": 1, "error": why}
     return {"value": v, "unit": "cells/s", "cores": 1, "sample": "%d cells, same oracle path" % sample}
 
 
