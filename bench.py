@@ -442,6 +442,7 @@ def bench_ann(args, rank, world, local):
         if fp8:
             # E4M3 activation scales from the BF16 forward of training states
             binding.chem_mlp_calibrate_fp8(net, min(data.n, 262144), data.ld, data.T, data.p, data.Y)
+    tiles = binding.chem_mlp_autotune(net, min(args.chunk, 524288))
     # ---- the paper's model form: one network per species (Sec. 3.2), trained on the same pairs
     ens = None
     ens_train = None
@@ -463,7 +464,6 @@ def bench_ann(args, rank, world, local):
     if not args.untrained:
         del data
     fb_opts = binding.make_opts(**STIFF_OPTS)
-    tiles = binding.chem_mlp_autotune(net, min(args.chunk, 524288))
     # ---- inference workload
     ncells = args.cells
     T, p, Y = synth.states_profiles(smech, ncells, shard_seed(2003, rank), ld=synth.padded_ld(ncells))
