@@ -446,20 +446,17 @@ def bench_ann(args, rank, world, local):
     # ---- the paper's model form: one network per species (Sec. 3.2), trained on the same pairs
     ens = None
     ens_train = None
-    if args.ens_epochs > 0:
+    if args.ens_epochs > 0 and not args.untrained:
         ens = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3004, chunk=args.ens_chunk, max_batch=4096, ensemble=True)
-        if args.untrained:
-            ens_train = {"epochs": 0}
-        else:
-            train.fit_norm(ens, data)
-            t0 = time.perf_counter()
-            ens_hist = train.train(ens, data, epochs=args.ens_epochs, batch=4096, lr0=args.lr)
-            torch.cuda.synchronize()
-            ens_train = {"pairs": args.train_pairs, "epochs": args.ens_epochs, "batch": 4096,
-                         "loss_first_epoch": ens_hist[0], "loss_last_epoch": ens_hist[-1],
-                         "train_s": time.perf_counter() - t0}
-            binding.chem_mlp_fit_ood_multi(ens, dm, data.n, data.ld, data.T, data.p, data.Y,
-                                           [smech.roles[r] for r in args.ood_species.split(",")], 64, args.ood_kmin)
+        train.fit_norm(ens, data)
+        t0 = time.perf_counter()
+        ens_hist = train.train(ens, data, epochs=args.ens_epochs, batch=4096, lr0=args.lr)
+        torch.cuda.synchronize()
+        ens_train = {"pairs": args.train_pairs, "epochs": args.ens_epochs, "batch": 4096,
+                     "loss_first_epoch": ens_hist[0], "loss_last_epoch": ens_hist[-1],
+                     "train_s": time.perf_counter() - t0}
+        binding.chem_mlp_fit_ood_multi(ens, dm, data.n, data.ld, data.T, data.p, data.Y,
+                                       [smech.roles[r] for r in args.ood_species.split(",")], 64, args.ood_kmin)
         ens_tiles = binding.chem_mlp_autotune(ens, min(args.ens_chunk, 262144))
     if not args.untrained:
         del data
@@ -888,7 +885,7 @@ def main():
     ap.add_argument("--ood-kmin", type=int, default=1,
                     help="training states the 3x3x3 neighbourhood of a cell's bin must hold for the network")
     ap.add_argument("--ens-epochs", type=int, default=30,
-                    help="epochs of the per-species ensemble's training (0: no ensemble line)")
+                    help="epochs of the per-species ensemble's training (0, or --untrained: no ensemble line)")
     ap.add_argument("--ens-chunk", type=int, default=262144,
                     help="cells per inference chunk of the ensemble (G x 2800 BF16 activations per cell)")
     ap.add_argument("--untrained", action="store_true",
