@@ -394,7 +394,9 @@ int chem_mlp_get_ood_grid(const chem_mlp *mlp, int32_t grid, float *lo3, float *
  * prec: CHEM_PREC_BF16, or CHEM_PREC_FP8 after chem_mlp_calibrate_fp8 /
  * chem_mlp_set_fp8_scales. status [ld] (int32, device, may be NULL) receives
  * CHEM_CELL_OK, or for cells outside the network's training distribution (when
- * the test of chem_mlp_fit_ood is enabled) the stiff fallback's code.
+ * the test of chem_mlp_fit_ood is enabled) the stiff fallback's code. A cell
+ * whose prediction is not finite goes to the fallback too when the test is
+ * enabled; without it, the cell keeps its state with CHEM_CELL_NONFINITE.
  * fallback: stiff options for those cells (NULL = defaults).
  */
 int chem_step_ann(const chem_mech *mech, const chem_mlp *mlp, int64_t ncells, int64_t ld, double dt, int prec,

@@ -249,13 +249,20 @@ __global__ void __launch_bounds__(128, (NMAX <= 32 ? 8 : 4)) epilogue_kernel(int
             h0 = fmaf(y * q2.w, hh, h0);
         }
     }
+    // a non-finite prediction (non-finite weights or statistics, an overflow) never reaches the
+    // state: the sum of the outputs' dY is non-finite exactly when one of them is or they overflow
+    const bool bad = !isfinite(sum);
     if (ood.range) {
-        // a cell outside the training distribution keeps its state and goes to the stiff integrator
-        if (ood_outside(ood, T0, h0, Y, ld, i)) {
+        // a cell outside the training distribution, or with a non-finite prediction, keeps its
+        // state and goes to the stiff integrator
+        if (bad || ood_outside(ood, T0, h0, Y, ld, i)) {
             const unsigned int q = atomicAdd(ood.count, 1u);
             ood.queue[q] = (int32_t)(ood.base + i);
             return;
         }
+    } else if (bad) {
+        if (status) status[i] = CHEM_CELL_NONFINITE;     // without the guard: the state is kept
+        return;
     }
     dyS[bath][t] = -sum;
     float s = 0.0f;
