@@ -349,7 +349,8 @@ int chem_mlp_error(const chem_mlp *mlp, int *host_err);
  * ---------------------------------------------------------------------------
  * The paper has no such guard: it applies its networks to every cell. Here the
  * network is trusted only where it was trained; other cells go to the plain
- * method (chem_step_stiff's integrator), which is both fallback and judge.
+ * method (chem_step_stiff's integrator), which is both the fallback and the
+ * reference for the network's error.
  * chem_mlp_fit_ood builds, from n training states (T, p, Y; device, SoA), an
  * nbins^3 occupancy grid over the per-cell features
  *     (T, h/R = sum_k (Y_k / W_k) H_k/R, Y_species)        (FP32, NASA-7)
