@@ -23,18 +23,30 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "chem_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libchem_oracle.so")
+# ORACLE_SANITIZE=1 loads a build instrumented with AddressSanitizer and UndefinedBehaviorSanitizer
+# (every finding aborts); the process must preload the ASan runtime (the tests do this)
+_SAN_LIB = os.path.join(_BUILD, "libchem_oracle_san.so")
 _lib = None
 
 
-def build(force: bool = False) -> str:
+def _sanitized() -> bool:
+    return os.environ.get("ORACLE_SANITIZE", "") == "1"
+
+
+def build(force: bool = False, sanitize: bool = None) -> str:
     """Compile the C oracle with gcc (-O2, OpenMP). Returns the library path."""
+    if sanitize is None:
+        sanitize = _sanitized()
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".tmp%d" % os.getpid()
-        cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    out = _SAN_LIB if sanitize else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".tmp%d" % os.getpid()
+        flags = (["-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all", "-fno-omit-frame-pointer"]
+                 if sanitize else ["-O2"])
+        cmd = ["gcc"] + flags + ["-std=c99", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 class _Mech(ctypes.Structure):
@@ -53,8 +65,7 @@ class _Opts(ctypes.Structure):
 def lib():
     global _lib
     if _lib is None:
-        build()
-        _lib = ctypes.CDLL(_LIB)
+        _lib = ctypes.CDLL(build())
         vp = ctypes.c_void_p
         L = ctypes.c_long
         d = ctypes.c_double
