@@ -778,7 +778,9 @@ def bench_ann(args, rank, world, local):
             "pasr": pasr_line,
             "props_thermo": props_thermo,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (chunks * 6 + 3),
+            # per step: prologue, four GEMMs and the epilogue per chunk, the fallback launch (with the
+            # guard on) and the properties kernel
+            "gpu_launches": args.steps * (chunks * 6 + (0 if args.untrained else 1) + 1),
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ann(smech, T, p, Y)
