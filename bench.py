@@ -737,8 +737,8 @@ def bench_ann(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": ann_workload(smech),
                        "path": "chem_step_ann_props: BF16 tcgen05 GEMMs (FP32 accumulation); out-of-distribution "
-                               "cells to the FP64 stiff integrator; FP32 properties of the advanced state, run "
-                               "beside the fallback",
+                               "cells to the FP64 stiff integrator; then the FP32 properties of the advanced "
+                               "state, after the fallback",
                        "cells_per_gpu": ncells, "l2": "inputs larger than L2 (1 GB FP64 state)",
                        "parallelism": "replicas" if world > 1 else "1 GPU"},
             "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_throughput_setting_vs_tight_stiff": acc_stiff,

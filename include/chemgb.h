@@ -178,6 +178,9 @@ int chem_step_stiff(const chem_mech *mech, int64_t ncells, int64_t ld, double dt
  *  - The first call on each device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
  *    before any stream capture on the device.
+ *  - That address is kept per device index for the life of the process: after
+ *    a cudaDeviceReset in the same process it is stale, so do not call this
+ *    entry point after resetting the device.
  */
 int chem_step_stiff_noalloc(const chem_mech *mech, int64_t ncells, int64_t ld, double dt, const chem_ode_opts *opts,
                             double *T, const double *p, double *Y, int32_t *status, int32_t *nsteps,
@@ -221,13 +224,9 @@ int chem_pasr(const chem_mech *mech, int64_t ncells, int64_t ld, double y_min, c
  * x: [M][ldx] BF16, W: [N][ldw] BF16 (row n = output n), b: [N] float or NULL,
  * y: [M][ldy]. ldx and ldw must make rows a multiple of 16 bytes and the bases
  * 16-byte aligned. tile_n selects the output tile width (32, 64, 128, 160, 208
- * or 256; 0 = automatic); adding CHEM_TILE_PAIR (widths 128, 160, 208, 256)
- * selects the two-CTA variant, in which a cluster of two CTAs computes
- * 256-row tiles with one tensor-core instruction stream (each CTA holds half
- * of the weight tile). err (device int, may be NULL) receives a non-zero
+ * or 256; 0 = automatic). err (device int, may be NULL) receives a non-zero
  * code if a pipeline wait timed out (the call then returns without a result).
  */
-#define CHEM_TILE_PAIR 0x10000
 int chem_dense_bf16(int64_t M, int N, int K, const void *x, int64_t ldx, const void *W, int64_t ldw,
                     const float *b, int act, void *y, int64_t ldy, int tile_n, int *err, chem_stream_t stream);
 

@@ -38,7 +38,6 @@ class chem_mlp_desc(ctypes.Structure):
 
 
 CHEM_PREC_BF16, CHEM_PREC_FP8 = 0, 1
-CHEM_TILE_PAIR = 0x10000
 
 
 def library_path() -> str:

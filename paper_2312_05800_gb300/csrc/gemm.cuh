@@ -565,200 +565,3 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 }
 
 }  // namespace chemgb
-
-// ---- two-CTA variant ---------------------------------------------------------
-//
-// The same contraction on CTA pairs (clusters of two): one MMA instruction of
-// the pair computes a 256 x BN tile (tcgen05 cta_group::2, M = 256). Each CTA
-// loads its own 128 rows of A and half of the BN rows of B, so a pipeline stage
-// takes 16 KB + BN x 64 B of shared memory per CTA instead of 16 KB + BN x 128 B:
-// six stages fit where four did, and B is read from L2 once per pair. The
-// first CTA of the pair (rank 0) issues the MMAs; its commits arrive on both
-// CTAs' barriers. Both CTAs' producers arrive on rank 0's full barriers, both
-// CTAs' epilogues on rank 0's TMEM-empty barriers. Each CTA's TMEM holds the
-// accumulator rows of its own 128 rows, so the epilogue is the single-CTA one.
-
-namespace chemgb {
-
-template <int BN, int STAGES>
-struct GemmPairSmem {
-    static constexpr uint32_t kABytes = kBM * 128;             // 128 rows x 128 bytes of K
-    static constexpr uint32_t kBBytes = (BN / 2) * 128;        // this CTA's half of B
-    static constexpr uint32_t kTiles = STAGES * (kABytes + kBBytes);
-    static constexpr uint32_t kStaging = kEpiWarps * 2 * kStageBytesPerWarp;
-    static constexpr uint32_t kBars = (2 * STAGES + 5) * 8 + 16;
-    static constexpr uint32_t kTotal = 1024 + kTiles + kStaging + kBars;
-    static_assert(kBBytes % 1024 == 0, "half B tile must keep 1024-byte alignment");
-};
-
-template <int BN, int STAGES, class Epi>
-__global__ void __launch_bounds__(kGemmThreads, 1)
-    gemm_tn_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                        const __grid_constant__ CUtensorMap tmC, int M, int N, int K, Epi epi, int *err) {
-    static_assert(BN % 16 == 0 && BN >= 32 && BN <= 256, "UMMA N for M = 256");
-    using L = GemmPairSmem<BN, STAGES>;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + STAGES * L::kABytes;
-    uint8_t *staging = smem + L::kTiles;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::kTiles + L::kStaging);
-    uint64_t *full = bars;
-    uint64_t *empty = bars + STAGES;
-    uint64_t *tfull = bars + 2 * STAGES;
-    uint64_t *tempty = tfull + 2;
-    uint64_t *drain = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t rank = tc::cluster_ctarank();
-    const int pair = blockIdx.x >> 1, npairs = gridDim.x >> 1;
-    const int m_pairs = (M + 2 * kBM - 1) / (2 * kBM), n_tiles = (N + BN - 1) / BN;
-    const int tiles = m_pairs * n_tiles;
-    constexpr int kBKe = Epi::kF8 ? kBK8 : kBK;
-    const int kblocks = (K + kBKe - 1) / kBKe;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) { tc::mbar_init(&full[s], 2); tc::mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { tc::mbar_init(&tfull[a], 1); tc::mbar_init(&tempty[a], 2 * kEpiWarps); }
-        tc::mbar_init(drain, 1);
-        tc::fence_barrier_init();
-    }
-    if (warp == 1) {
-        tc::tmem_alloc_pair(tmem_slot, kTmemCols);
-        tc::tmem_relinquish_pair();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::cluster_sync();          // both CTAs' barriers exist before any cross-CTA arrival
-    tc::tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-
-    if (warp == 0) {
-        if (lane == 0) {
-            tc::tma_prefetch_desc(&tmA);
-            tc::tma_prefetch_desc(&tmB);
-            int it = 0;
-            bool ok = true;
-            for (int tile = pair; tile < tiles && ok; tile += npairs) {
-                const int m_pair = tile / n_tiles, n_blk = tile % n_tiles;
-                for (int kb = 0; kb < kblocks; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!tc::mbar_wait_cluster(&empty[s], ph ^ 1u)) {
-                        atomicExch(err, tc::kErrTimeoutEmpty);
-                        ok = false;
-                        break;
-                    }
-                    const uint32_t fb = tc::mapa_shared(tc::smem_u32(&full[s]), 0);
-                    tc::mbar_arrive_expect_tx_cluster(fb, L::kABytes + L::kBBytes);
-                    tc::tma_load_2d_pair(sA + s * L::kABytes, &tmA, fb, kb * kBKe, (2 * m_pair + (int)rank) * kBM);
-                    tc::tma_load_2d_pair(sB + s * L::kBBytes, &tmB, fb, kb * kBKe, n_blk * BN + (int)rank * (BN / 2));
-                }
-            }
-            // rank 0 sees every issued load of the pair land before the pair may exit (bounded);
-            // rank 1 waits for rank 0 at the closing cluster barrier
-            if (rank == 0)
-                for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
-                    if (!tc::mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) {
-                        atomicExch(err, tc::kErrTimeoutDrain);
-                        break;
-                    }
-        }
-    } else if (warp == 1) {
-        if (lane == 0 && rank == 0) {
-            constexpr uint32_t idesc = Epi::kF8 ? tc::idesc_e4m3_f32(2 * kBM, BN) : tc::idesc_bf16_f32(2 * kBM, BN);
-            int it = 0, t = 0;
-            bool ok = true;
-            for (int tile = pair; tile < tiles && ok; tile += npairs, ++t) {
-                const int acc = t & 1;
-                const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-                if (!tc::mbar_wait_cluster(&tempty[acc], aph ^ 1u)) { atomicExch(err, tc::kErrTimeoutTmemEmpty); break; }
-                tc::tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)acc * 256u;
-                for (int kb = 0; kb < kblocks; ++kb, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!tc::mbar_wait_cluster(&full[s], ph)) { atomicExch(err, tc::kErrTimeoutFull); ok = false; break; }
-                    tc::tc_fence_after();
-                    const uint32_t a0 = tc::smem_u32(sA + s * L::kABytes);
-                    const uint32_t b0 = tc::smem_u32(sB + s * L::kBBytes);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ad = tc::sdesc_kmajor_sw128(a0 + kk * 32), bd = tc::sdesc_kmajor_sw128(b0 + kk * 32);
-                        if (Epi::kF8) tc::umma_f8_pair(d_tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                        else tc::umma_f16_pair(d_tmem, ad, bd, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
-                    }
-                    tc::umma_commit_pair(&empty[s], 0x3);
-                }
-                if (!ok) break;
-                tc::umma_commit_pair(&tfull[acc], 0x3);
-            }
-            // all MMAs issued by this thread complete before TMEM is released (bounded)
-            tc::umma_commit_pair(drain, 0x1);
-            if (!tc::mbar_wait(drain, 0)) atomicExch(err, tc::kErrTimeoutDrain);
-        }
-    } else {
-        const int quad = warp & 3;
-        const int group = (warp - 2) >> 2;
-        const bool tma = epi.tma_store();
-        uint8_t *my_stage = staging + (size_t)(warp - 2) * 2 * kStageBytesPerWarp;
-        int nstore = 0;
-        if (tma && lane == 0) tc::tma_prefetch_desc(&tmC);
-        const uint32_t tempty0 = tc::mapa_shared(tc::smem_u32(&tempty[0]), 0);
-        const uint32_t tempty1 = tc::mapa_shared(tc::smem_u32(&tempty[1]), 0);
-        int t = 0;
-        for (int tile = pair; tile < tiles; tile += npairs, ++t) {
-            const int acc = t & 1;
-            const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-            if (!__all_sync(0xffffffffu, tc::mbar_wait_cluster(&tfull[acc], aph))) {
-                if (lane == 0) atomicExch(err, tc::kErrTimeoutTmemFull);
-                break;
-            }
-            tc::tc_fence_after();
-            const int m_pair = tile / n_tiles, n_blk = tile % n_tiles;
-            const int row0 = (2 * m_pair + (int)rank) * kBM + quad * 32;
-            const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u;
-#pragma unroll 1
-            for (int c = group; c < BN / 16; c += kEpiWarps / 4) {
-                const int col0 = n_blk * BN + c * 16;
-                if (col0 >= N) break;               // warp-uniform
-                float v[16];
-                tc::tmem_ld16(tbase + (uint32_t)(c * 16), v);
-                if (tma) {
-                    if (row0 >= M) continue;            // warp-uniform: nothing of this slice is in range
-                    uint32_t w[8];
-                    epi.compute(col0, v, w);
-                    uint8_t *buf = my_stage + (nstore & 1) * kStageBytesPerWarp;
-                    if (nstore >= 2 && lane == 0) tc::bulk_wait_read<1>();
-                    __syncwarp();
-                    uint4 *dst = reinterpret_cast<uint4 *>(buf + lane * Epi::kOutBytes);
-                    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-                    if (Epi::kOutBytes == 32) dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
-                    tc::fence_proxy_async_smem();
-                    __syncwarp();
-                    if (lane == 0) {
-                        tc::tma_store_2d(&tmC, buf, col0, row0);
-                        tc::bulk_commit();
-                    }
-                    ++nstore;
-                } else {
-                    epi(row0 + lane, col0, v);
-                }
-            }
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive_cluster(acc ? tempty1 : tempty0);
-        }
-        if (tma && lane == 0) tc::bulk_wait<0>();
-        __syncwarp();
-    }
-    __syncthreads();
-    tc::cluster_sync();          // neither CTA exits while the other may still signal its barriers
-    if (warp == 1) {
-        tc::tc_fence_after();
-        tc::tmem_dealloc_pair(tmem, kTmemCols);
-    }
-}
-
-}  // namespace chemgb

@@ -182,63 +182,8 @@ int launch_gemm_grouped_bn(const GemmOperand &A, const GemmOperand &B, int G, in
     return check_cuda(cudaGetLastError(), "GEMM launch");
 }
 
-// Two-CTA variant (clusters of two, M = 256 per MMA); grid = 2 x pairs.
-template <int BN, int STAGES, class Epi>
-int launch_gemm_pair_bn(const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K, const Epi &epi,
-                        int *err, cudaStream_t st, int max_ctas) {
-    using L = GemmPairSmem<BN, STAGES>;
-    static bool configured = false;
-    if (!configured) {
-        int rc = check_cuda(cudaFuncSetAttribute(gemm_tn_pair_kernel<BN, STAGES, Epi>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::kTotal),
-                            "GEMM (pair) smem attribute");
-        if (rc) return rc;
-        configured = true;
-    }
-    CUtensorMap ta, tb;
-    const int esize = Epi::kF8 ? 1 : 2;
-    int rc = make_tmap_operand(&ta, X, M, K, ldx, kBM, esize);
-    if (rc) return rc;
-    rc = make_tmap_operand(&tb, W, N, K, ldw, BN / 2, esize);
-    if (rc) return rc;
-    CUtensorMap tc;
-    std::memset(&tc, 0, sizeof(tc));
-    if (const void *op = epi.tma_ptr()) {
-        rc = make_tmap_out(&tc, op, M, N, epi.ldo, Epi::kOutBytes / 16);
-        if (rc) return rc;
-    }
-    const int tiles = ((M + 2 * kBM - 1) / (2 * kBM)) * ((N + BN - 1) / BN);
-    int pairs = num_sms() / 2;
-    if (max_ctas > 0 && max_ctas / 2 < pairs) pairs = max_ctas / 2 > 0 ? max_ctas / 2 : 1;
-    if (tiles < pairs) pairs = tiles;
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof(cfg));
-    cfg.gridDim = dim3(2 * pairs, 1, 1);
-    cfg.blockDim = dim3(kGemmThreads, 1, 1);
-    cfg.dynamicSmemBytes = L::kTotal;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    void *pb = prof_begin(st);
-    rc = check_cuda(cudaLaunchKernelEx(&cfg, gemm_tn_pair_kernel<BN, STAGES, Epi>, ta, tb, tc, M, N, K, epi, err),
-                    "GEMM (pair) launch");
-    if (pb)
-        prof_end(pb, st, "gemm_tn_pair_kernel<" + std::to_string(BN) + (Epi::kF8 ? ",e4m3> " : "> ") +
-                             std::to_string(N) + "x" + std::to_string(K),
-                 2.0 * M * N * K, (double)esize * ((double)M * K + (double)N * K));
-    return rc;
-}
-
-// Tile widths the library is built with (the autotuner picks among them). A tile code is the
-// width, plus kPairTile for the two-CTA variant (widths 128, 160, 208, 256).
+// Tile widths the library is built with (the autotuner picks among them).
 constexpr int kTileWidths[] = {32, 64, 128, 160, 208, 256};
-constexpr int kPairTile = 0x10000;
-constexpr int kPairWidths[] = {128, 160, 208, 256};
 
 // G products in one launch (single-CTA tiles only).
 template <class Epi>
@@ -264,15 +209,6 @@ template <class Epi>
 int launch_gemm(int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N, int K,
                 const Epi &epi, int *err, cudaStream_t st, int max_ctas = 0) {
     if (M <= 0 || N <= 0 || K <= 0) return CHEM_OK;
-    if (bn & kPairTile) {
-        switch (bn & 0xFFFF) {
-            case 128: return launch_gemm_pair_bn<128, 8>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
-            case 160: return launch_gemm_pair_bn<160, 7>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
-            case 208: return launch_gemm_pair_bn<208, 6>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
-            case 256: return launch_gemm_pair_bn<256, 6>(X, ldx, W, ldw, M, N, K, epi, err, st, max_ctas);
-            default: return set_error(CHEM_EINVAL, "GEMM: unsupported pair tile width " + std::to_string(bn & 0xFFFF));
-        }
-    }
     return launch_gemm_grouped(bn, GemmOperand{X, ldx, kMap2D, 0}, GemmOperand{W, ldw, kMap2D, 0}, 1, kMap2D, 0, M, N,
                                K, epi, err, st, max_ctas);
 }

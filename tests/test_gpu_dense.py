@@ -75,39 +75,6 @@ def test_dense_every_tile_width(tile_n):
     _case(515, 450, 200, 0, tile_n, tile_n + 1)
 
 
-PAIR = 0x10000   # tile code of the two-CTA variant (clusters of two, M = 256 per MMA)
-
-
-@pytest.mark.parametrize("tile_n", [128, 160, 208, 256])
-def test_dense_pair_tiles(tile_n):
-    # ragged M (odd number of 128-row tiles: the second CTA of the last pair computes on zero rows),
-    # ragged N and K, one pair tile and many pair tiles per persistent pair
-    _case(515, 450, 200, 1, tile_n | PAIR, 3 * tile_n)
-    _case(515, 450, 200, 0, tile_n | PAIR, 3 * tile_n + 1)
-    _case(20000, 800, 1600, 1, tile_n | PAIR, 3 * tile_n + 2)
-    _case(129, 1024, 2048, 1, tile_n | PAIR, 3 * tile_n + 3)
-
-
-def test_pair_tiles_are_bitwise_single_tiles():
-    # the same K order per output element: a 256-row pair tile gives the single-CTA bits
-    import torch
-    from paper_2312_05800_gb300 import binding
-    g = torch.Generator().manual_seed(5)
-    M, N, K = 20000, 800, 1600
-    x = (torch.randn(M, K, generator=g) * 0.7).to(torch.bfloat16).cuda()
-    W = (torch.randn(N, K, generator=g) / math.sqrt(K)).to(torch.bfloat16).cuda()
-    b = (torch.randn(N, generator=g) * 0.1).cuda()
-    err = torch.zeros(4, dtype=torch.int32, device="cuda")
-    outs = []
-    for tile in (208, 208 | PAIR, 256 | PAIR):
-        y = torch.empty((M, N), dtype=torch.bfloat16, device="cuda")
-        binding.chem_dense_bf16(M, N, K, x, K, W, K, b, 1, y, N, tile, err)
-        outs.append(y)
-    torch.cuda.synchronize()
-    assert int(err[0].item()) == 0
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
-
-
 def _bf16_round(a):
     a = np.ascontiguousarray(a, dtype=np.float32)
     b = a.view(np.uint32).astype(np.uint64)

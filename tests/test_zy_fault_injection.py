@@ -5,7 +5,8 @@ out-of-distribution guard every cell keeps its state, bit for bit, with status
 CHEM_CELL_NONFINITE; with the guard every cell goes to the stiff fallback, whose
 result equals chem_step_stiff's with the same options (status CHEM_CELL_FALLBACK).
 Non-finite states and a step budget of one step are covered by the stiff tests
-(status codes 4 and 2). The file runs last, after every parity test."""
+(status codes 4 and 2). The file runs after every parity test (only the
+allocation-free entry point's test comes later)."""
 import numpy as np
 import pytest
 
