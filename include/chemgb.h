@@ -340,8 +340,21 @@ int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
  * Synchronises the stream; results are bitwise
  * the same for every tile width. */
 int chem_mlp_autotune(chem_mlp *mlp, int64_t rows, int32_t *tiles_out, chem_stream_t stream);
-/* Sticky error word of the network's pipeline waits (0 = none); synchronises the device. */
+/* Sticky error word of the network's pipeline waits (0 = none); synchronises the device.
+ * Codes: 1 a k-block's operands did not arrive, 2 a pipeline stage was not
+ * released, 3 an accumulator was not completed, 4 an accumulator was not
+ * released (the tensor-core GEMM's producer, MMA and epilogue roles), 5 a
+ * closing drain did not finish. After a non-zero code the network's results
+ * are undefined; the word stays set for the life of the handle. */
 int chem_mlp_error(const chem_mlp *mlp, int *host_err);
+/* Bounded waits (no counterpart in the paper; a failure-detection aid). Every
+ * wait of the network's tensor-core pipeline is a loop of at most `tries`
+ * mbarrier try_wait operations (0 = the default, 2^22, seconds in total);
+ * one that runs out records its code in the error word and the kernel
+ * unwinds: it waits (always with the default limit) for the copies and
+ * tensor-core operations it has issued, frees its tensor memory and returns.
+ * A small limit makes waits run out on purpose, to test that path. */
+int chem_mlp_set_wait_limit(chem_mlp *mlp, uint32_t tries);
 
 /* ---------------------------------------------------------------------------
  * Out-of-distribution test and stiff fallback of the learned step

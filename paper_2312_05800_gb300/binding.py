@@ -85,6 +85,7 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_calibrate_fp8.argtypes = [vp, i64, i64, vp, vp, vp, vp]
     L.chem_mlp_get_fp8_weights.argtypes = [vp, i32, vp, vp]
     L.chem_mlp_error.argtypes = [vp, vp]
+    L.chem_mlp_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
     L.chem_mlp_fit_ood.argtypes = [vp, vp, i64, i64, vp, vp, vp, i32, i32, i32, vp]
     L.chem_mlp_fit_ood_multi.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, i32, i32, i32, vp]
     L.chem_mlp_get_ood_grid.argtypes = [vp, i32, vp, vp, vp]
@@ -281,6 +282,9 @@ class Mlp:
         e = ctypes.c_int()
         _check(lib().chem_mlp_error(self.handle, ctypes.byref(e)))
         return e.value
+
+    def set_wait_limit(self, tries: int):
+        _check(lib().chem_mlp_set_wait_limit(self.handle, int(tries)))
 
     def free(self):
         if self.handle:

@@ -50,6 +50,8 @@ enum : int { kMap2D = 0, kMapRowGrp = 1, kMapColGrp = 2 };
 struct GemmGroups {
     int count;           // G >= 1
     int a, b, c;         // map kinds of X, W and the TMA-store output
+    uint32_t spin;       // tries of a pipeline wait before it gives up (the closing drains always
+                         // take tc::kSpinLimit, so that nothing is in flight when the CTA exits)
 };
 
 // load one box of a (k, row) tile of group g from a map of the given kind
@@ -454,7 +456,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!tc::mbar_wait(&empty[s], ph ^ 1u)) { atomicExch(err, tc::kErrTimeoutEmpty); ok = false; break; }
+                    if (!tc::mbar_wait(&empty[s], ph ^ 1u, grp.spin)) { atomicExch(err, tc::kErrTimeoutEmpty); ok = false; break; }
                     tc::mbar_arrive_expect_tx(&full[s], L::kABytes + L::kBBytes);
                     load_tile(sA + s * L::kABytes, &tmA, &full[s], grp.a, kb * kBKe, m_blk * kBM, g);
                     load_tile(sB + s * L::kBBytes, &tmB, &full[s], grp.b, kb * kBKe, n_blk * BN, g);
@@ -475,13 +477,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x, ++t) {
                 const int acc = t & 1;
                 const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-                if (!tc::mbar_wait(&tempty[acc], aph ^ 1u)) { atomicExch(err, tc::kErrTimeoutTmemEmpty); break; }
+                if (!tc::mbar_wait(&tempty[acc], aph ^ 1u, grp.spin)) { atomicExch(err, tc::kErrTimeoutTmemEmpty); break; }
                 tc::tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)acc * 256u;
                 for (int kb = 0; kb < kblocks; ++kb, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                    if (!tc::mbar_wait(&full[s], ph)) { atomicExch(err, tc::kErrTimeoutFull); ok = false; break; }
+                    if (!tc::mbar_wait(&full[s], ph, grp.spin)) { atomicExch(err, tc::kErrTimeoutFull); ok = false; break; }
                     tc::tc_fence_after();
                     const uint32_t a0 = tc::smem_u32(sA + s * L::kABytes);
                     const uint32_t b0 = tc::smem_u32(sB + s * L::kBBytes);
@@ -512,7 +514,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++t) {
             const int acc = t & 1;
             const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[acc], aph))) {   // warp-uniform outcome
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&tfull[acc], aph, grp.spin))) {   // warp-uniform outcome
                 if (lane == 0) atomicExch(err, tc::kErrTimeoutTmemFull);
                 break;
             }

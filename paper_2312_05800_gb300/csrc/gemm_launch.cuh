@@ -90,6 +90,21 @@ inline int make_operand_map(CUtensorMap *map, const GemmOperand &op, int64_t row
     return make_tmap_operand_grouped(map, op, rows, cols, G, box_rows, esize);
 }
 
+// Tries of each pipeline wait of the GEMMs launched by this host thread (tc::kSpinLimit unless a
+// network handle with a smaller limit is launching; see WaitLimitScope).
+inline uint32_t &gemm_wait_limit() {
+    static thread_local uint32_t limit = tc::kSpinLimit;
+    return limit;
+}
+// Sets this thread's GEMM wait limit for the lifetime of the object, then restores it.
+struct WaitLimitScope {
+    uint32_t saved;
+    explicit WaitLimitScope(uint32_t limit) : saved(gemm_wait_limit()) { gemm_wait_limit() = limit; }
+    ~WaitLimitScope() { gemm_wait_limit() = saved; }
+    WaitLimitScope(const WaitLimitScope &) = delete;
+    WaitLimitScope &operator=(const WaitLimitScope &) = delete;
+};
+
 inline int num_sms() {
     static int sms = 0;
     if (sms == 0) {
@@ -171,7 +186,7 @@ int launch_gemm_grouped_bn(const GemmOperand &A, const GemmOperand &B, int G, in
     int grid = num_sms();
     if (max_ctas > 0 && max_ctas < grid) grid = max_ctas;
     if (tiles < grid) grid = tiles;
-    const GemmGroups grp{G, A.kind, B.kind, out_kind};
+    const GemmGroups grp{G, A.kind, B.kind, out_kind, gemm_wait_limit()};
     void *pb = prof_begin(st);
     gemm_tn_kernel<BN, STAGES, Epi><<<grid, kGemmThreads, L::kTotal, st>>>(ta, tb, tc, M, N, K, grp, epi, err);
     if (pb)

@@ -102,6 +102,7 @@ struct chem_mlp {
     size_t blob_bytes;
     int device;
     uint64_t seed;
+    uint32_t wait_limit;                    // tries of each GEMM pipeline wait (chem_mlp_set_wait_limit)
 };
 
 namespace chemgb {
@@ -743,6 +744,7 @@ int ens_output(const chem_mlp *m, int64_t n, const __nv_bfloat16 *h, float *u, c
 // h3 as BF16 for the BF16 output layer.
 int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *p, const double *Y,
                   cudaStream_t st, int prec = CHEM_PREC_BF16, int nlayers = kLayers) {
+    WaitLimitScope wl(m->wait_limit);
     void *pb = prof_begin(st);
     prologue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, T, p, Y, nullptr, m->N, m->n_in_pad, m->mu_x,
                                                                  m->isd_x, m->a0);
@@ -854,6 +856,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     m->chunk = (m->chunk + 127) / 128 * 128;
     m->max_batch = desc->max_batch > 0 ? (desc->max_batch + 7) / 8 * 8 : 4096;
     m->seed = seed;
+    m->wait_limit = tc::kSpinLimit;
     m->widths[0] = m->n_in;
     for (int i = 0; i < 3; ++i) m->widths[1 + i] = desc->n_hidden[i];
     m->widths[4] = m->n_out;
@@ -1464,6 +1467,7 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     std::string why;
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "mlp_train_step: " + why);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    WaitLimitScope wl(m->wait_limit);
     const int B = (int)batch;
     // forward with saved pre-activations
     prologue_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, ld, T, p, Y, idx, m->N, m->n_in_pad, m->mu_x, m->isd_x, m->tx0);
@@ -1531,6 +1535,12 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
                                                                  L.vW, L.mb, L.vb, L.Wb, L.Wt, lr, bc1, bc2);
     }
     return check_cuda(cudaGetLastError(), "train adam");
+}
+
+extern "C" int chem_mlp_set_wait_limit(chem_mlp *m, uint32_t tries) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_set_wait_limit: null handle");
+    m->wait_limit = tries == 0 ? tc::kSpinLimit : tries;
+    return CHEM_OK;
 }
 
 extern "C" int chem_mlp_error(const chem_mlp *m, int *host_err) {
@@ -1695,6 +1705,7 @@ extern "C" int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp *
 // ---------------------------------------------------------------------------
 extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, chem_stream_t stream) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_autotune: null handle");
+    WaitLimitScope wl(m->wait_limit);
     if (rows < 128) rows = 128;
     if (rows > m->chunk) rows = m->chunk;
     std::string why;

@@ -7,8 +7,9 @@ layers 1600, 800, 400, each trained on its own output) on the GPU against the or
   several chunks and a ragged tail. Bound as for the multi-output network: 99.99 %
   within 1e-2 (|u| + rms u), all within 3e-2 (|u| + rms u).
 * chem_step_ann on an ensemble: Y', T' against the oracle step.
-* Training: the gradients of one step against the oracle's per-network backward
-  (cosine >= 0.999, relative L2 <= 3e-2 per layer), the L1 sign taken on the BF16 forward.
+* Training: the gradients of one step against the oracle's per-network backward,
+  element by element within 8 standard deviations of the device's BF16 rounding
+  (tests/grad_bounds.py), with the norms as a summary.
 * The autotuner's tile widths change no output bit; a checkpoint restores the ensemble
   exactly; E4M3 requests are refused.
 Weights, statistics and states come from the seeded generator, never from the GPU.
@@ -129,34 +130,45 @@ def test_ensemble_step_ann_parity():
 
 @pytest.mark.parametrize("hidden", [(256, 128, 64), (104, 56, 24)])
 def test_ensemble_train_gradients_match_oracle(hidden):
+    # Each network's gradients against the oracle's backward of its own Eq. 5 term, element by
+    # element within 8 standard deviations of the device's BF16 rounding (tests/grad_bounds.py),
+    # norms as a summary; targets keep every residual at least 0.5 rms(u) from zero.
     import torch
     from paper_2312_05800_gb300 import binding
+    from tests.grad_bounds import check, gradients_with_sigma, separated_targets
     B = 512
     mech, T, p, Y, widths, nets, stats = _problem(B, hidden, seed=2045)
-    dY = np.random.default_rng(5).normal(size=Y.shape) * stats[3].mean()
+    mu_x, sd_x, mu_u, sd_u = stats
+    z = (M.features(T[:B], p[:B], Y[:, :B]) - mu_x) / sd_x
+    uq = A.network_ensemble(nets, np.asarray(z, np.float32).astype(np.float64), round_bf16=True)
+    target = separated_targets(uq, np.random.default_rng(5))
+    sp = A.out_species(mech)
+    Y1 = Y.copy()
+    Y1[sp, :B] += (target * sd_u + mu_u).T
     net = _ens(widths, nets, stats, max_batch=B)
     ld = T.shape[0]
     loss = torch.zeros(4, dtype=torch.float32, device="cuda")
-    binding.mlp_train_step(net, B, None, ld, to_dev(T), to_dev(p), to_dev(Y), to_dev(Y + dY), 0.0, loss)
+    binding.mlp_train_step(net, B, None, ld, to_dev(T), to_dev(p), to_dev(Y), to_dev(Y1), 0.0, loss)
     torch.cuda.synchronize()
     assert net.error() == 0
     G = widths[4]
     grads = synth.unstack_ensemble(_restack(net.get_grads(), widths, G), G)
-    mu_x, sd_x, mu_u, sd_u = stats
-    z = (M.features(T[:B], p[:B], Y[:, :B]) - mu_x) / sd_x
-    sp = A.out_species(mech)
-    target = ((((Y + dY) - Y)[sp, :B].T) - mu_u) / sd_u
-    uq = A.network_ensemble(nets, np.asarray(z, np.float32).astype(np.float64), round_bf16=True)
-    lo, go = M.ensemble_grads([[{"W": W.copy(), "b": b.copy()} for W, b in n_] for n_ in nets], z, target,
-                              sign_from=uq)
-    assert abs(float(loss[0].item()) - lo) <= 2e-2 * lo
+    total = 0.0
+    ga, gb = [[] for _ in range(4)], [[] for _ in range(4)]
+    for g in range(G):
+        lo, go, sig, min_res = gradients_with_sigma(nets[g], z, target[:, g:g + 1], uq[:, g:g + 1])
+        total += lo
+        for l in range(4):
+            for j in range(2):
+                check(grads[g][l][j], go[l][j], sig[l][j], "network %d layer %d %s" % (g, l + 1, "dW" if j == 0 else "db"))
+            ga[l].append(grads[g][l][0].ravel())
+            gb[l].append(go[l][0].ravel())
+    assert abs(float(loss[0].item()) - total) <= 2e-2 * total
     for l in range(4):
-        for key, j in (("W", 0), ("b", 1)):
-            a = np.concatenate([grads[g][l][j].ravel() for g in range(G)])
-            b = np.concatenate([go[g][l][key].ravel() for g in range(G)])
-            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
-            rel = np.linalg.norm(a - b) / np.linalg.norm(b)
-            assert cos >= 0.999 and rel <= 3e-2, (l, key, cos, rel)
+        a, b = np.concatenate(ga[l]), np.concatenate(gb[l])
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert cos >= 0.9999 and rel <= 1e-2, (l, cos, rel)
     net.free()
 
 
