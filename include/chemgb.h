@@ -220,7 +220,7 @@ int chem_pasr(const chem_mech *mech, int64_t ncells, int64_t ld, double y_min, c
  * Computes, for i < M and n < N,
  *     acc[i][n] = sum_k x[i][k] W[n][k]      (BF16 operands, FP32 accumulation)
  *     act = 0:  y[i][n] = acc + b[n]         (float y)
- *     act = 1:  y[i][n] = GELU(acc + b[n])   (BF16 y; GELU(z) = z Phi(z) to 2e-7 (1 + |z|))
+ *     act = 1:  y[i][n] = GELU(acc + b[n])   (BF16 y; GELU(z) = z Phi(z) to 4e-6 (1 + |z|))
  * x: [M][ldx] BF16, W: [N][ldw] BF16 (row n = output n), b: [N] float or NULL,
  * y: [M][ldy]. ldx and ldw must make rows a multiple of 16 bytes and the bases
  * 16-byte aligned. tile_n selects the output tile width (32, 64, 128, 160, 208
@@ -340,6 +340,18 @@ int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
  * Synchronises the stream; results are bitwise
  * the same for every tile width. */
 int chem_mlp_autotune(chem_mlp *mlp, int64_t rows, int32_t *tiles_out, chem_stream_t stream);
+/* Layer fusion of the BF16 forward (no counterpart in the paper). With on = 1
+ * (the default) the multi-output network's first two hidden layers run as one
+ * tensor-core launch in which h1 is made on chip, 64 columns at a time, and
+ * consumed at once as layer 2's operand, so it never round-trips through
+ * memory; the results are bitwise those of the two separate layers. It applies
+ * when the first layer's K is 64 (the two BF16 terms of at most 32 inputs,
+ * i.e. at most 30 species), h1 is a multiple of 64 and h2 a multiple of 16;
+ * otherwise, for E4M3, for training and for the per-species ensemble the layers
+ * run one by one. chem_mlp_autotune times both and keeps the faster.
+ * chem_mlp_get_fusion returns 1 when the forward runs fused, 0 otherwise. */
+int chem_mlp_set_fusion(chem_mlp *mlp, int on);
+int chem_mlp_get_fusion(const chem_mlp *mlp);
 /* Sticky error word of the network's pipeline waits (0 = none); synchronises the device.
  * Codes: 1 a k-block's operands did not arrive, 2 a pipeline stage was not
  * released, 3 an accumulator was not completed, 4 an accumulator was not

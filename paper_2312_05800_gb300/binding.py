@@ -86,6 +86,8 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_get_fp8_weights.argtypes = [vp, i32, vp, vp]
     L.chem_mlp_error.argtypes = [vp, vp]
     L.chem_mlp_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
+    L.chem_mlp_set_fusion.argtypes = [vp, i32]
+    L.chem_mlp_get_fusion.argtypes = [vp]
     L.chem_mlp_fit_ood.argtypes = [vp, vp, i64, i64, vp, vp, vp, i32, i32, i32, vp]
     L.chem_mlp_fit_ood_multi.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, i32, i32, i32, vp]
     L.chem_mlp_get_ood_grid.argtypes = [vp, i32, vp, vp, vp]
@@ -285,6 +287,16 @@ class Mlp:
 
     def set_wait_limit(self, tries: int):
         _check(lib().chem_mlp_set_wait_limit(self.handle, int(tries)))
+
+    def set_fusion(self, on: bool):
+        _check(lib().chem_mlp_set_fusion(self.handle, 1 if on else 0))
+
+    @property
+    def fused(self) -> bool:
+        r = lib().chem_mlp_get_fusion(self.handle)
+        if r < 0:
+            _check(r)
+        return bool(r)
 
     def free(self):
         if self.handle:

@@ -13,7 +13,7 @@ of their FP32 Horner evaluation. Run: python fit_erfcx.py
 import numpy as np
 from scipy.special import erfcx
 
-DEG = 11
+DEG = 7
 X = 4.5 / np.sqrt(2.0)
 
 

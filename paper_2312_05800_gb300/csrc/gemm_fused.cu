@@ -1,0 +1,62 @@
+// gemm_fused.cu -- host launch of gemm_fused12_kernel (the network's first two
+// layers in one persistent launch, h1 kept on chip; see gemm_fused.cuh).
+#include "gemm_fused.cuh"
+#include "gemm_launch.cuh"
+
+namespace chemgb {
+namespace {
+
+template <int NP>
+int launch_fused12_np(const void *X, int64_t ldx, const void *W1, int64_t ldw1, const void *W2, int64_t ldw2, int M,
+                      int N1, int N2, const float *b1, const float *b2, void *h2, int64_t ldh2, int *err,
+                      cudaStream_t st) {
+    using L = F12Smem<NP>;
+    static bool configured = false;
+    if (!configured) {
+        int rc = check_cuda(cudaFuncSetAttribute(gemm_fused12_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)L::kTotal),
+                            "fused GEMM smem attribute");
+        if (rc) return rc;
+        configured = true;
+    }
+    CUtensorMap tx, tw1, tw2, th2;
+    int rc = make_tmap_operand(&tx, X, M, 64, ldx, kBM, 2);
+    if (!rc) rc = make_tmap_operand(&tw1, W1, N1, 64, ldw1, kF12Chunk, 2);
+    if (!rc) rc = make_tmap_operand(&tw2, W2, N2, N1, ldw2, NP / 2, 2);
+    if (!rc) rc = make_tmap_out(&th2, h2, M, N2, ldh2, 2);
+    if (rc) return rc;
+    const int m_tiles = (M + kBM - 1) / kBM;
+    int grid = num_sms();
+    if (m_tiles < grid) grid = m_tiles;
+    const F12Args a{M, N1, N2, (N2 + NP - 1) / NP, b1, b2, gemm_wait_limit()};
+    void *pb = prof_begin(st);
+    gemm_fused12_kernel<NP><<<grid, kGemmThreads, L::kTotal, st>>>(tx, tw1, tw2, th2, a, err);
+    if (pb)
+        prof_end(pb, st, "gemm_fused12_kernel<" + std::to_string(NP) + "> " + std::to_string(N1) + "x" +
+                             std::to_string(N2),
+                 2.0 * M * ((double)N1 * 64 + (double)N2 * N1), 2.0 * ((double)M * 64 + (double)N2 * M));
+    return check_cuda(cudaGetLastError(), "fused GEMM launch");
+}
+
+}  // namespace
+
+bool fused12_supported(int K1, int N1, int N2) {
+    return K1 == 64 && N1 >= kF12Chunk && N1 % kF12Chunk == 0 && N2 >= 16 && N2 % 16 == 0;
+}
+
+int gemm_fused12(const void *X, int64_t ldx, int K1, const void *W1, int64_t ldw1, const void *W2, int64_t ldw2, int M,
+                 int N1, int N2, const float *b1, const float *b2, void *h2, int64_t ldh2, int *err, cudaStream_t st) {
+    if (M <= 0) return CHEM_OK;
+    if (!fused12_supported(K1, N1, N2))
+        return set_error(CHEM_EINVAL, "fused GEMM: needs K1 = 64, h1 a multiple of 64 and h2 a multiple of 16");
+    if (!aligned16(b1) || !aligned16(b2)) return set_error(CHEM_EINVAL, "fused GEMM: biases must be 16-byte aligned");
+    // the fewest passes of at most 400 columns (the widest pass whose W2 ring fits in shared memory),
+    // then the narrowest compiled pass width that covers them
+    const int passes = (N2 + 399) / 400;
+    const int need = (N2 + passes - 1) / passes;
+    if (need <= 128) return launch_fused12_np<128>(X, ldx, W1, ldw1, W2, ldw2, M, N1, N2, b1, b2, h2, ldh2, err, st);
+    if (need <= 256) return launch_fused12_np<256>(X, ldx, W1, ldw1, W2, ldw2, M, N1, N2, b1, b2, h2, ldh2, err, st);
+    return launch_fused12_np<400>(X, ldx, W1, ldw1, W2, ldw2, M, N1, N2, b1, b2, h2, ldh2, err, st);
+}
+
+}  // namespace chemgb

@@ -103,6 +103,7 @@ struct chem_mlp {
     int device;
     uint64_t seed;
     uint32_t wait_limit;                    // tries of each GEMM pipeline wait (chem_mlp_set_wait_limit)
+    int fuse12;                             // layers 1 and 2 of the BF16 forward in one launch (where supported)
 };
 
 namespace chemgb {
@@ -738,6 +739,12 @@ int ens_output(const chem_mlp *m, int64_t n, const __nv_bfloat16 *h, float *u, c
     return check_cuda(cudaGetLastError(), "ensemble output units");
 }
 
+// whether the BF16 forward runs layers 1 and 2 as one fused launch (multi-output network, the
+// first layer's K of 64 and widths the fused kernel takes)
+bool fused12_on(const chem_mlp *m) {
+    return m->fuse12 && !m->ens && fused12_supported(m->L[0].kx, m->L[0].out, m->L[1].out);
+}
+
 // prologue + the first nlayers layers on cells [0, n) of the given SoA pointers; with all four,
 // the normalised outputs are in m->out. prec CHEM_PREC_FP8 runs the hidden-to-hidden layers on
 // E4M3 operands: h1 and h2 are stored as E4M3 (scales act_scale) in the buffers of h[0] and h[1],
@@ -763,7 +770,18 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
         if (rc || nlayers < kLayers) return rc;
         return ens_output(m, n, m->h[2], m->out, st);
     }
-    for (int l = 0; l < 3 && l < nlayers; ++l) {
+    int l0 = 0;
+    if (prec == CHEM_PREC_BF16 && nlayers == kLayers && fused12_on(m)) {
+        // layers 1 and 2 in one launch: h1 stays on chip, h2 is written (bitwise the two-launch result)
+        const Layer &L0 = m->L[0], &L1 = m->L[1];
+        rc = gemm_fused12(x, ldx, L0.kx, L0.Wb, L0.kx, L1.Wb, L1.kx, (int)n, L0.out, L1.out, L0.b, L1.b, m->h[1],
+                          L1.out, m->err, st);
+        if (rc) return rc;
+        x = m->h[1];
+        ldx = L1.out;
+        l0 = 2;
+    }
+    for (int l = l0; l < 3 && l < nlayers; ++l) {
         const Layer &L = m->L[l];
         if (prec == CHEM_PREC_FP8) {
             const bool f8in = fp8_layer(l), f8out = fp8_layer(l + 1);
@@ -857,6 +875,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     m->max_batch = desc->max_batch > 0 ? (desc->max_batch + 7) / 8 * 8 : 4096;
     m->seed = seed;
     m->wait_limit = tc::kSpinLimit;
+    m->fuse12 = 1;
     m->widths[0] = m->n_in;
     for (int i = 0; i < 3; ++i) m->widths[1 + i] = desc->n_hidden[i];
     m->widths[4] = m->n_out;
@@ -1537,6 +1556,17 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
     return check_cuda(cudaGetLastError(), "train adam");
 }
 
+extern "C" int chem_mlp_set_fusion(chem_mlp *m, int on) {
+    if (!m || (on != 0 && on != 1)) return set_error(CHEM_EINVAL, "chem_mlp_set_fusion: null handle or on not 0/1");
+    m->fuse12 = on;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_get_fusion(const chem_mlp *m) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_fusion: null handle");
+    return fused12_on(m) ? 1 : 0;
+}
+
 extern "C" int chem_mlp_set_wait_limit(chem_mlp *m, uint32_t tries) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_set_wait_limit: null handle");
     m->wait_limit = tries == 0 ? tc::kSpinLimit : tries;
@@ -1712,6 +1742,7 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_autotune: " + why);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     cudaEvent_t e0, e1;
+    float best_ms[kLayers] = {0.0f, 0.0f, 0.0f, 0.0f};
     int rc = check_cuda(cudaEventCreate(&e0), "autotune event");
     if (rc) return rc;
     rc = check_cuda(cudaEventCreate(&e1), "autotune event");
@@ -1727,6 +1758,7 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
         const int width = (m->ens && l > 0) ? L.gout : L.out;    // output columns of one product
         float best = 3.4e38f;
         int best_bn = L.tile;
+        best_ms[l] = 0.0f;
         // the two-CTA variant is not a candidate: measured on GB300 it runs at half the single-CTA rate
         const std::vector<int> codes(std::begin(kTileWidths), std::end(kTileWidths));
         for (int bn : codes) {
@@ -1755,7 +1787,25 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
             if (!rc && ms_sum < best) { best = ms_sum; best_bn = bn; }
         }
         L.tile = best_bn;
+        best_ms[l] = best;
         if (tiles_out) tiles_out[l] = best_bn;
+    }
+    // layers 1 and 2 fused into one launch, against the best two-launch pair
+    if (!rc && !m->ens && fused12_supported(m->L[0].kx, m->L[0].out, m->L[1].out)) {
+        const Layer &L0 = m->L[0], &L1 = m->L[1];
+        float ms_sum = 0.0f;
+        for (int rep = 0; rep < 4 && !rc; ++rep) {
+            rc = check_cuda(cudaEventRecord(e0, st), "autotune record");
+            if (!rc)
+                rc = gemm_fused12(m->a0, 2 * m->n_in_pad, L0.kx, L0.Wb, L0.kx, L1.Wb, L1.kx, (int)rows, L0.out, L1.out,
+                                  L0.b, L1.b, m->h[1], L1.out, m->err, st);
+            if (!rc) rc = check_cuda(cudaEventRecord(e1, st), "autotune record");
+            if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "autotune sync");
+            float ms = 0.0f;
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;
+        }
+        if (!rc) m->fuse12 = ms_sum < best_ms[0] + best_ms[1] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

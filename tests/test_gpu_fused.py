@@ -1,0 +1,77 @@
+"""The fused first two layers (h1 made on chip and consumed as layer 2's operand,
+gemm_fused.cuh) against the two-launch path and the oracle.
+
+* Bitwise: every output of chem_mlp_forward with fusion on equals the output
+  with fusion off (the same BF16 roundings and k order per element), at the
+  paper's widths (two passes of 400 columns), a one-pass network, a ragged last
+  pass (h2 = 560: the second pass covers 160 columns) and a ragged row count
+  over several chunks.
+* chem_step_ann with fusion on matches the oracle as in test_gpu_mlp.py (the
+  default path of the learned step).
+Weights, statistics and states come from the seeded generator, never from the GPU.
+"""
+import numpy as np
+import pytest
+
+from oracle import ann as A
+from oracle import mlp as M
+from paper_2312_05800_gb300 import synth
+from tests.gpu_util import dev_mech, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(n, hidden, seed):
+    mech = synth.get_mech("c2")
+    T, p, Y = synth.states_profiles(mech, n, seed, synth.padded_ld(n))
+    widths = [mech.N + 2, *hidden, mech.N - 1]
+    layers = synth.mlp_layers(widths, 3000 + seed)
+    mu_x, sd_x = M.zscore_stats(M.features(T[:n], p[:n], Y[:, :n]))
+    rng = np.random.default_rng(seed + 7)
+    stats = (mu_x, sd_x, rng.uniform(-1e-5, 1e-5, mech.N - 1), 10.0 ** rng.uniform(-6, -3, mech.N - 1))
+    return mech, T, p, Y, widths, layers, stats
+
+
+def _net(widths, layers, stats, **kw):
+    from paper_2312_05800_gb300 import binding
+    net = binding.Mlp(dev_mech("c2"), hidden=widths[1:4], **kw)
+    net.set_params(synth.flatten_layers(layers))
+    net.set_norm(*stats)
+    return net
+
+
+def _u(net, T, p, Y, n):
+    import torch
+    from paper_2312_05800_gb300 import binding
+    u = torch.full((n, 32), float("nan"), dtype=torch.float32, device="cuda")
+    binding.chem_mlp_forward(net, n, T.shape[0], to_dev(T), to_dev(p), to_dev(Y), u, 32)
+    torch.cuda.synchronize()
+    assert net.error() == 0
+    return u.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,hidden,chunk", [(3001, (1600, 800, 400), 2048), (20000, (1600, 800, 400), 8192),
+                                            (1000, (640, 256, 64), 4096), (2600, (1600, 560, 400), 1024)])
+def test_fused_layers_are_bitwise_the_two_launches(n, hidden, chunk):
+    mech, T, p, Y, widths, layers, stats = _problem(n, hidden, 2071)
+    net = _net(widths, layers, stats, chunk=chunk)
+    assert net.fused
+    uf = _u(net, T, p, Y, n)
+    net.set_fusion(False)
+    assert not net.fused
+    u2 = _u(net, T, p, Y, n)
+    assert np.array_equal(uf, u2), np.argwhere(uf != u2)[:5]
+    # and against the oracle with the device's BF16 rounding points
+    uq = A.forward_u(mech, layers, stats, T[:n], p[:n], Y[:, :n], round_bf16=True)
+    rms = np.sqrt(np.mean(uq ** 2))
+    err = np.abs(uf[:, :widths[4]].astype(np.float64) - uq)
+    assert np.mean(err <= 1e-2 * (np.abs(uq) + rms)) >= 0.9999
+    assert np.all(err <= 3e-2 * (np.abs(uq) + rms))
+    net.free()
+
+
+def test_fusion_is_off_where_it_does_not_apply():
+    mech, T, p, Y, widths, layers, stats = _problem(256, (600, 200, 100), 2072)    # h1 not a multiple of 64
+    net = _net(widths, layers, stats)
+    assert not net.fused
+    net.free()
