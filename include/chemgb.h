@@ -214,6 +214,48 @@ int chem_pasr(const chem_mech *mech, int64_t ncells, int64_t ld, double y_min, c
               double *tau_c, double *kappa, chem_stream_t stream);
 
 /* ---------------------------------------------------------------------------
+ * Random training-data generation (Sec. 3.1, Eq. 1-4 and Table 1)
+ * ---------------------------------------------------------------------------
+ * The paper widens its flamelet dataset by random perturbations of every base
+ * composition and keeps those whose element ratios stay physical (Table 1).
+ * chem_hfrd_perturb computes, per state i < n (SoA, leading dimension ld), with
+ * the caller's uniform random numbers c in [-1, 1] (device, [3 + N][ld]: rows
+ * c_T, c_p, c_bath, then one row per species, the bath's row unused):
+ *   T'    = T + alpha c_T (T_max - T_min)                 (Eq. 1)
+ *   p'    = p + beta  c_p (p_max - p_min)                 (Eq. 2)
+ *   Y'_b  = Y_b + alpha c_bath (Yb_max - Yb_min)          (Eq. 3; b = the bath, N2)
+ *   Y'_j  = max(Y_j, 0)^(1 + gamma c_j), j != b           (Eq. 4)
+ * and scales the other species to sum to 1 - Y'_b. keep[i] (uint8, device) is
+ * 1 when the state is admissible (0 <= Y'_b < 1, T' > 0, p' > 0, some other
+ * species left) and H/C, O/N and phi = (2 n_C + n_H / 2) / n_O, from the
+ * element moles n_e = sum_k a_ek Y'_k / W_k, lie in the closed Table 1 ranges.
+ * T2, p2 [ld] and Y2 [N][ld] (device) receive the perturbed state (for a
+ * rejected inadmissible state, Y2 holds the unscaled Eq. 4 values and 0 for
+ * the bath). chon (host int32 [4][N]): the atoms of C, H, O and N in each
+ * species. Every operation is FP64, rounded as written (no fused multiply-add).
+ * Errors: CHEM_EINVAL for null or misaligned arrays or bad sizes.
+ *
+ * chem_hfrd_blend: the lean-mixing states of Sec. 3.1, linear in T and every
+ * Y between endpoint a (s = 0) and endpoint b (s = 1):
+ *   T = (1 - s) Ta + s Tb,  Y_k = (1 - s) Ya_k + s Yb_k
+ * for s [n] (device), endpoints Ya, Yb [N] (host), outputs T [ld], Y [N][ld].
+ */
+typedef struct {
+    double alpha, beta, gamma;            /* amplitudes of Eq. 1-4 (Sec. 3.1: 0.125, 10, 0.1) */
+    double T_min, T_max, p_min, p_max;    /* ranges over the base dataset */
+    double Yb_min, Yb_max;                /* bath mass-fraction range over the base dataset */
+    double hc_lo, hc_hi, on_lo, on_hi, phi_lo, phi_hi;   /* Table 1: 2.65-4.67, 0.254-0.32, 0.20-1.15 */
+} chem_hfrd_params;
+
+/* The paper's alpha, beta, gamma and Table 1; the dataset ranges set to 0. */
+void chem_hfrd_params_default(chem_hfrd_params *params);
+int chem_hfrd_perturb(const chem_mech *mech, const chem_hfrd_params *params, const int32_t *chon, int64_t n,
+                      int64_t ld, const double *T, const double *p, const double *Y, const double *c, double *T2,
+                      double *p2, double *Y2, uint8_t *keep, chem_stream_t stream);
+int chem_hfrd_blend(int N, int64_t n, int64_t ld, const double *s, double Ta, const double *Ya, double Tb,
+                    const double *Yb, double *T, double *Y, chem_stream_t stream);
+
+/* ---------------------------------------------------------------------------
  * chem_dense_bf16 -- one dense layer of the network on the tensor cores
  * ---------------------------------------------------------------------------
  * Sec. 3.2: each hidden layer applies GELU to an affine map of the layer below.

@@ -12,6 +12,8 @@ import ctypes
 import os
 from typing import Optional
 
+import numpy as np
+
 from . import build as _build
 
 CHEM_OK, CHEM_EINVAL, CHEM_ECUDA, CHEM_EUNSUPPORTED, CHEM_EIO = 0, -1, -2, -3, -4
@@ -35,6 +37,12 @@ class chem_ode_opts(ctypes.Structure):
 class chem_mlp_desc(ctypes.Structure):
     _fields_ = [("n_hidden", ctypes.c_int32 * 3), ("chunk", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("ensemble", ctypes.c_int32), ("dt", ctypes.c_double)]
+
+
+class chem_hfrd_params(ctypes.Structure):
+    _fields_ = [(nm, ctypes.c_double) for nm in ("alpha", "beta", "gamma", "T_min", "T_max", "p_min", "p_max",
+                                                 "Yb_min", "Yb_max", "hc_lo", "hc_hi", "on_lo", "on_hi", "phi_lo",
+                                                 "phi_hi")]
 
 
 CHEM_PREC_BF16, CHEM_PREC_FP8 = 0, 1
@@ -65,6 +73,11 @@ def lib() -> ctypes.CDLL:
     L.chem_step_stiff.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
     L.chem_step_stiff_noalloc.argtypes = [vp, i64, i64, d, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp, vp, vp]
     L.chem_pasr.argtypes = [vp, i64, i64, d, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.chem_hfrd_params_default.argtypes = [ctypes.POINTER(chem_hfrd_params)]
+    L.chem_hfrd_params_default.restype = None
+    L.chem_hfrd_perturb.argtypes = [vp, ctypes.POINTER(chem_hfrd_params), vp, i64, i64, vp, vp, vp, vp, vp, vp, vp,
+                                    vp, vp]
+    L.chem_hfrd_blend.argtypes = [i32, i64, i64, vp, d, vp, d, vp, vp, vp, vp]
     L.chem_dense_bf16.argtypes = [i64, i32, i32, vp, i64, vp, i64, vp, i32, vp, i64, i32, vp, vp]
     L.chem_mlp_create.argtypes = [vp, ctypes.POINTER(chem_mlp_desc), ctypes.c_uint64, ctypes.POINTER(vp)]
     L.chem_mlp_free.argtypes = [vp]
@@ -208,6 +221,30 @@ def chem_dense_bf16(M: int, N: int, K: int, x, ldx: int, W, ldw: int, b, act: in
                     err=None, stream=None):
     _check(lib().chem_dense_bf16(M, N, K, _ptr(x), ldx, _ptr(W), ldw, _ptr(b), act, _ptr(y), ldy, tile_n, _ptr(err),
                                  _stream(stream)))
+
+
+def hfrd_params(**kw) -> chem_hfrd_params:
+    """chem_hfrd_params with the paper's defaults, then the given fields."""
+    q = chem_hfrd_params()
+    lib().chem_hfrd_params_default(ctypes.byref(q))
+    for k, v in kw.items():
+        setattr(q, k, float(v))
+    return q
+
+
+def chem_hfrd_perturb(mech: Mech, params: chem_hfrd_params, chon, n: int, ld: int, T, p, Y, c, T2, p2, Y2, keep,
+                      stream=None):
+    a = np.ascontiguousarray(chon, dtype=np.int32)
+    _check(lib().chem_hfrd_perturb(mech.handle, ctypes.byref(params), a.ctypes.data_as(ctypes.c_void_p), n, ld,
+                                   _ptr(T), _ptr(p), _ptr(Y), _ptr(c), _ptr(T2), _ptr(p2), _ptr(Y2), _ptr(keep),
+                                   _stream(stream)))
+
+
+def chem_hfrd_blend(N: int, n: int, ld: int, s, Ta: float, Ya, Tb: float, Yb, T, Y, stream=None):
+    ya = np.ascontiguousarray(Ya, dtype=np.float64)
+    yb = np.ascontiguousarray(Yb, dtype=np.float64)
+    _check(lib().chem_hfrd_blend(N, n, ld, _ptr(s), float(Ta), ya.ctypes.data_as(ctypes.c_void_p), float(Tb),
+                                 yb.ctypes.data_as(ctypes.c_void_p), _ptr(T), _ptr(Y), _stream(stream)))
 
 
 def chem_pasr(mech: Mech, ncells: int, ld: int, y_min: float, T0, p, Y0, tau_taylor, tau_kolmogorov, T=None, Y=None,

@@ -537,6 +537,48 @@ def states_profiles(m: Mech, ncells: int, seed: int, ld: int | None = None,
     return To, po, Yo
 
 
+def fuel_air(m: Mech, phi: float):
+    """Mass fractions of the fuel / air mixture at equivalence ratio phi (1 mol O2 with 3.76 mol
+    of the bath species) and of its complete-combustion products (min(1, 1/phi) of the fuel burnt
+    to water and CO2): the unburnt and burnt ends of the profiles above, for one phi."""
+    r = m.roles
+    E = m.elements
+    fuel = r.get("fuel", r["h2"])
+    ox, bath, water, co2 = r["oxidizer"], r["bath"], r["water"], r.get("co2")
+    nC = m.elem[fuel, E.index("C")] if "C" in E else 0
+    nH = m.elem[fuel, E.index("H")]
+    o2_st = nC + nH / 4.0
+    Xu = np.zeros(m.N)
+    Xu[fuel] = phi / o2_st
+    Xu[ox] = 1.0
+    Xu[bath] = 3.76
+    burnt = min(1.0, 1.0 / phi) * Xu[fuel]
+    Xb = Xu.copy()
+    Xb[fuel] -= burnt
+    Xb[ox] = max(Xb[ox] - burnt * o2_st, 0.0)
+    Xb[water] += burnt * nH / 2.0
+    if co2 is not None:
+        Xb[co2] += burnt * nC
+    return Xu * m.W / np.dot(Xu, m.W), Xb * m.W / np.dot(Xb, m.W)
+
+
+def air(m: Mech):
+    """Mass fractions of ambient air: 1 mol O2 with 3.76 mol of the bath species."""
+    X = np.zeros(m.N)
+    X[m.roles["oxidizer"]] = 1.0
+    X[m.bath] = 3.76
+    return X * m.W / np.dot(X, m.W)
+
+
+def element_table(m: Mech, names=("C", "H", "O", "N")) -> np.ndarray:
+    """[len(names)][N] int32 atom counts of the named elements (0 for an element the mechanism lacks)."""
+    out = np.zeros((len(names), m.N), np.int32)
+    for e, nm in enumerate(names):
+        if nm in m.elements:
+            out[e] = m.elem[:, m.elements.index(nm)]
+    return out
+
+
 def perturb_off_manifold(T: np.ndarray, Y: np.ndarray, ncells: int, frac: float, seed: int,
                          dT: float = 300.0, sigma: float = 0.2):
     """Move a seeded fraction of cells off the sampled manifold (T +/- dT with a

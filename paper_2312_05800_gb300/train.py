@@ -34,18 +34,22 @@ class TrainingSet:
 
 
 def make_training_set(mech: binding.Mech, smech: synth.Mech, n: int, seed: int, opts=None,
-                      perturb_frac: float = 0.0) -> TrainingSet:
+                      perturb_frac: float = 0.0, hfrd: bool = False) -> TrainingSet:
     """Samples n states (stratified premixed profiles; optionally a perturbed
-    fraction), integrates them with the GPU stiff integrator over dt and keeps
+    fraction; or, with hfrd, the random states of Sec. 3.1 from hfrd_states, about
+    n of them), integrates them with the GPU stiff integrator over dt and keeps
     the pairs. Raises if any integration failed."""
     import torch
-    ld = synth.padded_ld(n)
-    T, p, Y = synth.states_profiles(smech, n, seed, ld)
-    if perturb_frac > 0.0:
-        T, Y, _ = synth.perturb_off_manifold(T, Y, n, perturb_frac, seed + 1)
-    Td = torch.from_numpy(T).cuda()
-    pd = torch.from_numpy(p).cuda()
-    Yd = torch.from_numpy(Y).cuda()
+    if hfrd:
+        n, ld, Td, pd, Yd = hfrd_states(mech, smech, n, seed)
+    else:
+        ld = synth.padded_ld(n)
+        T, p, Y = synth.states_profiles(smech, n, seed, ld)
+        if perturb_frac > 0.0:
+            T, Y, _ = synth.perturb_off_manifold(T, Y, n, perturb_frac, seed + 1)
+        Td = torch.from_numpy(T).cuda()
+        pd = torch.from_numpy(p).cuda()
+        Yd = torch.from_numpy(Y).cuda()
     T1 = Td.clone()
     Y1 = Yd.clone()
     st = torch.zeros(ld, dtype=torch.int32, device="cuda")
@@ -55,6 +59,91 @@ def make_training_set(mech: binding.Mech, smech: synth.Mech, n: int, seed: int, 
     if nbad:
         raise RuntimeError("%d training states failed to integrate" % nbad)
     return TrainingSet(n=n, ld=ld, T=Td, p=pd, Y=Yd, Y1=Y1, T1=T1, status=st)
+
+
+def lean_equilibrium(mech: binding.Mech, smech: synth.Mech, phi: float = 0.45, T0: float = 300.0,
+                     p: float = synth.P_ATM, t_end: float = 1.0):
+    """The lean-mixing endpoint of Sec. 3.1: the adiabatic, isobaric equilibrium of the fuel / air
+    mixture at phi. Its complete-combustion products start at the temperature that keeps the
+    unburnt mixture's enthalpy (Newton steps T -= (h - h0) / cp with props_eval in FP64), then the
+    stiff integrator takes them to rest over t_end. Returns (T_eq, Y_eq) as host values."""
+    import torch
+    Yu, Yb = synth.fuel_air(smech, phi)
+    N = smech.N
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+    Td = dev(np.full(4, T0))
+    pd = dev(np.full(4, p))
+    Yd = dev(np.repeat(Yu[:, None], 4, axis=1))
+    cp = torch.zeros(4, dtype=torch.float64, device="cuda")
+    h = torch.zeros_like(cp)
+    binding.props_eval(mech, 1, 4, binding.CHEM_F64, Td, pd, Yd, cp, h)
+    h0 = float(h[0].item())
+    Yd.copy_(dev(np.repeat(Yb[:, None], 4, axis=1)))
+    T = 2000.0
+    for _ in range(100):
+        Td.fill_(T)
+        binding.props_eval(mech, 1, 4, binding.CHEM_F64, Td, pd, Yd, cp, h)
+        d = (float(h[0].item()) - h0) / float(cp[0].item())
+        T -= d
+        if abs(d) < 1e-10:
+            break
+    Td.fill_(T)
+    st = torch.zeros(4, dtype=torch.int32, device="cuda")
+    o = binding.make_opts(rtol=1e-10, atol_Y=1e-16, atol_T=1e-10, h0=1e-9, max_steps=200000)
+    binding.chem_step_stiff(mech, 1, 4, t_end, o, Td, pd, Yd, st)
+    if int(st[0].item()) != 0:
+        raise RuntimeError("equilibrium integration failed with status %d" % int(st[0].item()))
+    return float(Td[0].item()), Yd[:N, 0].cpu().numpy()
+
+
+def hfrd_states(mech: binding.Mech, smech: synth.Mech, n_base: int, seed: int, lean_frac: float = 0.1,
+                t_min: float = 500.0):
+    """Random training states of Sec. 3.1 on the GPU: base states (the profile sampler standing in
+    for the flamelets) with T >= t_min perturbed by Eq. 1-4 with seeded uniform draws and filtered
+    by Table 1 (chem_hfrd_perturb), plus lean_frac as many lean-mixing states blended between the
+    phi = 0.45 adiabatic equilibrium and air (chem_hfrd_blend). Returns (n, ld, T, p, Y) on the
+    device (SoA, ld a multiple of 4)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    ldb = synth.padded_ld(n_base)
+    Tb, pb, Yb = synth.states_profiles(smech, n_base, seed, ldb)
+    base = np.flatnonzero(Tb[:n_base] >= t_min)
+    nb = base.size
+    ld = synth.padded_ld(nb)
+    T = np.zeros(ld); p = np.zeros(ld); Y = np.zeros((smech.N, ld))
+    T[:nb], p[:nb], Y[:, :nb] = Tb[base], pb[base], Yb[:, base]
+    b = smech.bath
+    prm = binding.hfrd_params(T_min=T[:nb].min(), T_max=T[:nb].max(), p_min=p[:nb].min(), p_max=p[:nb].max(),
+                              Yb_min=Y[b, :nb].min(), Yb_max=Y[b, :nb].max())
+    c = np.zeros((3 + smech.N, ld))
+    c[:, :nb] = rng.uniform(-1.0, 1.0, (3 + smech.N, nb))
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    T2 = torch.zeros(ld, dtype=torch.float64, device="cuda")
+    p2 = torch.zeros_like(T2)
+    Y2 = torch.zeros((smech.N, ld), dtype=torch.float64, device="cuda")
+    keep = torch.zeros(ld, dtype=torch.uint8, device="cuda")
+    binding.chem_hfrd_perturb(mech, prm, synth.element_table(smech), nb, ld, dev(T), dev(p), dev(Y), dev(c), T2, p2,
+                              Y2, keep)
+    kept = torch.nonzero(keep[:nb]).flatten()
+    nk = int(kept.numel())
+    nl = int(round(lean_frac * nk))
+    n = nk + nl
+    ldo = synth.padded_ld(n)
+    To = torch.zeros(ldo, dtype=torch.float64, device="cuda")
+    po = torch.full((ldo,), synth.P_ATM, dtype=torch.float64, device="cuda")
+    Yo = torch.zeros((smech.N, ldo), dtype=torch.float64, device="cuda")
+    To[:nk] = T2[kept]
+    po[:nk] = p2[kept]
+    Yo[:, :nk] = Y2[:, kept]
+    if nl:
+        Te, Ye = lean_equilibrium(mech, smech)
+        s = dev(np.concatenate([rng.uniform(0.0, 1.0, nl), np.zeros(synth.padded_ld(nl) - nl)]))
+        Tl = torch.zeros(synth.padded_ld(nl), dtype=torch.float64, device="cuda")
+        Yl = torch.zeros((smech.N, synth.padded_ld(nl)), dtype=torch.float64, device="cuda")
+        binding.chem_hfrd_blend(smech.N, nl, Tl.shape[0], s, Te, Ye, 300.0, synth.air(smech), Tl, Yl)
+        To[nk:n] = Tl[:nl]
+        Yo[:, nk:n] = Yl[:, :nl]
+    return n, ldo, To, po, Yo
 
 
 def fit_norm(net: binding.Mlp, data: TrainingSet):
