@@ -50,12 +50,13 @@ TIGHT_OPTS = dict(rtol=1e-6, atol_Y=1e-13, atol_T=1e-6, h0=1e-9, max_steps=20000
 STIFF_OPTS = dict(rtol=1e-2, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000)
 PARITY_OPTS = dict(rtol=1e-9, atol_Y=1e-15, atol_T=1e-9, h0=1e-9, max_steps=10000)
 MECH = "c2"
+ORACLE_ACC_CELLS = 4096          # held-out cells whose learned-step error is measured against the oracle
+E2E_PARTS = 4                   # parts of the end-to-end step whose host copies overlap the others' compute
 HIDDEN = {"c2": (1600, 800, 400), "c5": (2048, 1024, 512)}
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of the four GEMM launches of one 262,144-cell chunk
-# in the timed step (one capture of this configuration); unmeasured for other mechanisms. The capture
-# predates the epilogue's current GELU arithmetic, so the JSON line reports it as history and its
-# traffic as null until the kernel is captured again.
-GEMM_CHUNK_TRAFFIC_BEFORE_GELU_CHANGE = {"c2": 1510.9e6 + 1362.1e6}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of the network's tensor-core launches of one
+# 262,144-cell chunk of the timed step, from one capture of the current kernels; a mechanism without
+# a capture reports null.
+GEMM_CHUNK_TRAFFIC = {}
 CELLS = {("ann", "c2"): NCELLS_ANN, ("stiff", "c2"): NCELLS, ("ann", "c5"): 16777216, ("stiff", "c5"): 1048576}
 SEED = 2002
 METRIC = "chem+props cells/s at stated dY/T error: ANN (BF16/FP8) vs stiff integrator, 1 GB300"
@@ -397,6 +398,35 @@ def measured_peak(key: str, fallback: float):
         return fallback, "fallback"
 
 
+def gemm_traffic(chunk: int, ncells: int):
+    """DRAM bytes of the network's tensor-core launches per step, from GEMM_CHUNK_TRAFFIC (one ncu
+    capture of a 262,144-cell chunk of the current kernels), scaled by the cells; None when the
+    current kernels have not been captured for this mechanism."""
+    t = GEMM_CHUNK_TRAFFIC.get(MECH)
+    return None if t is None else t * ncells / 262144
+
+
+def dominant_gemm(dom, ncells: int, chunk: int, widths, peak: float, steps: int):
+    """The longest-running tensor-core kernel of the step: its share of the GEMM time and its own
+    roofline fraction on its algorithmic flops per launch (the fused first two layers: 2 (K0 h1 +
+    h1 h2) per cell; a single layer: 2 fan_in fan_out per cell; chunk cells per launch)."""
+    if dom is None:
+        return None
+    name, (launches, ms, _, _) = dom
+    if name.startswith("gemm_fused12"):
+        per_cell = 2.0 * (widths[0] * widths[1] + widths[1] * widths[2])
+    else:
+        shape = name.split()[-1]                      # "N x K" of the launch
+        n_out, k_in = (int(x) for x in shape.split("x"))
+        fan_in = widths[0] if n_out == widths[1] else k_in
+        per_cell = 2.0 * fan_in * n_out
+    cells_per_launch = ncells * steps / launches
+    avg_ms = ms / launches
+    achieved = cells_per_launch * per_cell / (avg_ms / 1e3) / 1e12
+    return {"kernel": name, "launches": launches, "avg_ms": avg_ms, "cells_per_launch": cells_per_launch,
+            "mflop_per_cell": per_cell / 1e6, "achieved": achieved, "frac": achieved / peak}
+
+
 def accuracy(mech, T0, Y0, Ta, Ya, Tr, Yr, n):
     """Per major species relative L2 of dY, and |T error| max / p99.9, against a reference."""
     import numpy as np
@@ -493,6 +523,13 @@ def bench_ann(args, rank, world, local):
     acc_stiff = accuracy(smech, T, Y, Ts, Ys, Tr, Yr, ne)
     acc_fp8 = accuracy(smech, T, Y, T8, Y8, Tr, Yr, ne) if fp8 else None
     acc_ens = accuracy(smech, T, Y, Te, Ye, Tr, Yr, ne) if ens is not None else None
+    # the learned steps' results on the first cells, for the oracle-referenced accuracy of the CPU leg
+    no = min(ORACLE_ACC_CELLS, ne)
+    first = {"ann": (Ta[:no].copy(), Ya[:, :no].copy())}
+    if fp8:
+        first["fp8"] = (T8[:no].copy(), Y8[:, :no].copy())
+    if ens is not None:
+        first["ensemble"] = (Te[:no].copy(), Ye[:, :no].copy())
     del Ta, Ya, Tr, Yr, Ts, Ys, T8, Y8, Te, Ye
 
     def step(st=stream, prec=binding.CHEM_PREC_BF16):
@@ -570,7 +607,7 @@ def bench_ann(args, rank, world, local):
         prof8 = binding.chem_prof_read()
         binding.chem_prof_enable(False)
         f8_ms = g0.elapsed_time(g1) / args.steps
-        g8 = {k: v for k, v in prof8.items() if k.startswith("gemm_tn")}
+        g8 = {k: v for k, v in prof8.items() if k.startswith("gemm_")}
         e8 = {k: v for k, v in g8.items() if "e4m3" in k}
         e8_ms, e8_fl = sum(v[1] for v in e8.values()), sum(v[2] for v in e8.values())
         peak8 = measured_peak("bf16_tflops", 1900.0)[0] * 2.0
@@ -633,7 +670,7 @@ def bench_ann(args, rank, world, local):
         profe = binding.chem_prof_read()
         binding.chem_prof_enable(False)
         e_ms = g0.elapsed_time(g1) / ens_steps
-        ge = {k: v for k, v in profe.items() if k.startswith("gemm_tn")}
+        ge = {k: v for k, v in profe.items() if k.startswith("gemm_")}
         ge_ms, ge_fl = sum(v[1] for v in ge.values()), sum(v[2] for v in ge.values())
         bf_peak = measured_peak("bf16_tflops", 1900.0)[0]
         ens_line = {"value": world * ncells / (e_ms / 1e3), "unit": "cells/s", "ms_per_step": e_ms,
@@ -656,11 +693,17 @@ def bench_ann(args, rank, world, local):
         ens.free()
     total_s = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, world)
     value = job_rate(ncells * args.steps, world, total_s)
-    gemm = {k: v for k, v in prof.items() if k.startswith("gemm_tn")}
+    # every tensor-core launch of the network (the fused first two layers and the two-launch
+    # layers); the work is the method's: 2 sum fan_in fan_out per cell with the first layer's true
+    # K of N + 2 inputs (the device's hi/lo input split doubles K but is not the method's work)
+    gemm = {k: v for k, v in prof.items() if k.startswith("gemm_")}
     g_ms = sum(v[1] for v in gemm.values())
-    g_fl = sum(v[2] for v in gemm.values())
+    widths = [N + 2, *hidden, N - 1]
+    mflop_cell = 2.0 * sum(a * b for a, b in zip(widths[:-1], widths[1:])) / 1e6
+    g_fl = ncells * args.steps * mflop_cell * 1e6
     peak, src = measured_peak("bf16_tflops", 1900.0)
     achieved = g_fl / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
+    dom = max(gemm.items(), key=lambda kv: kv[1][1]) if gemm else None
     # ---- the plain method on a sample of the same cells (stiff at the throughput setting + props)
     ns = min(args.stiff_sample, ncells)
     torch.cuda.synchronize()
@@ -705,32 +748,79 @@ def bench_ann(args, rank, world, local):
                            "Y x exp(0.2 xi)); guard + stiff fallback (rtol %g) in the step" % (ncells, STIFF_OPTS["rtol"])}
     del T4d, Y4d, Tr4, Yr4
 
-    # ---- end to end through the C ABI with pinned host buffers
-    Th, ph, Yh = torch.from_numpy(T).pin_memory(), torch.from_numpy(p).pin_memory(), torch.from_numpy(Y).pin_memory()
-    Tout, Yout = torch.empty_like(Th).pin_memory(), torch.empty_like(Yh).pin_memory()
-    sout = torch.empty(ld, dtype=torch.int32).pin_memory()
-    pout = [torch.empty(ld, dtype=torch.float32).pin_memory() for _ in range(4)]
-    Dout = torch.empty(N, ld, dtype=torch.float32).pin_memory()
-    h2d = (Th.numel() + ph.numel() + Yh.numel()) * 8
-    d2h = (Tout.numel() + Yout.numel()) * 8 + sout.numel() * 4 + 4 * ld * 4 + Dout.numel() * 4
+    # ---- end to end through the C ABI with pinned host buffers. The cells go in E2E_PARTS parts (each
+    # its own SoA arrays on host and device); the host-to-device copies of part i + 1 and the
+    # device-to-host copies of part i - 1 run on two copy streams while part i steps, so the copies
+    # hide behind the computation.
     e2e_steps = max(1, min(args.steps, 3))
+    parts = []
+    sub = (ncells // E2E_PARTS + 3) // 4 * 4
+    for c0 in range(0, ncells, sub):
+        n_i = min(sub, ncells - c0)
+        ld_i = synth.padded_ld(n_i)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        hT, hp, hY = pin(T[c0:c0 + n_i]), pin(p[c0:c0 + n_i]), pin(Y[:, c0:c0 + n_i])
+        if ld_i != n_i:
+            hT = pin(np.pad(T[c0:c0 + n_i], (0, ld_i - n_i), constant_values=300.0))
+            hp = pin(np.pad(p[c0:c0 + n_i], (0, ld_i - n_i), constant_values=synth.P_ATM))
+            hY = pin(np.pad(Y[:, c0:c0 + n_i], ((0, 0), (0, ld_i - n_i))))
+        d = dict(n=n_i, ld=ld_i, hT=hT, hp=hp, hY=hY,
+                 T=torch.empty(ld_i, dtype=torch.float64, device=dev), p=torch.empty(ld_i, dtype=torch.float64,
+                                                                                      device=dev),
+                 Y=torch.empty(N, ld_i, dtype=torch.float64, device=dev),
+                 st=torch.empty(ld_i, dtype=torch.int32, device=dev),
+                 props=[torch.empty(ld_i, dtype=torch.float32, device=dev) for _ in range(4)],
+                 Dk=torch.empty(N, ld_i, dtype=torch.float32, device=dev),
+                 oT=torch.empty(ld_i, dtype=torch.float64).pin_memory(),
+                 oY=torch.empty(N, ld_i, dtype=torch.float64).pin_memory(),
+                 ost=torch.empty(ld_i, dtype=torch.int32).pin_memory(),
+                 oprops=[torch.empty(ld_i, dtype=torch.float32).pin_memory() for _ in range(4)],
+                 oDk=torch.empty(N, ld_i, dtype=torch.float32).pin_memory(),
+                 ev_in=torch.cuda.Event(), ev_done=torch.cuda.Event(), ev_out=torch.cuda.Event())
+        parts.append(d)
+    h2d = sum((q["hT"].numel() + q["hp"].numel() + q["hY"].numel()) * 8 for q in parts)
+    d2h = sum((q["oT"].numel() + q["oY"].numel()) * 8 + q["ost"].numel() * 4 + 4 * q["ld"] * 4 + q["oDk"].numel() * 4
+              for q in parts)
+    s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def e2e_step():
+        for q in parts:
+            s_in.wait_event(q["ev_out"])           # the previous step's results of this part are on the host
+            with torch.cuda.stream(s_in):
+                q["T"].copy_(q["hT"], non_blocking=True)
+                q["p"].copy_(q["hp"], non_blocking=True)
+                q["Y"].copy_(q["hY"], non_blocking=True)
+                q["ev_in"].record(s_in)
+        for q in parts:
+            stream.wait_event(q["ev_in"])
+            binding.chem_step_ann_props(dm, net, q["n"], q["ld"], DT, binding.CHEM_PREC_BF16, fb_opts, q["T"], q["p"],
+                                        q["Y"], q["st"], *q["props"], q["Dk"], stream)
+            q["ev_done"].record(stream)
+            s_out.wait_event(q["ev_done"])
+            with torch.cuda.stream(s_out):
+                q["oT"].copy_(q["T"], non_blocking=True)
+                q["oY"].copy_(q["Y"], non_blocking=True)
+                q["ost"].copy_(q["st"], non_blocking=True)
+                for o_, d_ in zip(q["oprops"], q["props"]):
+                    o_.copy_(d_, non_blocking=True)
+                q["oDk"].copy_(q["Dk"], non_blocking=True)
+                q["ev_out"].record(s_out)
+
+    for q in parts:
+        q["ev_out"].record(stream)
+    e2e_step()                                   # warm: the parts' first calls
     torch.cuda.synchronize()
     e0.record(stream)
+    s_in.wait_event(e0)
     for _ in range(e2e_steps):
-        Tw.copy_(Th, non_blocking=True)
-        p0.copy_(ph, non_blocking=True)
-        Yw.copy_(Yh, non_blocking=True)
-        binding.chem_step_ann_props(dm, net, ncells, ld, DT, binding.CHEM_PREC_BF16, fb_opts, Tw, p0, Yw, status, cp,
-                                    hh, mu, lam, Dk, stream)
-        Tout.copy_(Tw, non_blocking=True)
-        Yout.copy_(Yw, non_blocking=True)
-        sout.copy_(status, non_blocking=True)
-        for o, d in zip(pout, (cp, hh, mu, lam)):
-            o.copy_(d, non_blocking=True)
-        Dout.copy_(Dk, non_blocking=True)
+        e2e_step()
+    for q in parts:
+        stream.wait_event(q["ev_out"])
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_value = world * ncells * e2e_steps / (e0.elapsed_time(e1) / 1e3)
+    assert all(int((q["ost"][:q["n"]] >= 2).sum()) == 0 for q in parts)
+    del parts
     chunks = (ncells + args.chunk - 1) // args.chunk
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -752,15 +842,15 @@ def bench_ann(args, rank, world, local):
                          "train_s": t_train},
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": (achieved / peak) if achieved else None,
-                         "traffic": None,
-                         "traffic_before_gelu_change": (
-                             GEMM_CHUNK_TRAFFIC_BEFORE_GELU_CHANGE[MECH] * args.chunk / 262144
-                             if MECH in GEMM_CHUNK_TRAFFIC_BEFORE_GELU_CHANGE else None),
-                         "traffic_unit": "DRAM bytes (read + write) of the four GEMM launches of one chunk of "
-                                         "%d cells: one ncu capture of a 262,144-cell chunk, scaled by the "
-                                         "cells (every activation makes one DRAM round trip); null because "
-                                         "the epilogue changed after that capture" % args.chunk,
-                         "kernel": "gemm_tn_kernel (all four layers; logical 2MNK flops)", "peak_source": src,
+                         "traffic": gemm_traffic(args.chunk, ncells),
+                         "traffic_unit": "DRAM bytes (read + write) of the network's tensor-core launches per step: "
+                                         "ncu dram__bytes of one 262,144-cell chunk, scaled by the cells",
+                         "kernel": "every tensor-core launch of the network per step (layers 1-2 fused, layers 3 "
+                                   "and 4); CUDA events around each launch",
+                         "work": "%.4f MFLOP per cell: 2 sum fan_in x fan_out over %s (first layer K = N + 2, "
+                                 "not the device's hi/lo K)" % (mflop_cell, "-".join(str(w) for w in widths)),
+                         "peak_source": src,
+                         "dominant": dominant_gemm(dom, ncells, args.chunk, widths, peak, args.steps),
                          "per_shape": {k: {"launches": v[0], "ms": v[1],
                                            "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
                                        for k, v in gemm.items()}},
@@ -777,15 +867,40 @@ def bench_ann(args, rank, world, local):
             "ensemble": ens_line,
             "pasr": pasr_line,
             "props_thermo": props_thermo,
-            "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            # per step: prologue, four GEMMs and the epilogue per chunk, the fallback launch (with the
-            # guard on) and the properties kernel
-            "gpu_launches": args.steps * (chunks * 6 + (0 if args.untrained else 1) + 1),
+            "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "overlap": "%d parts of the cells; host-to-device and device-to-host copies on two streams "
+                               "beside the compute stream" % E2E_PARTS},
+            # the library's kernel launches of the timed steps, counted by its profiler (per chunk: the
+            # prologue, the tensor-core layers and the epilogue; per step: the fallback and props)
+            "gpu_launches": int(sum(v[0] for v in prof.values())),
             "clocks": clk.summary()}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_ann(smech, T, p, Y)
         line["cpu_baseline"]["one_core"] = cpu_baseline_one_core()
+        if not args.untrained and no > 0:
+            # the FP64 oracle's integration (parity setting) of the first held-out cells: the error of
+            # each learned step against it
+            To, Yo, so, t_or = oracle_reference(smech, T, p, Y, no)
+            ref = "oracle stiff integration (FP64, rtol %g) of the first %d held-out cells (%.1f s on %d host " \
+                  "cores)" % (PARITY_OPTS["rtol"], no, t_or, omp_threads())
+            line["accuracy"]["ann_vs_oracle"] = accuracy(smech, T, Y, *first["ann"], To, Yo, no)
+            line["accuracy"]["oracle_reference"] = ref
+            line["accuracy"]["oracle_failed_cells"] = int((so != 0).sum())
+            if line.get("fp8") and "fp8" in first:
+                line["fp8"]["accuracy_vs_oracle"] = accuracy(smech, T, Y, *first["fp8"], To, Yo, no)
+            if line.get("ensemble") and "ensemble" in first:
+                line["ensemble"]["accuracy_vs_oracle"] = accuracy(smech, T, Y, *first["ensemble"], To, Yo, no)
     return line
+
+
+def oracle_reference(smech, T, p, Y, n):
+    """The oracle's FP64 stiff integration over dt at the parity setting of the first n cells (the
+    reference of the learned step's error). Returns (T, Y, status, seconds)."""
+    import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    To, Yo, so, _ = O.step_stiff(smech, T[:n].copy(), p[:n].copy(), Y[:, :n].copy(), DT, **PARITY_OPTS)
+    return To, Yo, so, time.perf_counter() - t0
 
 
 def cpu_baseline_ann(smech, T, p, Y, sample=4096):

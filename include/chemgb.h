@@ -146,8 +146,20 @@ typedef struct {
     double atol_T;    /* absolute tolerance on temperature, K (default 1e-6) */
     double h0;        /* first trial step, s (default 1e-9; clipped to dt) */
     int32_t max_steps;/* attempted-step limit per cell (default 10000) */
-    int32_t _pad;
+    int32_t mode;     /* CHEM_ODE_FP64 (default) or CHEM_ODE_MIXED */
 } chem_ode_opts;
+
+/* Arithmetic of the integrator. CHEM_ODE_FP64: everything in FP64 (the parity
+ * setting). CHEM_ODE_MIXED, for loose tolerances (the learned step's fallback
+ * and the plain method's throughput setting, rtol 1e-2): the exponentials of
+ * the rate constants and the Troe blending are evaluated in FP32 (relative
+ * error about 1e-6 on the rates, far below rtol), and each stage solve uses an
+ * FP32 LU of I/(h gamma) - J followed by one step of iterative refinement with
+ * the FP64 matrix (the FP64 residual r = b - G x and x += G_f32^-1 r), which
+ * brings the solve to FP64-grade accuracy for FP32 work. The state update, the
+ * error norm and the step-size control stay FP64. The mode needs 12 R >= (N+1)^2
+ * (the FP32 factors share the reaction workspace); otherwise FP64 is used. */
+enum { CHEM_ODE_FP64 = 0, CHEM_ODE_MIXED = 1 };
 
 /* Fills *o with the defaults listed above. */
 void chem_ode_opts_default(chem_ode_opts *o);
@@ -494,6 +506,28 @@ int chem_step_ann_props(const chem_mech *mech, const chem_mlp *mlp, int64_t ncel
  */
 int mlp_train_step(chem_mlp *mlp, int64_t batch, const int32_t *idx, int64_t ld, const double *T, const double *p,
                    const double *Y, const double *Y1, float lr, float *loss_dev, chem_stream_t stream);
+
+/* Physics terms of the training loss (Sec. 3.2 adds the principles of
+ * mass-fraction unity, energy conservation and heat release to Eq. 5, with no
+ * formula or weight; the forms below are this library's reading). For sample
+ * i, with r_j = u_j - u*_j on normalised outputs, sd_j the output scales and
+ * c_ij = h_k(T_i) - h_bath(T_i) (J/kg; species k of output j; the bath closes
+ * sum dY = 0, so its change is folded in):
+ *   r_m,i = sum_j sd_j r_j            error of the implied bath change (unity)
+ *   r_q,i = -sum_j c_ij sd_j r_j      error of the heat release at T_i,
+ *                                     q = -sum_k h_k(T) dY_k (energy and heat release)
+ *   L = Eq. 5 + (1/B) sum_i (lam_m |r_m,i| / s_m + lam_q |r_q,i| / s_q)
+ * and mlp_train_step descends this L (subgradient sign(0) = 0). Enthalpies are
+ * the mechanism's NASA-7 rows in FP32. lam_m = lam_q = 0 (the default) is
+ * Eq. 5 alone. Weights >= 0, scales > 0 (CHEM_EINVAL otherwise); non-zero
+ * weights on a per-species ensemble return CHEM_EUNSUPPORTED.
+ * chem_mlp_fit_physics_scales: s_m = mean_i |sum_j dY*_ij| and
+ * s_q = mean_i |sum_j c_ij dY*_ij| over n training pairs (dY* = Y1 - Y of the
+ * output species; device SoA), in FP64 with a fixed summation order; host
+ * outputs; synchronises the stream. */
+int chem_mlp_set_physics_loss(chem_mlp *mlp, double lam_m, double lam_q, double s_m, double s_q);
+int chem_mlp_fit_physics_scales(chem_mlp *mlp, int64_t n, int64_t ld, const double *T, const double *Y,
+                                const double *Y1, double *s_m, double *s_q, chem_stream_t stream);
 
 /* Opt-in kernel timing (no counterpart in the paper; a measurement aid).
  * chem_prof_enable(1) clears the counters and starts recording CUDA events on

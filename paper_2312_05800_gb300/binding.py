@@ -31,7 +31,10 @@ class ChemError(RuntimeError):
 
 class chem_ode_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol_Y", ctypes.c_double), ("atol_T", ctypes.c_double),
-                ("h0", ctypes.c_double), ("max_steps", ctypes.c_int32), ("_pad", ctypes.c_int32)]
+                ("h0", ctypes.c_double), ("max_steps", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+CHEM_ODE_FP64, CHEM_ODE_MIXED = 0, 1
 
 
 class chem_mlp_desc(ctypes.Structure):
@@ -100,6 +103,8 @@ def lib() -> ctypes.CDLL:
     L.chem_mlp_error.argtypes = [vp, vp]
     L.chem_mlp_set_wait_limit.argtypes = [vp, ctypes.c_uint32]
     L.chem_mlp_set_fusion.argtypes = [vp, i32]
+    L.chem_mlp_set_physics_loss.argtypes = [vp, d, d, d, d]
+    L.chem_mlp_fit_physics_scales.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp, vp]
     L.chem_mlp_get_fusion.argtypes = [vp]
     L.chem_mlp_fit_ood.argtypes = [vp, vp, i64, i64, vp, vp, vp, i32, i32, i32, vp]
     L.chem_mlp_fit_ood_multi.argtypes = [vp, vp, i64, i64, vp, vp, vp, vp, i32, i32, i32, vp]
@@ -324,6 +329,15 @@ class Mlp:
 
     def set_wait_limit(self, tries: int):
         _check(lib().chem_mlp_set_wait_limit(self.handle, int(tries)))
+
+    def set_physics_loss(self, lam_m: float, lam_q: float, s_m: float = 1.0, s_q: float = 1.0):
+        _check(lib().chem_mlp_set_physics_loss(self.handle, float(lam_m), float(lam_q), float(s_m), float(s_q)))
+
+    def fit_physics_scales(self, n: int, ld: int, T, Y, Y1, stream=None):
+        sm, sq = ctypes.c_double(), ctypes.c_double()
+        _check(lib().chem_mlp_fit_physics_scales(self.handle, n, ld, _ptr(T), _ptr(Y), _ptr(Y1), ctypes.byref(sm),
+                                                 ctypes.byref(sq), _stream(stream)))
+        return sm.value, sq.value
 
     def set_fusion(self, on: bool):
         _check(lib().chem_mlp_set_fusion(self.handle, 1 if on else 0))

@@ -360,7 +360,7 @@ extern "C" void chem_ode_opts_default(chem_ode_opts *o) {
     o->atol_T = 1e-6;
     o->h0 = 1e-9;
     o->max_steps = 10000;
-    o->_pad = 0;
+    o->mode = CHEM_ODE_FP64;
 }
 
 extern "C" const char *chem_last_error(void) { return chemgb::g_last_error.c_str(); }

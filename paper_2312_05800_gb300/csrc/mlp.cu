@@ -104,6 +104,11 @@ struct chem_mlp {
     uint64_t seed;
     uint32_t wait_limit;                    // tries of each GEMM pipeline wait (chem_mlp_set_wait_limit)
     int fuse12;                             // layers 1 and 2 of the BF16 forward in one launch (where supported)
+    // physics terms of the training loss (chem_mlp_set_physics_loss): weights and scales, and the
+    // mechanism's FP32 NASA-7 enthalpy rows [2][N][6] and 1/W [N] for the heat release
+    double lam_m, lam_q, s_m, s_q;
+    float *nasa_h, *invW;
+    float T_mid;
 };
 
 namespace chemgb {
@@ -381,29 +386,130 @@ __global__ void ood_flags_kernel(int64_t n, int64_t ld, const double *T, const d
     out[i] = ood_outside(ood, f[0], f[1], Y, ld, i) ? 1 : 0;
 }
 
-// L1 loss of Eq. 5 on normalised outputs; dL/du = sign(u - u*)/B written as BF16.
+// Physics terms of the training loss (Sec. 3.2 names mass-fraction unity, energy and heat
+// release; the forms are readings): with r_j = u_j - u*_j on normalised outputs, sd_j the output
+// scales and c_j = h_k(T) - h_bath(T) (J/kg, species k of output j, the bath closure folded in),
+//   r_m = sum_j sd_j r_j              the error of the implied bath change (sum dY = 0)
+//   r_q = -sum_j c_j sd_j r_j         the error of the heat release q = -sum_k h_k(T) dY_k
+// and the loss adds lam_m |r_m| / s_m + lam_q |r_q| / s_q per sample (then / B).
+struct PhysLoss {
+    float wm, wq;                 // lam_m / s_m and lam_q / s_q (0: Eq. 5 alone)
+    const float *nasa_h;          // [2][N][6] H/RT rows
+    const float *invW;            // [N]
+    float T_mid;
+    int N, bath;
+};
+
+// H_k(T) / R (K) from the FP32 NASA-7 row of H/RT coefficients (a1, a2/2, a3/3, a4/4, a5/5, a6)
+__device__ __forceinline__ float h_over_R(const float *b, float T) {
+    float hh = fmaf(fmaf(fmaf(fmaf(__ldg(b + 4), T, __ldg(b + 3)), T, __ldg(b + 2)), T, __ldg(b + 1)), T, __ldg(b));
+    return hh * T + __ldg(b + 5);
+}
+
+// L1 loss of Eq. 5 on normalised outputs, dL/du = sign(u - u*)/B, plus the physics terms above
+// when their weights are non-zero; dL/du written as BF16, the per-sample loss to part.
 __global__ void l1_loss_kernel(int64_t B, const float *__restrict__ u, int ldu, const int32_t *__restrict__ idx,
                                int64_t ld, const double *__restrict__ Y0, const double *__restrict__ Y1, int n_out,
-                               const int *__restrict__ out_sp,
-                               const float *__restrict__ mu_u, const float *__restrict__ sd_u,
-                               __nv_bfloat16 *__restrict__ dout, int lddo, float *__restrict__ part) {
+                               const int *__restrict__ out_sp, const float *__restrict__ mu_u,
+                               const float *__restrict__ sd_u, __nv_bfloat16 *__restrict__ dout, int lddo,
+                               float *__restrict__ part, const double *__restrict__ Tc, PhysLoss ph) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= B) return;
     const int64_t c = idx ? (int64_t)idx[i] : i;
     const float invB = 1.0f / (float)B;
-    float acc = 0.0f;
+    const bool phys = ph.wm != 0.0f || ph.wq != 0.0f;
+    float acc = 0.0f, rm = 0.0f, rq = 0.0f, T = 0.0f, hb = 0.0f;
+    const float *rows = nullptr;
+    if (phys) {
+        T = (float)Tc[c];
+        rows = ph.nasa_h + (size_t)((T >= ph.T_mid) ? 1 : 0) * ph.N * 6;
+        hb = h_over_R(rows + ph.bath * 6, T) * __ldg(ph.invW + ph.bath);
+    }
+    for (int j = 0; j < n_out; ++j) {
+        const int64_t q = (int64_t)out_sp[j] * ld + c;
+        const float target = ((float)(Y1[q] - Y0[q]) - __ldg(mu_u + j)) / __ldg(sd_u + j);
+        const float d = u[i * ldu + j] - target;
+        acc += fabsf(d);
+        if (phys) {
+            const int k = out_sp[j];
+            const float cj = h_over_R(rows + k * 6, T) * __ldg(ph.invW + k) - hb;   // (h_k - h_bath) / R
+            rm = fmaf(__ldg(sd_u + j), d, rm);
+            rq = fmaf(-cj * __ldg(sd_u + j), d, rq);
+        }
+    }
+    // r_q in J/kg: the enthalpy differences above are in units of R (K mol/kg)
+    constexpr float kRf = 8.314462618f;
+    rq *= kRf;
+    const float sm = (rm > 0.0f) ? 1.0f : ((rm < 0.0f) ? -1.0f : 0.0f);
+    const float sq = (rq > 0.0f) ? 1.0f : ((rq < 0.0f) ? -1.0f : 0.0f);
+    if (phys) acc += ph.wm * fabsf(rm) + ph.wq * fabsf(rq);
     for (int j = 0; j < lddo; ++j) {
         float g = 0.0f;
         if (j < n_out) {
             const int64_t q = (int64_t)out_sp[j] * ld + c;
             const float target = ((float)(Y1[q] - Y0[q]) - __ldg(mu_u + j)) / __ldg(sd_u + j);
             const float d = u[i * ldu + j] - target;
-            acc += fabsf(d);
             g = (d > 0.0f) ? invB : ((d < 0.0f) ? -invB : 0.0f);
+            if (phys) {
+                const int k = out_sp[j];
+                const float cj = (h_over_R(rows + k * 6, T) * __ldg(ph.invW + k) - hb) * kRf;
+                g += invB * __ldg(sd_u + j) * (ph.wm * sm - ph.wq * sq * cj);
+            }
         }
         dout[i * lddo + j] = __float2bfloat16_rn(g);
     }
     part[i] = acc;
+}
+
+// Scales of the physics terms over n training pairs, FP64: per-block sums of |sum_j dY*_j| and
+// |sum_j (h_k - h_bath)(T) dY*_j| (dY* = Y1 - Y of the output species), fixed order within a
+// block (grid-stride, then a tree), written to part[2 blockIdx.x + {0, 1}].
+__global__ void phys_scales_kernel(int64_t n, int64_t ld, const double *__restrict__ T, const double *__restrict__ Y,
+                                   const double *__restrict__ Y1, int n_out, const int *__restrict__ out_sp,
+                                   PhysLoss ph, double *__restrict__ part) {
+    __shared__ double sm[256], sq[256];
+    double am = 0.0, aq = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float t = (float)T[i];
+        const float *rows = ph.nasa_h + (size_t)((t >= ph.T_mid) ? 1 : 0) * ph.N * 6;
+        const double hb = (double)(h_over_R(rows + ph.bath * 6, t) * __ldg(ph.invW + ph.bath));
+        double m = 0.0, q = 0.0;
+        for (int j = 0; j < n_out; ++j) {
+            const int k = out_sp[j];
+            const double d = Y1[(int64_t)k * ld + i] - Y[(int64_t)k * ld + i];
+            m += d;
+            q += ((double)(h_over_R(rows + k * 6, t) * __ldg(ph.invW + k)) - hb) * d;
+        }
+        am += fabs(m);
+        aq += fabs(q) * 8.314462618;
+    }
+    sm[threadIdx.x] = am;
+    sq[threadIdx.x] = aq;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sm[threadIdx.x] += sm[threadIdx.x + w];
+            sq[threadIdx.x] += sq[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sm[0];
+        part[2 * blockIdx.x + 1] = sq[0];
+    }
+}
+
+// the block partials of phys_scales_kernel summed in block order, divided by n
+__global__ void phys_scales_reduce_kernel(int nblocks, int64_t n, const double *__restrict__ part,
+                                          double *__restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double m = 0.0, q = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        m += part[2 * b];
+        q += part[2 * b + 1];
+    }
+    out[0] = m / (double)n;
+    out[1] = q / (double)n;
 }
 
 // Deterministic sum of the per-sample partials (one block, fixed order), then / B.
@@ -739,6 +845,19 @@ int ens_output(const chem_mlp *m, int64_t n, const __nv_bfloat16 *h, float *u, c
     return check_cuda(cudaGetLastError(), "ensemble output units");
 }
 
+// the training loss's physics terms as the loss kernel takes them (zero weights: Eq. 5 alone)
+PhysLoss phys_loss(const chem_mlp *m) {
+    PhysLoss p{};
+    p.wm = (float)(m->lam_m / m->s_m);
+    p.wq = (float)(m->lam_q / m->s_q);
+    p.nasa_h = m->nasa_h;
+    p.invW = m->invW;
+    p.T_mid = m->T_mid;
+    p.N = m->N;
+    p.bath = m->bath;
+    return p;
+}
+
 // whether the BF16 forward runs layers 1 and 2 as one fused launch (multi-output network, the
 // first layer's K of 64 and widths the fused kernel takes)
 bool fused12_on(const chem_mlp *m) {
@@ -949,6 +1068,8 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->fb_count, 64});
     parts.push_back({(void **)&m->fb_status, (size_t)C * 4});
     parts.push_back({(void **)&m->ood_part, (size_t)kOodBlocks * 6 * 4});
+    parts.push_back({(void **)&m->nasa_h, (size_t)2 * m->N * 6 * 4});
+    parts.push_back({(void **)&m->invW, (size_t)m->N * 4});
     size_t total = 0;
     for (auto &pp : parts) total = align256(total) + pp.second;
     total = align256(total);
@@ -968,6 +1089,15 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     cudaGetDevice(&m->device);
     rc = check_cuda(cudaMemcpy(m->out_sp_dev, m->out_species, sizeof(int) * m->n_out, cudaMemcpyHostToDevice),
                     "chem_mlp_create: species map");
+    if (!rc)
+        rc = check_cuda(cudaMemcpy(m->nasa_h, mech->dev.f32.nasa_h, sizeof(float) * 2 * m->N * 6,
+                                   cudaMemcpyDeviceToDevice), "chem_mlp_create: enthalpy rows");
+    if (!rc)
+        rc = check_cuda(cudaMemcpy(m->invW, mech->dev.f32.invW, sizeof(float) * m->N, cudaMemcpyDeviceToDevice),
+                        "chem_mlp_create: molar masses");
+    m->T_mid = (float)mech->T_mid;
+    m->lam_m = m->lam_q = 0.0;
+    m->s_m = m->s_q = 1.0;
     // seeded U(-1/sqrt(fan_in), 1/sqrt(fan_in)) initialisation (splitmix64 stream)
     std::vector<float> host(param_count(m));
     uint64_t s = seed;
@@ -1422,7 +1552,8 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
     if (!rc) rc = ens_output(m, B, m->th[2], m->tout, st);
     if (rc) return rc;
     l1_loss_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, m->tout, m->n_out_pad, idx, ld, Y, Y1, m->n_out, m->out_sp_dev,
-                                                     m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part);
+                                                     m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part, nullptr,
+                                                     PhysLoss{});
     if (loss_dev) loss_reduce_kernel<<<1, 256, 0, st>>>(B, m->loss_part, loss_dev);
     if ((rc = check_cuda(cudaGetLastError(), "ensemble loss"))) return rc;
     // output units
@@ -1511,7 +1642,8 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
         }
         // loss and dL/du
         l1_loss_kernel<<<(B + 127) / 128, 128, 0, st>>>(B, m->tout, m->n_out_pad, idx, ld, Y, Y1, m->n_out, m->out_sp_dev,
-                                                         m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part);
+                                                         m->mu_u, m->sd_u, m->tdout, m->n_out_pad, m->loss_part, T,
+                                                         phys_loss(m));
         if (loss_dev) loss_reduce_kernel<<<1, 256, 0, st>>>(B, m->loss_part, loss_dev);
         if ((rc = check_cuda(cudaGetLastError(), "train loss"))) return rc;
         // backward, top layer down: dW_l = dZ_l^T H_{l-1}, db_l = colsum dZ_l, dZ_{l-1} = (dZ_l W_l) * GELU'(Z_{l-1})
@@ -1554,6 +1686,45 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
                                                                  L.vW, L.mb, L.vb, L.Wb, L.Wt, lr, bc1, bc2);
     }
     return check_cuda(cudaGetLastError(), "train adam");
+}
+
+extern "C" int chem_mlp_set_physics_loss(chem_mlp *m, double lam_m, double lam_q, double s_m, double s_q) {
+    if (!m) return set_error(CHEM_EINVAL, "chem_mlp_set_physics_loss: null handle");
+    if (!(lam_m >= 0.0) || !(lam_q >= 0.0) || !(s_m > 0.0) || !(s_q > 0.0) || !std::isfinite(lam_m) ||
+        !std::isfinite(lam_q) || !std::isfinite(s_m) || !std::isfinite(s_q))
+        return set_error(CHEM_EINVAL, "chem_mlp_set_physics_loss: weights must be >= 0 and scales > 0, finite");
+    if (m->ens && (lam_m != 0.0 || lam_q != 0.0))
+        return set_error(CHEM_EUNSUPPORTED, "chem_mlp_set_physics_loss: the per-species ensemble trains each network "
+                                            "on its own output; the physics terms couple the outputs");
+    m->lam_m = lam_m;
+    m->lam_q = lam_q;
+    m->s_m = s_m;
+    m->s_q = s_q;
+    return CHEM_OK;
+}
+
+extern "C" int chem_mlp_fit_physics_scales(chem_mlp *m, int64_t n, int64_t ld, const double *T, const double *Y,
+                                           const double *Y1, double *s_m, double *s_q, chem_stream_t stream) {
+    if (!m || !s_m || !s_q) return set_error(CHEM_EINVAL, "chem_mlp_fit_physics_scales: null argument");
+    if (n < 1 || ld < n || (ld & 3) != 0 || !T || !Y || !Y1 || !aligned16(T) || !aligned16(Y) || !aligned16(Y1))
+        return set_error(CHEM_EINVAL, "chem_mlp_fit_physics_scales: need 1 <= n <= ld, ld % 4 == 0, aligned arrays");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_mlp_fit_physics_scales: " + why);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // the block partials and the result reuse the out-of-distribution fit's scratch (512 x 6 floats)
+    const int nb = 256;
+    double *part = reinterpret_cast<double *>(m->ood_part);
+    phys_scales_kernel<<<nb, 256, 0, st>>>(n, ld, T, Y, Y1, m->n_out, m->out_sp_dev, phys_loss(m), part);
+    phys_scales_reduce_kernel<<<1, 32, 0, st>>>(nb, n, part, part + 2 * nb);
+    int rc = check_cuda(cudaGetLastError(), "chem_mlp_fit_physics_scales launch");
+    double h[2] = {0.0, 0.0};
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(h, part + 2 * nb, sizeof(h), cudaMemcpyDeviceToHost, st),
+                             "chem_mlp_fit_physics_scales copy");
+    if (!rc) rc = check_cuda(cudaStreamSynchronize(st), "chem_mlp_fit_physics_scales sync");
+    if (rc) return rc;
+    *s_m = h[0];
+    *s_q = h[1];
+    return CHEM_OK;
 }
 
 extern "C" int chem_mlp_set_fusion(chem_mlp *m, int on) {

@@ -128,8 +128,35 @@ __device__ void troe_F(const double *tp, double T, double invT, double Prd, doub
     dFdT_atPr = F * 2.302585092994046 * dlgF_dphi * dphi_dT;
 }
 
-// f = f(y) for the warp's cell. With jac, also stores what build_matrix needs.
-template <int W>
+// The same blending in FP32 (the mixed mode): F, glg and dF/dT at fixed Pr to FP32 accuracy.
+__device__ void troe_F_f32(const double *tp, float T, float invT, float Prd, float &F, float &glg, float &dFdT_atPr) {
+    const float a = f64_to_f32_trunc(__ldg(tp)), r3 = f64_to_f32_trunc(__ldg(tp + 1));
+    const float r1 = f64_to_f32_trunc(__ldg(tp + 2)), T2 = f64_to_f32_trunc(__ldg(tp + 3));
+    const float e3 = expf(-T * r3), e1 = expf(-T * r1), e2 = expf(-T2 * invT);
+    const float Fc = (1.0f - a) * e3 + a * e1 + e2;
+    const float dFc = -(1.0f - a) * r3 * e3 - a * r1 * e1 + T2 * invT * invT * e2;
+    const float phi = log10f(Fc);
+    const float c = -0.4f - 0.67f * phi, nn = 0.75f - 1.27f * phi, d = 0.14f;
+    const float L = log10f(Prd) + c;
+    const float rden = 1.0f / (nn - d * L);
+    const float f1 = L * rden;
+    const float rq = 1.0f / (1.0f + f1 * f1);
+    F = exp10f(phi * rq);
+    const float df1_dL = nn * rden * rden;
+    glg = -phi * 2.0f * f1 * rq * rq * df1_dL;
+    const float df1_dphi = (-0.67f * (nn - d * L) - L * (-1.27f + d * 0.67f)) * rden * rden;
+    const float dlgF_dphi = rq - phi * 2.0f * f1 * rq * rq * df1_dphi;
+    const float dphi_dT = dFc / (Fc * 2.30258509f);
+    dFdT_atPr = F * 2.30258509f * dlgF_dphi * dphi_dT;
+}
+
+// exp(x) for the mixed mode: the argument and the result cross between FP64 and FP32 on the
+// integer pipe (truncation: relative error below 2^-23 of the argument), exp in FP32
+__device__ __forceinline__ double exp_mx(double x) { return f32_to_f64_int(expf(f64_to_f32_trunc(x))); }
+
+// f = f(y) for the warp's cell. With jac, also stores what build_matrix needs. MX (the mixed
+// mode): the rate constants' exponentials and the fall-off blending in FP32, the rest FP64.
+template <int W, bool MX>
 __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int lane, double p, const double y[2],
                              double f[2], bool jac) {
     const int N = m.N, R = m.R, n = N + 1;
@@ -199,7 +226,7 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int 
         const int p0 = __ldg(pr), p1 = __ldg(pr + 1), p2 = __ldg(pr + 2);
         const double beta = __ldg(m.beta + j), EaR = __ldg(m.EaR + j);
         const double lnkf = __ldg(m.lnA + j) + beta * lnT - EaR * invT;
-        const double kf = exp(lnkf);
+        const double kf = MX ? exp_mx(lnkf) : exp(lnkf);
         double lnKp = 0.0, dH = 0.0;
         if (p0 >= 0) { lnKp += sh.SR[p0] - sh.HRT[p0]; dH += sh.HRT[p0]; }
         if (r0 >= 0) { lnKp -= sh.SR[r0] - sh.HRT[r0]; dH -= sh.HRT[r0]; }
@@ -209,7 +236,7 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int 
         if (r2 >= 0) { lnKp -= sh.SR[r2] - sh.HRT[r2]; dH -= sh.HRT[r2]; }
         const double dnu = (double)__ldg(m.dnu + j);
         // k_r = k_f / K_c, ln K_c = ln K_p + dnu ln(P_std / RT)
-        const double kr = exp(lnkf - lnKp - dnu * lnPRT);
+        const double kr = MX ? exp_mx(lnkf - lnKp - dnu * lnPRT) : exp(lnkf - lnKp - dnu * lnPRT);
         double Pf = 1.0, Pr = 1.0;
         if (r0 >= 0) Pf *= sh.C[r0];
         if (r1 >= 0) Pf *= sh.C[r1];
@@ -229,11 +256,21 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int 
                 dFdC = 1.0;
             } else {
                 const double beta0 = __ldg(m.beta0 + j), Ea0R = __ldg(m.Ea0R + j);
-                const double ratio = exp(__ldg(m.lnA0 + j) + beta0 * lnT - Ea0R * invT - lnkf);   // k0 / k_inf
+                const double lr = __ldg(m.lnA0 + j) + beta0 * lnT - Ea0R * invT - lnkf;
+                const double ratio = MX ? exp_mx(lr) : exp(lr);   // k0 / k_inf
                 double Prd = M * ratio;
                 if (Prd < 1e-300) Prd = 1e-300;
                 double Ft, glg, dFtdT;
-                troe_F(m.troe_r + 4 * j, T, invT, Prd, Ft, glg, dFtdT);
+                if (MX) {
+                    float Ff, gf, df;
+                    troe_F_f32(m.troe_r + 4 * j, f64_to_f32_trunc(T), f64_to_f32_trunc(invT),
+                               fmaxf(f64_to_f32_trunc(Prd), 1e-37f), Ff, gf, df);
+                    Ft = f32_to_f64_int(Ff);
+                    glg = f32_to_f64_int(gf);
+                    dFtdT = f32_to_f64_int(df);
+                } else {
+                    troe_F(m.troe_r + 4 * j, T, invT, Prd, Ft, glg, dFtdT);
+                }
                 const double ip = 1.0 / (1.0 + Prd);
                 const double blend = Prd * ip;
                 const double dF_dPrd = Ft * ip * (ip + glg);
@@ -394,36 +431,36 @@ __device__ void build_matrix(const DevMech &m, const Slice &sh, Team<W> tm, int 
     tm.sync();
 }
 
-// In-place LU with partial pivoting; false for a zero or non-finite pivot column.
-// In a team every warp searches the pivot (same data, same choice), the first
-// warp swaps and scales, and the trailing update splits the rows over the warps.
-template <int W>
-__device__ bool lu_factor(const Slice &sh, Team<W> tm, int lane, int n) {
-    double *G = sh.G;
+// In-place LU with partial pivoting of G (FP64, or its FP32 copy in the mixed mode), the
+// reciprocal pivots in invd and the pivot rows in sh.piv; false for a zero or non-finite pivot
+// column. In a team every warp searches the pivot (same data, same choice), the first warp swaps
+// and scales, and the trailing update splits the rows over the warps.
+template <int W, typename real>
+__device__ bool lu_factor(const Slice &sh, real *G, real *invd, Team<W> tm, int lane, int n) {
     for (int k = 0; k < n; ++k) {
-        double best = -1.0;
+        real best = -1;
         int bi = n;
         for (int s = 0; s < 2; ++s) {
             const int i = lane + 32 * s;
             if (i >= k && i < n) {
-                const double v = fabs(G[i * n + k]);
+                const real v = fabs(G[i * n + k]);
                 if (v > best || (v == best && i < bi)) { best = v; bi = i; }
             }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(kFull, best, o);
+            const real ob = __shfl_xor_sync(kFull, best, o);
             const int oi = __shfl_xor_sync(kFull, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (!(best > 0.0) || bi >= n) return false;
+        if (!(best > 0) || !(best < (real)INFINITY) || bi >= n) return false;
         if (tm.lead()) {
             if (lane == 0) sh.piv[k] = bi;
             if (bi != k) {
                 for (int s = 0; s < 2; ++s) {
                     const int c = lane + 32 * s;
                     if (c < n) {
-                        const double t = G[k * n + c];
+                        const real t = G[k * n + c];
                         G[k * n + c] = G[bi * n + c];
                         G[bi * n + c] = t;
                     }
@@ -431,9 +468,9 @@ __device__ bool lu_factor(const Slice &sh, Team<W> tm, int lane, int n) {
             }
         }
         tm.sync();
-        const double rp = 1.0 / G[k * n + k];
+        const real rp = (real)1 / G[k * n + k];
         if (tm.lead()) {
-            if (lane == 0) sh.invd[k] = rp;
+            if (lane == 0) invd[k] = rp;
             for (int s = 0; s < 2; ++s) {
                 const int i = lane + 32 * s;
                 if (i > k && i < n) G[i * n + k] *= rp;
@@ -443,7 +480,7 @@ __device__ bool lu_factor(const Slice &sh, Team<W> tm, int lane, int n) {
         for (int s = 0; s < 2; ++s) {
             const int c = lane + 32 * s;
             if (c > k && c < n) {
-                const double akc = G[k * n + c];
+                const real akc = G[k * n + c];
                 for (int i = k + 1 + tm.wt; i < n; i += W) G[i * n + c] -= G[i * n + k] * akc;
             }
         }
@@ -452,10 +489,11 @@ __device__ bool lu_factor(const Slice &sh, Team<W> tm, int lane, int n) {
     return true;
 }
 
-// b <- G^-1 b with the stored factors; b is lane-distributed. bsw is this
-// warp's own permutation buffer (every warp of a team solves on its own).
-__device__ void lu_solve(const Slice &sh, double *bsw, int lane, int n, double b[2]) {
-    const double *G = sh.G;
+// b <- G^-1 b with the stored factors G, invd (FP64, or FP32 in the mixed mode); b is
+// lane-distributed. bsw is this warp's own permutation buffer (every warp of a team solves on
+// its own).
+template <typename real>
+__device__ void tri_solve(const Slice &sh, const real *G, const real *invd, real *bsw, int lane, int n, real b[2]) {
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
         if (c < n) bsw[c] = b[s];
@@ -464,16 +502,16 @@ __device__ void lu_solve(const Slice &sh, double *bsw, int lane, int n, double b
     if (lane == 0) {
         for (int k = 0; k < n; ++k) {
             const int p = sh.piv[k];
-            if (p != k) { const double t = bsw[k]; bsw[k] = bsw[p]; bsw[p] = t; }
+            if (p != k) { const real t = bsw[k]; bsw[k] = bsw[p]; bsw[p] = t; }
         }
     }
     __syncwarp();
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
-        b[s] = (c < n) ? bsw[c] : 0.0;
+        b[s] = (c < n) ? bsw[c] : (real)0;
     }
     for (int k = 0; k < n - 1; ++k) {
-        const double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
+        const real bk = __shfl_sync(kFull, k >> 5 ? b[1] : b[0], k & 31);
         for (int s = 0; s < 2; ++s) {
             const int i = lane + 32 * s;
             if (i > k && i < n) b[s] -= G[i * n + k] * bk;
@@ -481,10 +519,10 @@ __device__ void lu_solve(const Slice &sh, double *bsw, int lane, int n, double b
     }
     for (int k = n - 1; k >= 0; --k) {
         if ((k & 31) == lane) {
-            if (k >> 5) b[1] *= sh.invd[k];
-            else b[0] *= sh.invd[k];
+            if (k >> 5) b[1] *= invd[k];
+            else b[0] *= invd[k];
         }
-        const double bk = __shfl_sync(kFull, sel(b, k >> 5), k & 31);
+        const real bk = __shfl_sync(kFull, k >> 5 ? b[1] : b[0], k & 31);
         for (int s = 0; s < 2; ++s) {
             const int i = lane + 32 * s;
             if (i < k) b[s] -= G[i * n + k] * bk;
@@ -493,8 +531,60 @@ __device__ void lu_solve(const Slice &sh, double *bsw, int lane, int n, double b
     __syncwarp();
 }
 
-// Integrates cells popped from the work queue until it is exhausted; W warps per cell.
-template <int W>
+// b <- G^-1 b with the FP64 factors (the default, FP64 mode)
+__device__ __forceinline__ void lu_solve(const Slice &sh, double *bsw, int lane, int n, double b[2]) {
+    tri_solve<double>(sh, sh.G, sh.invd, bsw, lane, n, b);
+}
+
+// The mixed mode's stage solve: x = G^-1 b with the FP32 factors Gf of G, then one step of
+// iterative refinement against the FP64 matrix G: r = b - G x in FP64 and x += Gf^-1 r. The
+// correction solves the residual to FP32's relative accuracy, so the refined x carries about
+// cond(G) 2^-24 times that error (FP64-grade for the Jacobians of the fallback cells). The
+// conversions between FP64 and FP32 run on the integer pipe (truncation; magnitudes below
+// 2^-126 become 0).
+__device__ void lu_solve_mixed(const Slice &sh, const float *Gf, const float *invdf, double *bsw, int lane, int n,
+                               double b[2]) {
+    float v[2] = {f64_to_f32_trunc(b[0]), f64_to_f32_trunc(b[1])};
+    tri_solve<float>(sh, Gf, invdf, reinterpret_cast<float *>(bsw), lane, n, v);
+    const double x[2] = {f32_to_f64_int(v[0]), f32_to_f64_int(v[1])};
+    __syncwarp();
+    for (int s = 0; s < 2; ++s) {
+        const int c = lane + 32 * s;
+        if (c < n) bsw[c] = x[s];
+    }
+    __syncwarp();
+    double r[2] = {0.0, 0.0};
+    for (int s = 0; s < 2; ++s) {
+        const int c = lane + 32 * s;
+        if (c < n) {
+            const double *row = sh.G + (size_t)c * n;
+            double acc = b[s];
+            for (int j = 0; j < n; ++j) acc = fma(-row[j], bsw[j], acc);
+            r[s] = acc;
+        }
+    }
+    __syncwarp();
+    float w[2] = {f64_to_f32_trunc(r[0]), f64_to_f32_trunc(r[1])};
+    tri_solve<float>(sh, Gf, invdf, reinterpret_cast<float *>(bsw), lane, n, w);
+    for (int s = 0; s < 2; ++s) b[s] = x[s] + f32_to_f64_int(w[s]);
+}
+
+// The FP32 copy of G for the mixed mode's factors: it takes the space of the reaction
+// derivatives rdq, which build_matrix has consumed and the stage evaluations do not write
+// (the host checks 4 n^2 <= 48 R). One warp converts (column owners).
+__device__ void copy_matrix_f32(const Slice &sh, int lane, int n) {
+    float *Gf = reinterpret_cast<float *>(sh.rdq);
+    for (int s = 0; s < 2; ++s) {
+        const int c = lane + 32 * s;
+        if (c < n)
+            for (int r = 0; r < n; ++r) Gf[r * n + c] = f64_to_f32_trunc(sh.G[r * n + c]);
+    }
+    __syncwarp();
+}
+
+// Integrates cells popped from the work queue until it is exhausted; W warps per cell. MX: the
+// mixed mode (FP32 rate exponentials and fall-off blending; FP32 LU with one FP64 refinement).
+template <int W, bool MX>
 __device__ void integrate_cells(const DevMech &m, char *smem, int *blk_pos, int64_t limit, int64_t ld, double dt,
                                 const chem_ode_opts &o, double *__restrict__ Tg, const double *__restrict__ pg,
                                 double *__restrict__ Yg, int32_t *__restrict__ status,
@@ -536,34 +626,48 @@ __device__ void integrate_cells(const DevMech &m, char *smem, int *blk_pos, int6
             const double rem = dt - t;
             bool last = false;
             if (h >= rem) { h = rem; last = true; }
-            EvalInfo info = eval_rhs<W>(m, sh, tm, lane, p, y, f0, true);
+            EvalInfo info = eval_rhs<W, MX>(m, sh, tm, lane, p, y, f0, true);
             bool bad = false;
             for (int s = 0; s < 2; ++s)
                 if (lane + 32 * s < n && !isfinite(f0[s])) bad = true;
             if (__any_sync(kFull, bad)) { stat = CHEM_CELL_NONFINITE; break; }
             build_matrix<W>(m, sh, tm, lane, info, h);
             ++nst;
-            if (!lu_factor<W>(sh, tm, lane, n)) { h *= 0.2; rejected_last = 1; continue; }
+            float *Gf = reinterpret_cast<float *>(sh.rdq);
+            float *invdf = reinterpret_cast<float *>(sh.invd);
+            bool factored;
+            if (MX) {
+                if (tm.lead()) copy_matrix_f32(sh, lane, n);
+                tm.sync();
+                factored = lu_factor<W, float>(sh, Gf, invdf, tm, lane, n);
+            } else {
+                factored = lu_factor<W, double>(sh, sh.G, sh.invd, tm, lane, n);
+            }
+            if (!factored) { h *= 0.2; rejected_last = 1; continue; }
+            auto solve = [&](double b[2]) {
+                if (MX) lu_solve_mixed(sh, Gf, invdf, bsw, lane, n, b);
+                else lu_solve(sh, bsw, lane, n, b);
+            };
             const double ih = 1.0 / h;
             // stage 1
             for (int s = 0; s < 2; ++s) K1[s] = f0[s];
-            lu_solve(sh, bsw, lane, n, K1);
+            solve(K1);
             // stage 2: the stage point is y itself (a21 = 0)
             for (int s = 0; s < 2; ++s) K2[s] = f0[s] + (kC21 * ih) * K1[s];
-            lu_solve(sh, bsw, lane, n, K2);
+            solve(K2);
             // stage 3: y + 2 K1
             for (int s = 0; s < 2; ++s) ys[s] = y[s] + kA31 * K1[s];
-            eval_rhs<W>(m, sh, tm, lane, p, ys, fs, false);
+            eval_rhs<W, MX>(m, sh, tm, lane, p, ys, fs, false);
             for (int s = 0; s < 2; ++s) {
                 double v = fs[s];
                 v += (kC31 * ih) * K1[s];
                 v += (kC32 * ih) * K2[s];
                 K3[s] = v;
             }
-            lu_solve(sh, bsw, lane, n, K3);
+            solve(K3);
             // stage 4: y + 2 K1 + K3
             for (int s = 0; s < 2; ++s) ys[s] = y[s] + kA41 * K1[s] + kA43 * K3[s];
-            eval_rhs<W>(m, sh, tm, lane, p, ys, fs, false);
+            eval_rhs<W, MX>(m, sh, tm, lane, p, ys, fs, false);
             for (int s = 0; s < 2; ++s) {
                 double v = fs[s];
                 v += (kC41 * ih) * K1[s];
@@ -571,7 +675,7 @@ __device__ void integrate_cells(const DevMech &m, char *smem, int *blk_pos, int6
                 v += (kC43 * ih) * K3[s];
                 K4[s] = v;
             }
-            lu_solve(sh, bsw, lane, n, K4);
+            solve(K4);
             // y_new = y + 2 K1 + K3 + K4, error = K4
             double acc = 0.0;
             bool nonfinite = false;
@@ -653,13 +757,22 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
     char *smem = smem_raw + kSmemHeader;
     const int64_t limit = list ? (int64_t)(*list_count < (unsigned int)ncells ? *list_count : (unsigned int)ncells)
                                : ncells;
+    // the mixed mode keeps its FP32 factors in the space of the 6 R reaction derivatives
+    const bool mx = o.mode == CHEM_ODE_MIXED && 4 * (m.N + 1) * (m.N + 1) <= 48 * m.R;
     if (limit <= (int64_t)team_blocks) {
         if ((int)blockIdx.x >= team_blocks) return;
-        integrate_cells<kWarps>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue, list,
-                                ok_status);
+        if (mx)
+            integrate_cells<kWarps, true>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue,
+                                          list, ok_status);
+        else
+            integrate_cells<kWarps, false>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue,
+                                           list, ok_status);
+    } else if (mx) {
+        integrate_cells<1, true>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue, list,
+                                 ok_status);
     } else {
-        integrate_cells<1>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue, list,
-                           ok_status);
+        integrate_cells<1, false>(m, smem, blk_pos, limit, ld, dt, o, Tg, pg, Yg, status, nsteps_out, queue, list,
+                                  ok_status);
     }
 }
 
@@ -688,7 +801,7 @@ __global__ void __launch_bounds__(kWarps * 32) pasr_kernel(DevMech m, int64_t nc
             const int c = lane + 32 * s;
             y[s] = (c == 0) ? T0[cell] : (c < n ? Y0[(int64_t)(c - 1) * ld + cell] : 0.0);
         }
-        eval_rhs<1>(m, sh, tm, lane, pg[cell], y, f, false);
+        eval_rhs<1, false>(m, sh, tm, lane, pg[cell], y, f, false);
         double tmax = -1.0;                       // species times are >= 0: -1 marks none
         for (int s = 0; s < 2; ++s) {
             const int c = lane + 32 * s;
@@ -781,6 +894,8 @@ extern "C" int chem_step_stiff(const chem_mech *m, int64_t ncells, int64_t ld, d
     if (opts) o = *opts;
     if (!(o.rtol > 0.0) || !(o.atol_Y > 0.0) || !(o.atol_T > 0.0) || !(o.h0 > 0.0) || o.max_steps < 1)
         return set_error(CHEM_EINVAL, "chem_step_stiff: tolerances, h0 and max_steps must be positive");
+    if (o.mode != CHEM_ODE_FP64 && o.mode != CHEM_ODE_MIXED)
+        return set_error(CHEM_EINVAL, "chem_step_stiff: mode must be CHEM_ODE_FP64 or CHEM_ODE_MIXED");
     std::string why;
     if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "chem_step_stiff: " + why);
     size_t per_warp = slice_bytes(m->N, m->R);

@@ -39,10 +39,12 @@ def gelu_grad2(z):
     return np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi) * (2.0 - z * z)
 
 
-def gradients_with_sigma(layers, z, target, sign_from):
+def gradients_with_sigma(layers, z, target, sign_from, dout=None):
     """FP64 gradients of Eq. 5 for one network (layers: [(W [out, in], b)], inputs z [B, n_in],
     targets [B, n_out]), the L1 sign taken on sign_from, and the standard deviations above.
-    Returns (loss, grads, sigmas, min |sign_from - target|) with grads and sigmas as [(dW, db)]."""
+    dout (optional, [B, n_out]): dL/du of another loss (the physics terms), which the device
+    stores as BF16 (one rounding, s = 2^-9 |dout|). Returns (loss, grads, sigmas,
+    min |sign_from - target|) with grads and sigmas as [(dW, db)]; loss is Eq. 5's."""
     z = np.asarray(z, np.float64)
     Bn = z.shape[0]
     nl = len(layers)
@@ -63,8 +65,12 @@ def gradients_with_sigma(layers, z, target, sign_from):
     u = pres[-1]
     res = np.asarray(sign_from, np.float64) - target
     loss = float(np.abs(u - target).sum() / Bn)
-    g = np.sign(res) / Bn
-    vg = np.zeros_like(g)
+    if dout is None:
+        g = np.sign(res) / Bn
+        vg = np.zeros_like(g)
+    else:
+        g = np.asarray(dout, np.float64)
+        vg = R2 * g * g
     grads, sig = [None] * nl, [None] * nl
     for i in range(nl - 1, -1, -1):
         W = layers[i][0]
