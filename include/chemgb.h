@@ -158,7 +158,9 @@ typedef struct {
  * the FP64 matrix (the FP64 residual r = b - G x and x += G_f32^-1 r), which
  * brings the solve to FP64-grade accuracy for FP32 work. The state update, the
  * error norm and the step-size control stay FP64. The mode needs 12 R >= (N+1)^2
- * (the FP32 factors share the reaction workspace); otherwise FP64 is used. */
+ * (the FP32 factors share the reaction workspace) and rtol >= 1e-5 (the FP32
+ * rates' relative noise of about 1e-6 would stall the step control of tighter
+ * tolerances); otherwise the call integrates in FP64. */
 enum { CHEM_ODE_FP64 = 0, CHEM_ODE_MIXED = 1 };
 
 /* Fills *o with the defaults listed above. */

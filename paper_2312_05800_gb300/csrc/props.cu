@@ -243,11 +243,14 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 }
 
 // Thermo only (cp and h; the memory-bound part of props_eval), FP32 arithmetic.
-// One thread per cell in a grid-stride loop at full occupancy, so that enough
-// loads are in flight to keep HBM busy; the NASA-7 rows of both ranges and 1/W
-// are staged in shared memory (3 float4 per species and range). The arithmetic
-// is that of props_kernel's first pass, so cp and h are bitwise the same.
-template <typename in_t>
+// One thread per cell in a grid-stride loop. Every species row of the cell is
+// loaded before any arithmetic (the species loop unrolled to the compile-time
+// bound NMAX), so a thread has up to NMAX independent loads in flight: enough
+// bytes in flight to keep HBM busy at modest occupancy. The NASA-7 rows of both
+// ranges and 1/W are staged in shared memory (3 float4 per species and range).
+// The arithmetic is that of props_kernel's first pass, so cp and h are bitwise
+// the same.
+template <typename in_t, int NMAX>
 __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTables<float> tb, int64_t ncells,
                                                      int64_t ld, const in_t *__restrict__ Tg,
                                                      const in_t *__restrict__ Yg, float *__restrict__ cpg,
@@ -265,51 +268,64 @@ __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTab
     const float R = float(kR);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
-        const float T = to_real<float>(Tg[i]);
+        in_t yr[NMAX];
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) yr[k] = (k < N) ? __ldcs(Yg + (int64_t)k * ld + i) : in_t(0);
+        const float T = to_real<float>(__ldcs(Tg + i));
         const float4 *tab = th_tab + ((T >= T_mid) ? 3 * N : 0);
         float cpm = 0.0f, hm = 0.0f;
-#pragma unroll 4
-        for (int k = 0; k < N; ++k) {
-            const float y = to_real<float>(Yg[(int64_t)k * ld + i]);
-            const float4 q0 = tab[3 * k], q1 = tab[3 * k + 1], q2 = tab[3 * k + 2];
-            float cpR = q1.x;
-            cpR = fmaf(cpR, T, q0.w);
-            cpR = fmaf(cpR, T, q0.z);
-            cpR = fmaf(cpR, T, q0.y);
-            cpR = fmaf(cpR, T, q0.x);
-            float hR = q2.y;
-            hR = fmaf(hR, T, q2.x);
-            hR = fmaf(hR, T, q1.w);
-            hR = fmaf(hR, T, q1.z);
-            hR = fmaf(hR, T, q1.y);
-            hR = hR + q2.z / T;
-            const float yw = y * q2.w;
-            cpm = fmaf(yw, cpR, cpm);
-            hm = fmaf(yw, hR, hm);
+#pragma unroll
+        for (int k = 0; k < NMAX; ++k) {
+            if (k < N) {
+                const float y = to_real<float>(yr[k]);
+                const float4 q0 = tab[3 * k], q1 = tab[3 * k + 1], q2 = tab[3 * k + 2];
+                float cpR = q1.x;
+                cpR = fmaf(cpR, T, q0.w);
+                cpR = fmaf(cpR, T, q0.z);
+                cpR = fmaf(cpR, T, q0.y);
+                cpR = fmaf(cpR, T, q0.x);
+                float hR = q2.y;
+                hR = fmaf(hR, T, q2.x);
+                hR = fmaf(hR, T, q1.w);
+                hR = fmaf(hR, T, q1.z);
+                hR = fmaf(hR, T, q1.y);
+                hR = hR + q2.z / T;
+                const float yw = y * q2.w;
+                cpm = fmaf(yw, cpR, cpm);
+                hm = fmaf(yw, hR, hm);
+            }
         }
-        if (cpg) cpg[i] = cpm * R;
-        if (hg) hg[i] = hm * R * T;
+        if (cpg) __stcs(cpg + i, cpm * R);
+        if (hg) __stcs(hg + i, hm * R * T);
     }
+}
+
+template <typename in_t, int NMAX>
+int launch_thermo_n(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *Y, void *cp, void *h,
+                    cudaStream_t st) {
+    const size_t smem = (size_t)6 * m->N * sizeof(float4);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_kernel<in_t, NMAX>, 256, smem);
+    const int64_t max_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+    const int64_t need = (ncells + 255) / 256;
+    const int blocks = (int)(need < max_blocks ? need : max_blocks);
+    void *pb = prof_begin(st);
+    thermo_kernel<in_t, NMAX><<<blocks, 256, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,
+                                                         static_cast<const in_t *>(T), static_cast<const in_t *>(Y),
+                                                         static_cast<float *>(cp), static_cast<float *>(h));
+    prof_end(pb, st, "thermo_kernel", (double)ncells * 24.0 * m->N,
+             (double)ncells * ((m->N + 1) * sizeof(in_t) + 2 * sizeof(float)));
+    return check_cuda(cudaGetLastError(), "props_eval (thermo) launch");
 }
 
 template <typename in_t>
 int launch_thermo(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *Y, void *cp, void *h,
                   cudaStream_t st) {
-    const size_t smem = (size_t)6 * m->N * sizeof(float4);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_kernel<in_t>, 256, smem);
-    const int64_t max_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (ncells + 255) / 256;
-    const int blocks = (int)(need < max_blocks ? need : max_blocks);
-    void *pb = prof_begin(st);
-    thermo_kernel<in_t><<<blocks, 256, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,
-                                                   static_cast<const in_t *>(T), static_cast<const in_t *>(Y),
-                                                   static_cast<float *>(cp), static_cast<float *>(h));
-    prof_end(pb, st, "thermo_kernel", (double)ncells * 24.0 * m->N,
-             (double)ncells * ((m->N + 1) * sizeof(in_t) + 2 * sizeof(float)));
-    return check_cuda(cudaGetLastError(), "props_eval (thermo) launch");
+    if (m->N <= 16) return launch_thermo_n<in_t, 16>(m, ncells, ld, T, Y, cp, h, st);
+    if (m->N <= 32) return launch_thermo_n<in_t, 32>(m, ncells, ld, T, Y, cp, h, st);
+    return launch_thermo_n<in_t, 64>(m, ncells, ld, T, Y, cp, h, st);
 }
 
 template <typename real, typename in_t, int NMAX>

@@ -39,6 +39,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kWarps = 4;
 constexpr size_t kSmemHeader = 16;   // the team's queue ticket, ahead of the warp slices
+constexpr double kMixedMinRtol = 1e-5;   // tightest rtol the mixed mode integrates (below it: FP64)
 
 // Rodas3 coefficients (g = 1/2 on the diagonal)
 constexpr double kGam = 0.5;
@@ -757,8 +758,9 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
     char *smem = smem_raw + kSmemHeader;
     const int64_t limit = list ? (int64_t)(*list_count < (unsigned int)ncells ? *list_count : (unsigned int)ncells)
                                : ncells;
-    // the mixed mode keeps its FP32 factors in the space of the 6 R reaction derivatives
-    const bool mx = o.mode == CHEM_ODE_MIXED && 4 * (m.N + 1) * (m.N + 1) <= 48 * m.R;
+    // the mixed mode keeps its FP32 factors in the space of the 6 R reaction derivatives, and takes
+    // tolerances no tighter than kMixedMinRtol (its FP32 rates carry about 1e-6 relative noise)
+    const bool mx = o.mode == CHEM_ODE_MIXED && 4 * (m.N + 1) * (m.N + 1) <= 48 * m.R && o.rtol >= kMixedMinRtol;
     if (limit <= (int64_t)team_blocks) {
         if ((int)blockIdx.x >= team_blocks) return;
         if (mx)

@@ -2,9 +2,10 @@
 fall-off blending, FP32 LU with one FP64 iterative-refinement step per stage
 solve) against the FP64 oracle.
 
-* At a tight tolerance (rtol 1e-9) the mixed mode stays within 2e-5 relative of
-  the oracle on Y (|dY| <= 2e-5 |Y| + 1e-12) and 1e-6 on T: the FP32 parts
-  perturb the rates by about 1e-6 relative and the refined solves are FP64-grade.
+* At rtol 1e-5, the tightest tolerance it takes, the mixed mode stays within
+  20 rtol of the oracle's tight integration (the FP32 parts perturb the rates by
+  about 1e-6 relative and the refined solves are FP64-grade); below it the call
+  integrates in FP64 (bitwise the FP64 mode).
 * At the throughput setting (rtol 1e-2) on on-manifold and off-manifold cells,
   its error against the oracle's tight integration (relative L2 of dY over the
   major species, max |dT|) is within 1.5x (+1e-4, +0.01 K) of the FP64 mode's
@@ -42,17 +43,31 @@ def _err(mech, T0, Y0, Ta, Ya, Tr, Yr, n):
 
 
 @pytest.mark.parametrize("name,n", [("c2", 203), ("c5", 37)])
-def test_mixed_tight_tolerance_close_to_oracle(oracle, name, n):
+def test_mixed_moderate_tolerance_close_to_oracle(oracle, name, n):
+    # rtol 1e-5, the tightest the mixed mode takes: within 20 rtol of the oracle's tight integration
     from paper_2312_05800_gb300 import binding
     m = synth.get_mech(name)
     ld = synth.padded_ld(n)
     T, p, Y = synth.states_profiles(m, n, 2101, ld)
-    Tg, Yg, sg, _ = _gpu(name, T, p, Y, n, ld, binding.CHEM_ODE_MIXED, **TIGHT)
+    opts = dict(rtol=1e-5, atol_Y=1e-11, atol_T=1e-5, h0=1e-9, max_steps=20000)
+    Tg, Yg, sg, _ = _gpu(name, T, p, Y, n, ld, binding.CHEM_ODE_MIXED, **opts)
     To, Yo, so, _ = oracle.step_stiff(m, T, p, Y, DT, ncells=n, **TIGHT)
     assert np.all(sg[:n] == 0) and np.all(so[:n] == 0)
-    assert np.all(np.abs(Tg[:n] - To[:n]) <= 1e-6 * To[:n]), np.abs(Tg[:n] / To[:n] - 1).max()
-    err = np.abs(Yg[:, :n] - Yo[:, :n]) - (2e-5 * np.abs(Yo[:, :n]) + 1e-12)
+    assert np.all(np.abs(Tg[:n] - To[:n]) <= 2e-4 * To[:n]), np.abs(Tg[:n] / To[:n] - 1).max()
+    err = np.abs(Yg[:, :n] - Yo[:, :n]) - (2e-4 * np.abs(Yo[:, :n]) + 2e-10)
     assert np.all(err <= 0), err.max()
+
+
+def test_mixed_below_its_tolerance_integrates_in_fp64(oracle):
+    # a tighter rtol than 1e-5 takes the FP64 arithmetic: bitwise the FP64 mode's result
+    from paper_2312_05800_gb300 import binding
+    m = synth.get_mech("c2")
+    n = 203
+    ld = synth.padded_ld(n)
+    T, p, Y = synth.states_profiles(m, n, 2104, ld)
+    a = _gpu("c2", T, p, Y, n, ld, binding.CHEM_ODE_MIXED, **TIGHT)
+    b = _gpu("c2", T, p, Y, n, ld, binding.CHEM_ODE_FP64, **TIGHT)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
 
 
 @pytest.mark.parametrize("off_manifold", [False, True])
