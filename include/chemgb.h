@@ -153,14 +153,14 @@ typedef struct {
  * setting). CHEM_ODE_MIXED, for loose tolerances (the learned step's fallback
  * and the plain method's throughput setting, rtol 1e-2): the exponentials of
  * the rate constants and the Troe blending are evaluated in FP32 (relative
- * error about 1e-6 on the rates, far below rtol), and each stage solve uses an
- * FP32 LU of I/(h gamma) - J followed by one step of iterative refinement with
- * the FP64 matrix (the FP64 residual r = b - G x and x += G_f32^-1 r), which
- * brings the solve to FP64-grade accuracy for FP32 work. The state update, the
- * error norm and the step-size control stay FP64. The mode needs 12 R >= (N+1)^2
- * (the FP32 factors share the reaction workspace) and rtol >= 1e-5 (the FP32
+ * error about 1e-6 on the rates, far below rtol); the matrix I/(h gamma) - J is
+ * assembled and LU-factored in FP32 (a Jacobian with FP32 rounding, about 1e-7
+ * relative), and each stage solve takes one step of iterative refinement with
+ * an FP64 residual r = b - G x, x += G^-1 r, which solves that system to
+ * FP64-grade accuracy. The right-hand side's sums, the state update, the error
+ * norm and the step-size control stay FP64. It takes rtol >= 1e-5 (the FP32
  * rates' relative noise of about 1e-6 would stall the step control of tighter
- * tolerances); otherwise the call integrates in FP64. */
+ * tolerances); a tighter rtol integrates in FP64. */
 enum { CHEM_ODE_FP64 = 0, CHEM_ODE_MIXED = 1 };
 
 /* Fills *o with the defaults listed above. */

@@ -30,10 +30,7 @@
 //               for h1 each takes 16 of a chunk's 64 columns, for h2 the
 //               16-column slices of the pass in turn.
 // Every wait is bounded (a.spin tries); one that runs out records its code
-// and the kernel unwinds as gemm_tn_kernel does. The chunk-by-chunk hand-offs
-// (D1 full / empty, A2 full / empty) are busy tests rather than suspending
-// waits: each chunk's MMA2 depends on the GELU of the same chunk, so their
-// wake-up latency is on the critical path.
+// and the kernel unwinds as gemm_tn_kernel does.
 #pragma once
 
 #include "gemm.cuh"
@@ -202,7 +199,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     atomicExch(err, tc::kErrTimeoutFull);
                     return false;
                 }
-                if (!tc::mbar_spin(d1_empty, (uint32_t)(d1i & 1) ^ 1u, a.spin)) {
+                if (!tc::mbar_wait(d1_empty, (uint32_t)(d1i & 1) ^ 1u, a.spin)) {
                     atomicExch(err, tc::kErrTimeoutTmemEmpty);
                     return false;
                 }
@@ -226,7 +223,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     return false;
                 }
                 if (!tc::mbar_wait(&w2_full[s2], (uint32_t)(w2i / kF12W2Stages) & 1u, a.spin) ||
-                    !tc::mbar_spin(&a2_full[sa], (uint32_t)(a2i / kF12A2Stages) & 1u, a.spin)) {
+                    !tc::mbar_wait(&a2_full[sa], (uint32_t)(a2i / kF12A2Stages) & 1u, a.spin)) {
                     atomicExch(err, tc::kErrTimeoutFull);
                     return false;
                 }
@@ -280,7 +277,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int row0 = tile * kBM + quad * 32;
             for (int p = 0; p < a.passes && ok; ++p, ++pi) {
                 for (int c = 0; c < chunks; ++c, ++d1i, ++a2i) {
-                    if (!__all_sync(0xffffffffu, tc::mbar_spin(d1_full, (uint32_t)(d1i & 1), a.spin))) {
+                    if (!__all_sync(0xffffffffu, tc::mbar_wait(d1_full, (uint32_t)(d1i & 1), a.spin))) {
                         if (lane == 0) atomicExch(err, tc::kErrTimeoutTmemFull);
                         ok = false;
                         break;
@@ -312,7 +309,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     // k-block, at the 128-byte swizzle positions chunk ^ (r % 8)
                     const int sa = a2i % kF12A2Stages;
                     if (!__all_sync(0xffffffffu,
-                                    tc::mbar_spin(&a2_empty[sa], (uint32_t)((a2i / kF12A2Stages) & 1) ^ 1u, a.spin))) {
+                                    tc::mbar_wait(&a2_empty[sa], (uint32_t)((a2i / kF12A2Stages) & 1) ^ 1u, a.spin))) {
                         if (lane == 0) atomicExch(err, tc::kErrTimeoutEmpty);
                         ok = false;
                         break;

@@ -212,10 +212,16 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int 
     info.cp = cp;
     info.dcpdT = dcp;
     info.Wbar = Wbar;
+    // the mixed mode's FP32 concentrations for the third-body sums, in the space of V (written
+    // only by the gather below, after the reaction pass has used them)
+    float *Cf = reinterpret_cast<float *>(sh.V);
     if (wr)
         for (int s = 0; s < 2; ++s) {
             const int c = lane + 32 * s;
-            if (c >= 1 && c < n) sh.C[c - 1] = rho * yw_s[s];
+            if (c >= 1 && c < n) {
+                sh.C[c - 1] = rho * yw_s[s];
+                if (MX) Cf[c - 1] = f64_to_f32_trunc(rho * yw_s[s]);
+            }
         }
     tm.sync();
     // reaction pass (thread per reaction over the team's lanes)
@@ -251,7 +257,13 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int 
         if (type != 0) {
             const double *e = m.eff + (size_t)__ldg(m.tb_row + j) * N;
             double M = 0.0;
-            for (int k = 0; k < N; ++k) M += __ldg(e + k) * sh.C[k];
+            if (MX) {
+                float Mf = 0.0f;
+                for (int k = 0; k < N; ++k) Mf = fmaf(f64_to_f32_trunc(__ldg(e + k)), Cf[k], Mf);
+                M = f32_to_f64_int(Mf);
+            } else {
+                for (int k = 0; k < N; ++k) M += __ldg(e + k) * sh.C[k];
+            }
             if (type == 1) {
                 F = M;
                 dFdC = 1.0;
@@ -336,14 +348,24 @@ __device__ EvalInfo eval_rhs(const DevMech &m, const Slice &sh, Team<W> tm, int 
     return info;
 }
 
-// G = I/(h g) - J from the data of eval_rhs(..., jac = true), built by one warp.
-__device__ void build_matrix_warp(const DevMech &m, const Slice &sh, int lane, const EvalInfo &in, double h) {
+// shared-memory FP64 value in the working type of the matrix assembly (FP32: by truncation on
+// the integer pipe)
+template <typename real>
+__device__ __forceinline__ real rd(double x) {
+    if constexpr (sizeof(real) == 4) return f64_to_f32_trunc(x);
+    else return x;
+}
+
+// G = I/(h g) - J from the data of eval_rhs(..., jac = true), built by one warp into Gm (the FP64
+// matrix sh.G, or in the mixed mode its FP32 counterpart in the same space: the Jacobian then
+// carries FP32 rounding, about 1e-7 relative, which the mixed mode's loose tolerances absorb).
+template <typename real>
+__device__ void build_matrix_warp(const DevMech &m, const Slice &sh, real *G, int lane, const EvalInfo &in, double h) {
     const int N = m.N, n = N + 1;
-    double *G = sh.G;
     for (int s = 0; s < 2; ++s) {            // zero the species block (column owners)
         const int c = lane + 32 * s;
         if (c >= 1 && c < n)
-            for (int r = 1; r < n; ++r) G[r * n + c] = 0.0;
+            for (int r = 1; r < n; ++r) G[r * n + c] = 0;
     }
     __syncwarp();
     // sparse part of JC = d wdot / d C: row owners gather their reactions (ascending)
@@ -351,15 +373,15 @@ __device__ void build_matrix_warp(const DevMech &m, const Slice &sh, int lane, c
         const int c = lane + 32 * s;
         if (c >= 1 && c < n) {
             const int k = c - 1;
-            double *row = G + (size_t)c * n + 1;
+            real *row = G + (size_t)c * n + 1;
             const int b = __ldg(m.inc_ptr + k), e = __ldg(m.inc_ptr + k + 1);
             for (int t = b; t < e; ++t) {
                 const int2 ent = __ldg(m.inc + t);
-                const double nu = (double)ent.y;
+                const real nu = (real)ent.y;
                 for (int u = 0; u < 6; ++u) {
                     const int l = __ldg(m.rsp + 6 * ent.x + u);
                     if (l < 0) break;
-                    row[l] += nu * sh.rdq[6 * ent.x + u];
+                    row[l] += nu * rd<real>(sh.rdq[6 * ent.x + u]);
                 }
             }
         }
@@ -368,16 +390,16 @@ __device__ void build_matrix_warp(const DevMech &m, const Slice &sh, int lane, c
     // dense third-body part: rank-1 terms nu_j (rop dF/dM) eff_j (column owners)
     for (int t = 0; t < m.n_tb; ++t) {
         const int j = __ldg(m.tb_list + t);
-        const double c3 = sh.rc3[j];
+        const real c3 = rd<real>(sh.rc3[j]);
         const double *e = m.eff + (size_t)__ldg(m.tb_row + j) * N;
         for (int s = 0; s < 2; ++s) {
             const int c = lane + 32 * s;
             if (c >= 1 && c < n) {
-                const double v = c3 * __ldg(e + c - 1);
+                const real v = c3 * rd<real>(__ldg(e + c - 1));
                 for (int u = 0; u < 6; ++u) {
                     const int k = __ldg(m.rsp + 6 * j + u);
                     if (k < 0) break;
-                    G[(1 + k) * n + c] += (double)__ldg(m.rnu + 6 * j + u) * v;
+                    G[(1 + k) * n + c] += (real)__ldg(m.rnu + 6 * j + u) * v;
                 }
             }
         }
@@ -387,48 +409,53 @@ __device__ void build_matrix_warp(const DevMech &m, const Slice &sh, int lane, c
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
         if (c >= 1 && c < n) {
-            double acc = 0.0;
-            for (int l = 0; l < N; ++l) acc += G[c * n + 1 + l] * sh.C[l];
-            sh.JCC[c - 1] = acc;
+            real acc = 0;
+            for (int l = 0; l < N; ++l) acc += G[c * n + 1 + l] * rd<real>(sh.C[l]);
+            sh.JCC[c - 1] = (double)acc;
         }
     }
     __syncwarp();
     // chain rule through C(T, Y) and rho(T, Y); then G = I/(h g) - J
-    const double T = in.T, invT = in.invT, cp = in.cp, Wbar = in.Wbar, Q = in.Q;
-    const double invrcp = 1.0 / (in.rho * cp);
-    const double qq = Q * invrcp / cp;              // Q / (rho cp^2)
-    const double RT = kR * T;
-    const double ghinv = 1.0 / (h * kGam);
-    double sT = 0.0;
+    const real T = rd<real>(in.T), invT = rd<real>(in.invT), cp = rd<real>(in.cp), Wbar = rd<real>(in.Wbar);
+    const real Q = rd<real>(in.Q), rho = rd<real>(in.rho), dcpdT = rd<real>(in.dcpdT);
+    const real invrcp = (real)1 / (rho * cp);
+    const real qq = Q * invrcp / cp;              // Q / (rho cp^2)
+    const real Rr = (real)kR;
+    const real RT = Rr * T;
+    const real ghinv = rd<real>(1.0 / (h * kGam));
+    real sT = 0;
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
         if (c < 1 || c >= n) continue;
         // species column c (column owner)
         const int mm = c - 1;
-        const double iWm = __ldg(m.f64.invW + mm);
-        const double a = in.rho * iWm, b = Wbar * iWm;
-        double sTr = 0.0;
+        const real iWm = rd<real>(__ldg(m.f64.invW + mm));
+        const real a = rho * iWm, b = Wbar * iWm;
+        real sTr = 0;
         for (int k = 0; k < N; ++k) {
-            double *g = G + (size_t)(1 + k) * n + c;
-            const double dw = *g * a - b * sh.JCC[k];
-            sTr += sh.HRT[k] * RT * dw;
-            const double J = sh.U[k] * dw + sh.V[k] * iWm;
+            real *g = G + (size_t)(1 + k) * n + c;
+            const real dw = *g * a - b * rd<real>(sh.JCC[k]);
+            sTr += rd<real>(sh.HRT[k]) * RT * dw;
+            const real J = rd<real>(sh.U[k]) * dw + rd<real>(sh.V[k]) * iWm;
             *g = (1 + k == c) ? ghinv - J : -J;
         }
-        G[c] = sTr * invrcp + qq * (cp * Wbar - sh.cpR[mm] * kR) * iWm;   // -J[0][c]
+        G[c] = sTr * invrcp + qq * (cp * Wbar - rd<real>(sh.cpR[mm]) * Rr) * iWm;   // -J[0][c]
         // temperature column entry of row c (row owner)
-        const double dwdT = sh.wT[mm] - sh.JCC[mm] * invT;
-        G[(size_t)c * n] = -(sh.U[mm] * dwdT + sh.U[mm] * sh.wdot[mm] * invT);
-        sT += sh.cpR[mm] * kR * sh.wdot[mm] + sh.HRT[mm] * RT * dwdT;
+        const real dwdT = rd<real>(sh.wT[mm]) - rd<real>(sh.JCC[mm]) * invT;
+        const real Um = rd<real>(sh.U[mm]), wm = rd<real>(sh.wdot[mm]);
+        G[(size_t)c * n] = -(Um * dwdT + Um * wm * invT);
+        sT += rd<real>(sh.cpR[mm]) * Rr * wm + rd<real>(sh.HRT[mm]) * RT * dwdT;
     }
-    sT = warp_sum(sT);
-    if (lane == 0) G[0] = ghinv + sT * invrcp + qq * (cp * invT - in.dcpdT);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sT += __shfl_xor_sync(kFull, sT, o);
+    if (lane == 0) G[0] = ghinv + sT * invrcp + qq * (cp * invT - dcpdT);
     __syncwarp();
 }
 
-template <int W>
-__device__ void build_matrix(const DevMech &m, const Slice &sh, Team<W> tm, int lane, const EvalInfo &in, double h) {
-    if (tm.lead()) build_matrix_warp(m, sh, lane, in, h);
+template <int W, typename real>
+__device__ void build_matrix(const DevMech &m, const Slice &sh, real *G, Team<W> tm, int lane, const EvalInfo &in,
+                             double h) {
+    if (tm.lead()) build_matrix_warp<real>(m, sh, G, lane, in, h);
     tm.sync();
 }
 
@@ -537,14 +564,14 @@ __device__ __forceinline__ void lu_solve(const Slice &sh, double *bsw, int lane,
     tri_solve<double>(sh, sh.G, sh.invd, bsw, lane, n, b);
 }
 
-// The mixed mode's stage solve: x = G^-1 b with the FP32 factors Gf of G, then one step of
-// iterative refinement against the FP64 matrix G: r = b - G x in FP64 and x += Gf^-1 r. The
-// correction solves the residual to FP32's relative accuracy, so the refined x carries about
-// cond(G) 2^-24 times that error (FP64-grade for the Jacobians of the fallback cells). The
+// The mixed mode's stage solve with the FP32 matrix Gc and its FP32 LU factors Gf (both in the
+// space of the FP64 matrix: n^2 floats each): x = Gf^-1 b, then one step of iterative refinement,
+// r = b - Gc x in FP64 arithmetic and x += Gf^-1 r. The correction solves the residual to FP32's
+// relative accuracy, so the refined x carries about cond(G) 2^-24 times that error. The
 // conversions between FP64 and FP32 run on the integer pipe (truncation; magnitudes below
 // 2^-126 become 0).
-__device__ void lu_solve_mixed(const Slice &sh, const float *Gf, const float *invdf, double *bsw, int lane, int n,
-                               double b[2]) {
+__device__ void lu_solve_mixed(const Slice &sh, const float *Gf, const float *invdf, const float *Gc, double *bsw,
+                               int lane, int n, double b[2]) {
     float v[2] = {f64_to_f32_trunc(b[0]), f64_to_f32_trunc(b[1])};
     tri_solve<float>(sh, Gf, invdf, reinterpret_cast<float *>(bsw), lane, n, v);
     const double x[2] = {f32_to_f64_int(v[0]), f32_to_f64_int(v[1])};
@@ -558,9 +585,9 @@ __device__ void lu_solve_mixed(const Slice &sh, const float *Gf, const float *in
     for (int s = 0; s < 2; ++s) {
         const int c = lane + 32 * s;
         if (c < n) {
-            const double *row = sh.G + (size_t)c * n;
+            const float *row = Gc + (size_t)c * n;
             double acc = b[s];
-            for (int j = 0; j < n; ++j) acc = fma(-row[j], bsw[j], acc);
+            for (int j = 0; j < n; ++j) acc = fma(-f32_to_f64_int(row[j]), bsw[j], acc);
             r[s] = acc;
         }
     }
@@ -568,19 +595,6 @@ __device__ void lu_solve_mixed(const Slice &sh, const float *Gf, const float *in
     float w[2] = {f64_to_f32_trunc(r[0]), f64_to_f32_trunc(r[1])};
     tri_solve<float>(sh, Gf, invdf, reinterpret_cast<float *>(bsw), lane, n, w);
     for (int s = 0; s < 2; ++s) b[s] = x[s] + f32_to_f64_int(w[s]);
-}
-
-// The FP32 copy of G for the mixed mode's factors: it takes the space of the reaction
-// derivatives rdq, which build_matrix has consumed and the stage evaluations do not write
-// (the host checks 4 n^2 <= 48 R). One warp converts (column owners).
-__device__ void copy_matrix_f32(const Slice &sh, int lane, int n) {
-    float *Gf = reinterpret_cast<float *>(sh.rdq);
-    for (int s = 0; s < 2; ++s) {
-        const int c = lane + 32 * s;
-        if (c < n)
-            for (int r = 0; r < n; ++r) Gf[r * n + c] = f64_to_f32_trunc(sh.G[r * n + c]);
-    }
-    __syncwarp();
 }
 
 // Integrates cells popped from the work queue until it is exhausted; W warps per cell. MX: the
@@ -632,21 +646,32 @@ __device__ void integrate_cells(const DevMech &m, char *smem, int *blk_pos, int6
             for (int s = 0; s < 2; ++s)
                 if (lane + 32 * s < n && !isfinite(f0[s])) bad = true;
             if (__any_sync(kFull, bad)) { stat = CHEM_CELL_NONFINITE; break; }
-            build_matrix<W>(m, sh, tm, lane, info, h);
-            ++nst;
-            float *Gf = reinterpret_cast<float *>(sh.rdq);
+            // the mixed mode assembles an FP32 matrix Gc and factors its copy Gf, both in the space
+            // of the FP64 matrix
+            float *Gc = reinterpret_cast<float *>(sh.G);
+            float *Gf = Gc + n * n;
             float *invdf = reinterpret_cast<float *>(sh.invd);
             bool factored;
             if (MX) {
-                if (tm.lead()) copy_matrix_f32(sh, lane, n);
+                build_matrix<W, float>(m, sh, Gc, tm, lane, info, h);
+                ++nst;
+                if (tm.lead()) {
+                    for (int s = 0; s < 2; ++s) {
+                        const int c = lane + 32 * s;
+                        if (c < n)
+                            for (int r = 0; r < n; ++r) Gf[r * n + c] = Gc[r * n + c];
+                    }
+                }
                 tm.sync();
                 factored = lu_factor<W, float>(sh, Gf, invdf, tm, lane, n);
             } else {
+                build_matrix<W, double>(m, sh, sh.G, tm, lane, info, h);
+                ++nst;
                 factored = lu_factor<W, double>(sh, sh.G, sh.invd, tm, lane, n);
             }
             if (!factored) { h *= 0.2; rejected_last = 1; continue; }
             auto solve = [&](double b[2]) {
-                if (MX) lu_solve_mixed(sh, Gf, invdf, bsw, lane, n, b);
+                if (MX) lu_solve_mixed(sh, Gf, invdf, Gc, bsw, lane, n, b);
                 else lu_solve(sh, bsw, lane, n, b);
             };
             const double ih = 1.0 / h;
@@ -758,9 +783,9 @@ __global__ void __launch_bounds__(kWarps * 32) stiff_kernel(DevMech m, int64_t n
     char *smem = smem_raw + kSmemHeader;
     const int64_t limit = list ? (int64_t)(*list_count < (unsigned int)ncells ? *list_count : (unsigned int)ncells)
                                : ncells;
-    // the mixed mode keeps its FP32 factors in the space of the 6 R reaction derivatives, and takes
-    // tolerances no tighter than kMixedMinRtol (its FP32 rates carry about 1e-6 relative noise)
-    const bool mx = o.mode == CHEM_ODE_MIXED && 4 * (m.N + 1) * (m.N + 1) <= 48 * m.R && o.rtol >= kMixedMinRtol;
+    // the mixed mode takes tolerances no tighter than kMixedMinRtol (its FP32 rates carry about
+    // 1e-6 relative noise)
+    const bool mx = o.mode == CHEM_ODE_MIXED && o.rtol >= kMixedMinRtol;
     if (limit <= (int64_t)team_blocks) {
         if ((int)blockIdx.x >= team_blocks) return;
         if (mx)
