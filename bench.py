@@ -48,6 +48,7 @@ NCELLS_ANN = 4194304
 DT = 1.0e-6
 TIGHT_OPTS = dict(rtol=1e-6, atol_Y=1e-13, atol_T=1e-6, h0=1e-9, max_steps=20000)
 STIFF_OPTS = dict(rtol=1e-2, atol_Y=1e-8, atol_T=1e-2, h0=1e-9, max_steps=10000)
+STIFF_MODE = 1                  # CHEM_ODE_MIXED on the GPU at the throughput setting (the oracle is FP64)
 PARITY_OPTS = dict(rtol=1e-9, atol_Y=1e-15, atol_T=1e-9, h0=1e-9, max_steps=10000)
 MECH = "c2"
 ORACLE_ACC_CELLS = 4096          # held-out cells whose learned-step error is measured against the oracle
@@ -254,7 +255,7 @@ def bench_stiff(args, rank, world, local):
     cp = torch.empty(NCELLS, dtype=torch.float32, device=dev)
     hh, mu, lam = torch.empty_like(cp), torch.empty_like(cp), torch.empty_like(cp)
     Dk = torch.empty(N, NCELLS, dtype=torch.float32, device=dev)
-    opts = binding.make_opts(**STIFF_OPTS)
+    opts = binding.make_opts(mode=STIFF_MODE, **STIFF_OPTS)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -349,7 +350,7 @@ def bench_stiff(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": stiff_workload(mech),
-                       "path": "stiff+props (FP64 Rodas3 rtol %g, FP32 props)" % STIFF_OPTS["rtol"],
+                       "path": "stiff+props (Rodas3 rtol %g in the mixed mode, FP32 props)" % STIFF_OPTS["rtol"],
                        "cells_per_gpu": NCELLS,
                        "l2": "inputs larger than L2 (0.5 GB FP64 state)",
                        "mean_steps_per_cell": steps_total / NCELLS, "parallelism": "replicas" if world > 1 else "1 GPU"},
@@ -490,7 +491,7 @@ def bench_ann(args, rank, world, local):
         ens_tiles = binding.chem_mlp_autotune(ens, min(args.ens_chunk, 262144))
     if not args.untrained:
         del data
-    fb_opts = binding.make_opts(**STIFF_OPTS)
+    fb_opts = binding.make_opts(mode=STIFF_MODE, **STIFF_OPTS)
     # ---- inference workload
     ncells = args.cells
     T, p, Y = synth.states_profiles(smech, ncells, shard_seed(2003, rank), ld=synth.padded_ld(ncells))
@@ -510,7 +511,7 @@ def bench_ann(args, rank, world, local):
     Tr, Yr = T0.clone(), Y0.clone()
     binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**TIGHT_OPTS), Tr, p0, Yr, status)
     Ts, Ys = T0.clone(), Y0.clone()
-    binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(**STIFF_OPTS), Ts, p0, Ys, status)
+    binding.chem_step_stiff(dm, ne, ld, DT, binding.make_opts(mode=STIFF_MODE, **STIFF_OPTS), Ts, p0, Ys, status)
     T8, Y8 = T0.clone(), Y0.clone()
     if fp8:
         binding.chem_step_ann(dm, net, ne, ld, DT, binding.CHEM_PREC_FP8, fb_opts, T8, p0, Y8, status)
@@ -711,7 +712,8 @@ def bench_ann(args, rank, world, local):
     Yw.copy_(Y0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    binding.chem_step_stiff(dm, ns, ld, DT, binding.make_opts(**STIFF_OPTS), Tw, p0, Yw, status, None, stream)
+    binding.chem_step_stiff(dm, ns, ld, DT, binding.make_opts(mode=STIFF_MODE, **STIFF_OPTS), Tw, p0, Yw, status, None,
+                            stream)
     binding.props_eval(dm, ns, ld, binding.CHEM_F64_IN_F32, Tw, p0, Yw, cp, hh, mu, lam, Dk, stream)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -834,7 +836,7 @@ def bench_ann(args, rank, world, local):
             "accuracy": {"ann_vs_tight_stiff": acc_ann, "stiff_throughput_setting_vs_tight_stiff": acc_stiff,
                          "reference": "chem_step_stiff rtol 1e-6 on the first %d cells" % ne},
             "stiff": {"value": stiff_value, "unit": "cells/s",
-                      "path": "chem_step_stiff rtol %g + props_eval" % STIFF_OPTS["rtol"],
+                      "path": "chem_step_stiff rtol %g (mixed mode) + props_eval" % STIFF_OPTS["rtol"],
                       "sample": "first %d of the %d cells, one step" % (ns, ncells),
                       "ann_speedup": value / stiff_value},
             "training": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": 4096,
@@ -858,7 +860,7 @@ def bench_ann(args, rank, world, local):
             "guard": {"ood": not args.untrained,
                       "grid": "64^3 over (T, h/R, Y_s) for s in %s, neighbourhood >= %d; outside any grid -> fallback"
                       % (args.ood_species, args.ood_kmin), "fallback_cells_per_step": n_fallback, "failed_cells": n_failed,
-                      "fallback_rtol": STIFF_OPTS["rtol"]},
+                      "fallback_rtol": STIFF_OPTS["rtol"], "fallback_mode": "mixed (CHEM_ODE_MIXED)"},
             "autotuned_tiles": tiles,
             "graph": {"ms_per_step": graph_ms, "cells_per_s": world * ncells / (graph_ms / 1e3),
                       "note": "the whole step captured once as a CUDA graph and replayed"},

@@ -523,10 +523,11 @@ int mlp_train_step(chem_mlp *mlp, int64_t batch, const int32_t *idx, int64_t ld,
  * the mechanism's NASA-7 rows in FP32. lam_m = lam_q = 0 (the default) is
  * Eq. 5 alone. Weights >= 0, scales > 0 (CHEM_EINVAL otherwise); non-zero
  * weights on a per-species ensemble return CHEM_EUNSUPPORTED.
- * chem_mlp_fit_physics_scales: s_m = mean_i |sum_j dY*_ij| and
- * s_q = mean_i |sum_j c_ij dY*_ij| over n training pairs (dY* = Y1 - Y of the
- * output species; device SoA), in FP64 with a fixed summation order; host
- * outputs; synchronises the stream. */
+ * chem_mlp_fit_physics_scales: s_m = mean_i sum_j |dY*_ij| (the typical
+ * composition change; the mean bath change is no scale, since an inert bath
+ * such as N2 changes by exactly zero) and s_q = mean_i |sum_j c_ij dY*_ij|
+ * over n training pairs (dY* = Y1 - Y of the output species; device SoA), in
+ * FP64 with a fixed summation order; host outputs; synchronises the stream. */
 int chem_mlp_set_physics_loss(chem_mlp *mlp, double lam_m, double lam_q, double s_m, double s_q);
 int chem_mlp_fit_physics_scales(chem_mlp *mlp, int64_t n, int64_t ld, const double *T, const double *Y,
                                 const double *Y1, double *s_m, double *s_q, chem_stream_t stream);

@@ -9,8 +9,10 @@ conservation and the heat release rate. It gives no formula or weight; the readi
     composition change must get right is the chemical heat it releases at the cell's
     temperature, q = -sum_k h_k(T) dY_k (J/kg, bath included through the closure), so the
     energy and heat-release principles are one term:  L_q = (1/B) sum_i |q_i - q*_i| / s_q.
-  * dY_k = sd_k u_k + mu_k (de-normalised outputs); s_m and s_q are the mean absolute bath
-    change and heat release of the training targets; the total loss is
+  * dY_k = sd_k u_k + mu_k (de-normalised outputs); s_m is the mean total absolute change of the
+    output species, (1/B) sum_i sum_k |dY*_ik|, and s_q the mean absolute heat release of the
+    training targets (the mean bath change itself is no scale: a bath species that takes part in
+    no reaction, like N2 in these mechanisms, changes by exactly zero); the total loss is
     Eq. 5 + lam_m L_m + lam_q L_q.
 Returns the loss and dL/du (sign(0) = 0). Plain numpy and the C oracle's species enthalpies.
 """
@@ -41,8 +43,9 @@ def heat_release(mech, T, dY_out, sp):
 
 
 def scales(mech, T, dY_target, sp):
+    """(s_m, s_q): the mean over samples of sum_k |dY*_k| and of |q*|."""
     q, _ = heat_release(mech, T, dY_target, sp)
-    return float(np.abs(dY_target.sum(axis=1)).mean()), float(np.abs(q).mean())
+    return float(np.abs(dY_target).sum(axis=1).mean()), float(np.abs(q).mean())
 
 
 def loss(mech, u, u_target, T, stats, sp, lam_m, lam_q, s_m, s_q):

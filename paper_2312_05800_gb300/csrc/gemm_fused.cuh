@@ -276,7 +276,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int tile = blockIdx.x; tile < m_tiles && ok; tile += gridDim.x) {
             const int row0 = tile * kBM + quad * 32;
             for (int p = 0; p < a.passes && ok; ++p, ++pi) {
+                // this warp's 16 biases of chunk 0, then of each next chunk ahead of its wait
+                float4 bq[4];
+                {
+                    const float4 *bp = reinterpret_cast<const float4 *>(a.b1 + group * 16);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) bq[i] = __ldg(bp + i);
+                }
                 for (int c = 0; c < chunks; ++c, ++d1i, ++a2i) {
+                    float b[16];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        b[4 * i] = bq[i].x; b[4 * i + 1] = bq[i].y; b[4 * i + 2] = bq[i].z; b[4 * i + 3] = bq[i].w;
+                    }
+                    if (c + 1 < chunks) {
+                        const float4 *bp = reinterpret_cast<const float4 *>(a.b1 + (c + 1) * kF12Chunk + group * 16);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) bq[i] = __ldg(bp + i);
+                    }
                     if (!__all_sync(0xffffffffu, tc::mbar_wait(d1_full, (uint32_t)(d1i & 1), a.spin))) {
                         if (lane == 0) atomicExch(err, tc::kErrTimeoutTmemFull);
                         ok = false;
@@ -289,14 +306,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(d1_empty);
                     // GELU(D1 + b1) of columns 64 c + 16 group .. + 15 as 8 packed BF16 pairs
-                    const int col = c * kF12Chunk + group * 16;
-                    float b[16];
-                    const float4 *bp = reinterpret_cast<const float4 *>(a.b1 + col);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float4 q = __ldg(bp + i);
-                        b[4 * i] = q.x; b[4 * i + 1] = q.y; b[4 * i + 2] = q.z; b[4 * i + 3] = q.w;
-                    }
                     uint32_t w[8];
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {

@@ -461,7 +461,7 @@ __global__ void l1_loss_kernel(int64_t B, const float *__restrict__ u, int ldu, 
     part[i] = acc;
 }
 
-// Scales of the physics terms over n training pairs, FP64: per-block sums of |sum_j dY*_j| and
+// Scales of the physics terms over n training pairs, FP64: per-block sums of sum_j |dY*_j| and
 // |sum_j (h_k - h_bath)(T) dY*_j| (dY* = Y1 - Y of the output species), fixed order within a
 // block (grid-stride, then a tree), written to part[2 blockIdx.x + {0, 1}].
 __global__ void phys_scales_kernel(int64_t n, int64_t ld, const double *__restrict__ T, const double *__restrict__ Y,
@@ -477,10 +477,10 @@ __global__ void phys_scales_kernel(int64_t n, int64_t ld, const double *__restri
         for (int j = 0; j < n_out; ++j) {
             const int k = out_sp[j];
             const double d = Y1[(int64_t)k * ld + i] - Y[(int64_t)k * ld + i];
-            m += d;
+            m += fabs(d);
             q += ((double)(h_over_R(rows + k * 6, t) * __ldg(ph.invW + k)) - hb) * d;
         }
-        am += fabs(m);
+        am += m;
         aq += fabs(q) * 8.314462618;
     }
     sm[threadIdx.x] = am;
