@@ -49,6 +49,7 @@ class chem_hfrd_params(ctypes.Structure):
 
 
 CHEM_PREC_BF16, CHEM_PREC_FP8 = 0, 1
+CHEM_FUSE_12, CHEM_FUSE_34 = 1, 2
 
 
 def library_path() -> str:
@@ -339,15 +340,24 @@ class Mlp:
                                                  ctypes.byref(sq), _stream(stream)))
         return sm.value, sq.value
 
-    def set_fusion(self, on: bool):
-        _check(lib().chem_mlp_set_fusion(self.handle, 1 if on else 0))
+    def set_fusion(self, mask):
+        """CHEM_FUSE_* bits (True: both fusions, False: none)."""
+        if mask is True:
+            mask = CHEM_FUSE_12 | CHEM_FUSE_34
+        elif mask is False:
+            mask = 0
+        _check(lib().chem_mlp_set_fusion(self.handle, int(mask)))
 
     @property
-    def fused(self) -> bool:
+    def fusion(self) -> int:
         r = lib().chem_mlp_get_fusion(self.handle)
         if r < 0:
             _check(r)
-        return bool(r)
+        return r
+
+    @property
+    def fused(self) -> bool:
+        return self.fusion != 0
 
     def free(self):
         if self.handle:

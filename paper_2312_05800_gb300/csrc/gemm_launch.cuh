@@ -265,6 +265,12 @@ int gemm_gelu_grad_grouped(int bn, const GemmOperand &X, const GemmOperand &W, i
 bool fused12_supported(int K1, int N1, int N2);
 int gemm_fused12(const void *X, int64_t ldx, int K1, const void *W1, int64_t ldw1, const void *W2, int64_t ldw2, int M,
                  int N1, int N2, const float *b1, const float *b2, void *h2, int64_t ldh2, int *err, cudaStream_t st);
+// The last hidden layer and the output layer in one launch, h3 kept on chip (gemm_fused34.cuh):
+// u = bf16(GELU(X W3^T + b3)) W4^T + b4 in FP32, bitwise gemm_gelu (layer 3) then gemm_linear
+// (layer 4). X [M][ldx] BF16 with K3 columns, W3 [N3][ldw3], W4 [N4][ldw4] (K = N3), u [M][ldu].
+bool fused34_supported(int K3, int N3, int N4);
+int gemm_fused34(const void *X, int64_t ldx, int K3, const void *W3, int64_t ldw3, const void *W4, int64_t ldw4, int M,
+                 int N3, int N4, const float *b3, const float *b4, float *u, int64_t ldu, int *err, cudaStream_t st);
 // Reduced-precision hidden layer (EpiGeluQ): f8in selects E4M3 operands (X, W) with the per-column
 // scale cs, f8out an E4M3 output scaled by inv_so; otherwise BF16.
 int gemm_gelu_q(bool f8in, bool f8out, int bn, const void *X, int64_t ldx, const void *W, int64_t ldw, int M, int N,

@@ -104,6 +104,7 @@ struct chem_mlp {
     uint64_t seed;
     uint32_t wait_limit;                    // tries of each GEMM pipeline wait (chem_mlp_set_wait_limit)
     int fuse12;                             // layers 1 and 2 of the BF16 forward in one launch (where supported)
+    int fuse34;                             // layers 3 and 4 of the BF16 forward in one launch (where supported)
     // physics terms of the training loss (chem_mlp_set_physics_loss): weights and scales, and the
     // mechanism's FP32 NASA-7 enthalpy rows [2][N][6] and 1/W [N] for the heat release
     double lam_m, lam_q, s_m, s_q;
@@ -863,6 +864,10 @@ PhysLoss phys_loss(const chem_mlp *m) {
 bool fused12_on(const chem_mlp *m) {
     return m->fuse12 && !m->ens && fused12_supported(m->L[0].kx, m->L[0].out, m->L[1].out);
 }
+// the same for layers 3 and 4 (the last hidden layer and the output layer)
+bool fused34_on(const chem_mlp *m) {
+    return m->fuse34 && !m->ens && fused34_supported(m->L[2].kx, m->L[2].out, m->L[3].out);
+}
 
 // prologue + the first nlayers layers on cells [0, n) of the given SoA pointers; with all four,
 // the normalised outputs are in m->out. prec CHEM_PREC_FP8 runs the hidden-to-hidden layers on
@@ -900,7 +905,9 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
         ldx = L1.out;
         l0 = 2;
     }
-    for (int l = l0; l < 3 && l < nlayers; ++l) {
+    // layers 3 and 4 in one launch: h3 stays on chip, the outputs are written
+    const bool f34 = prec == CHEM_PREC_BF16 && nlayers == kLayers && fused34_on(m);
+    for (int l = l0; l < (f34 ? 2 : 3) && l < nlayers; ++l) {
         const Layer &L = m->L[l];
         if (prec == CHEM_PREC_FP8) {
             const bool f8in = fp8_layer(l), f8out = fp8_layer(l + 1);
@@ -919,6 +926,11 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
         x = m->h[l];
     }
     if (nlayers < kLayers) return CHEM_OK;
+    if (f34) {
+        const Layer &L3 = m->L[2], &L4 = m->L[3];
+        return gemm_fused34(x, ldx, L3.kx, L3.Wb, L3.kx, L4.Wb, L4.kx, (int)n, L3.out, L4.out, L3.b, L4.b, m->out,
+                            m->n_out_pad, m->err, st);
+    }
     const Layer &L = m->L[3];
     return gemm_linear(L.tile, x, ldx, L.Wb, L.kx, (int)n, L.out, L.kx, L.b, m->out, m->n_out_pad, m->err, st);
 }
@@ -995,6 +1007,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     m->seed = seed;
     m->wait_limit = tc::kSpinLimit;
     m->fuse12 = 1;
+    m->fuse34 = 1;
     m->widths[0] = m->n_in;
     for (int i = 0; i < 3; ++i) m->widths[1 + i] = desc->n_hidden[i];
     m->widths[4] = m->n_out;
@@ -1727,15 +1740,17 @@ extern "C" int chem_mlp_fit_physics_scales(chem_mlp *m, int64_t n, int64_t ld, c
     return CHEM_OK;
 }
 
-extern "C" int chem_mlp_set_fusion(chem_mlp *m, int on) {
-    if (!m || (on != 0 && on != 1)) return set_error(CHEM_EINVAL, "chem_mlp_set_fusion: null handle or on not 0/1");
-    m->fuse12 = on;
+extern "C" int chem_mlp_set_fusion(chem_mlp *m, int mask) {
+    if (!m || mask < 0 || mask > 3)
+        return set_error(CHEM_EINVAL, "chem_mlp_set_fusion: null handle or mask outside 0..3");
+    m->fuse12 = (mask & CHEM_FUSE_12) ? 1 : 0;
+    m->fuse34 = (mask & CHEM_FUSE_34) ? 1 : 0;
     return CHEM_OK;
 }
 
 extern "C" int chem_mlp_get_fusion(const chem_mlp *m) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_fusion: null handle");
-    return fused12_on(m) ? 1 : 0;
+    return (fused12_on(m) ? CHEM_FUSE_12 : 0) | (fused34_on(m) ? CHEM_FUSE_34 : 0);
 }
 
 extern "C" int chem_mlp_set_wait_limit(chem_mlp *m, uint32_t tries) {
@@ -1977,6 +1992,23 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
             if (rep > 0) ms_sum += ms;
         }
         if (!rc) m->fuse12 = ms_sum < best_ms[0] + best_ms[1] ? 1 : 0;
+    }
+    // layers 3 and 4 fused into one launch, against the best two-launch pair
+    if (!rc && !m->ens && fused34_supported(m->L[2].kx, m->L[2].out, m->L[3].out)) {
+        const Layer &L3 = m->L[2], &L4 = m->L[3];
+        float ms_sum = 0.0f;
+        for (int rep = 0; rep < 4 && !rc; ++rep) {
+            rc = check_cuda(cudaEventRecord(e0, st), "autotune record");
+            if (!rc)
+                rc = gemm_fused34(m->h[1], m->L[1].out, L3.kx, L3.Wb, L3.kx, L4.Wb, L4.kx, (int)rows, L3.out, L4.out,
+                                  L3.b, L4.b, m->out, m->n_out_pad, m->err, st);
+            if (!rc) rc = check_cuda(cudaEventRecord(e1, st), "autotune record");
+            if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "autotune sync");
+            float ms = 0.0f;
+            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_sum += ms;
+        }
+        if (!rc) m->fuse34 = ms_sum < best_ms[2] + best_ms[3] ? 1 : 0;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

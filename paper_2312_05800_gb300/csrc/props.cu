@@ -6,12 +6,14 @@
 // warp's loads of T, p and each Y_k row are 128-byte coalesced. The per-pair
 // tables (Wilke weights, binary-resistance fits) are read with uniform
 // addresses (one broadcast per warp) through the read-only cache. The
-// per-cell vectors X_j, X_j / r_j and X_j / r_j^2 (r = sqrt(mu)) live in
-// registers: the inner species loop is unrolled to a compile-time bound NMAX.
+// per-cell vectors X_j and 1 / r_j (r = sqrt(mu)) live in registers: the inner
+// species loop is unrolled to a compile-time bound NMAX.
 //
 // Wilke: sum_j X_j Phi_kj with Phi_kj = c_kj (1 + w_jk r_k / r_j)^2 is
-// evaluated as T0.X + r_k (T1.(X/r) + r_k T2.(X/r^2)) with constant tables
-// T0 = c, T1 = 2 c w, T2 = c w^2 (expanded once at load time).
+// evaluated per pair as T0 + t (T1 + t T2), t = r_k / r_j, with constant tables
+// T0 = c, T1 = 2 c w, T2 = c w^2 (expanded once at load time): one multiply
+// more per pair than three separate sums, for a third fewer registers (which
+// bound the kernel's occupancy).
 #include <cmath>
 
 #include "internal.cuh"
@@ -80,7 +82,7 @@ __device__ __forceinline__ real to_real(in_t x) {
 }
 
 template <typename real, typename in_t, int NMAX>
-__global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, PropTables<real> tb, int64_t ncells,
+__global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) props_kernel(int N, int Np, real T_mid, PropTables<real> tb, int64_t ncells,
                                                     int64_t ld, const in_t *__restrict__ Tg,
                                                     const in_t *__restrict__ pg, const in_t *__restrict__ Yg,
                                                     real *__restrict__ cpg, real *__restrict__ hg,
@@ -107,7 +109,7 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
         const int rng = (T >= T_mid) ? 1 : 0;
         const real x = log(T) - real(6.907755278982137);   // ln(T / 1000)
         real S = 0, cpm = 0, hm = 0;
-        real X[NMAX], xr[NMAX], xr2[NMAX];
+        real X[NMAX], ir[NMAX];
         // pass 1: thermo sums; keep Y_k / W_k
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
@@ -149,13 +151,10 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
                 lm = fma(lm, x, c[2]);
                 lm = fma(lm, x, c[1]);
                 lm = fma(lm, x, c[0]);
-                const real ir = exp(real(-0.5) * lm);              // 1 / sqrt(mu_k)
+                ir[k] = exp(real(-0.5) * lm);                      // 1 / sqrt(mu_k)
                 X[k] = X[k] * Wbar;
-                xr[k] = X[k] * ir;
-                xr2[k] = xr[k] * ir;
             } else {
-                xr[k] = 0;
-                xr2[k] = 0;
+                ir[k] = 0;
             }
         }
         const real T15 = T * sqrt(T);
@@ -191,7 +190,7 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
             const real *d2 = dif + (2 * N + k) * Np;
             const real *d3 = dif + (3 * N + k) * Np;
             const real *d4 = dif + (4 * N + k) * Np;
-            real a0 = 0, a1 = 0, a2 = 0, ds = 0, gs = 0;
+            real a0 = 0, ds = 0, gs = 0;
 #pragma unroll
             for (int j4 = 0; j4 < NMAX; j4 += 4) {
                 if (j4 < N) {
@@ -218,16 +217,16 @@ __global__ void __launch_bounds__(128) props_kernel(int N, int Np, real T_mid, P
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int j = j4 + u;   // padded columns have zero weights
-                        a0 = fma(w0[u], X[j], a0);
-                        a1 = fma(w1[u], xr[j], a1);
-                        a2 = fma(w2[u], xr2[j], a2);
+                        // Phi_kj = T0 + t (T1 + t T2) with t = r_k / r_j
+                        const real t = ir[j] * rk;
+                        a0 = fma(fma(t, fma(t, w2[u], w1[u]), w0[u]), X[j], a0);
                         real g = fma(fma(fma(fma(g4[u], x, g3[u]), x, g2[u]), x, g1[u]), x, g0[u]);
                         ds = fma(g, X[j], ds);
                         gs += g;
                     }
                 }
             }
-            const real den = fma(rk, fma(rk, a2, a1), a0);
+            const real den = a0;
             mu = fma(Xk, muk / den, mu);
             lam = fma(Xk, lamk / den, lam);
             if (Dkg) {

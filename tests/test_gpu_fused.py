@@ -1,11 +1,14 @@
-"""The fused first two layers (h1 made on chip and consumed as layer 2's operand,
-gemm_fused.cuh) against the two-launch path and the oracle.
+"""The fused layer pairs (gemm_fused.cuh: layers 1 and 2 with h1 made on chip and
+consumed as layer 2's operand; gemm_fused34.cuh: layers 3 and 4 with h3 made on
+chip and multiplied by the output weights) against the separate launches and
+the oracle.
 
-* Bitwise: every output of chem_mlp_forward with fusion on equals the output
-  with fusion off (the same BF16 roundings and k order per element), at the
-  paper's widths (two passes of 400 columns), a one-pass network, a ragged last
-  pass (h2 = 560: the second pass covers 160 columns) and a ragged row count
-  over several chunks.
+* Bitwise: every output of chem_mlp_forward with both fusions equals the
+  output with either one or none (the same BF16 roundings and k order per
+  element), at the paper's widths (two passes of 400 columns), a one-pass
+  first pair, a ragged last pass (h2 = 560: the second pass covers 160
+  columns), a last hidden layer the output fusion does not take (64 units) and
+  a ragged row count over several chunks.
 * chem_step_ann with fusion on matches the oracle as in test_gpu_mlp.py (the
   default path of the learned step).
 Weights, statistics and states come from the seeded generator, never from the GPU.
@@ -53,15 +56,18 @@ def _u(net, T, p, Y, n):
 @pytest.mark.parametrize("n,hidden,chunk", [(3001, (1600, 800, 400), 2048), (20000, (1600, 800, 400), 8192),
                                             (1000, (640, 256, 64), 4096), (2600, (1600, 560, 400), 1024)])
 def test_fused_layers_are_bitwise_the_two_launches(n, hidden, chunk):
+    from paper_2312_05800_gb300 import binding
     mech, T, p, Y, widths, layers, stats = _problem(n, hidden, 2071)
     net = _net(widths, layers, stats, chunk=chunk)
-    assert net.fused
+    expect = binding.CHEM_FUSE_12 | (binding.CHEM_FUSE_34 if hidden[2] == 400 else 0)
+    assert net.fusion == expect
     uf = _u(net, T, p, Y, n)
-    net.set_fusion(False)
-    assert not net.fused
-    u2 = _u(net, T, p, Y, n)
     k = widths[4]
-    assert np.array_equal(uf[:, :k], u2[:, :k]), np.argwhere(uf[:, :k] != u2[:, :k])[:5]
+    for mask in (0, binding.CHEM_FUSE_12, binding.CHEM_FUSE_34):
+        net.set_fusion(mask)
+        assert net.fusion == mask & expect
+        u2 = _u(net, T, p, Y, n)
+        assert np.array_equal(uf[:, :k], u2[:, :k]), (mask, np.argwhere(uf[:, :k] != u2[:, :k])[:5])
     # and against the oracle with the device's BF16 rounding points
     uq = A.forward_u(mech, layers, stats, T[:n], p[:n], Y[:, :n], round_bf16=True)
     rms = np.sqrt(np.mean(uq ** 2))
