@@ -527,14 +527,27 @@ __global__ void loss_reduce_kernel(int64_t B, const float *__restrict__ part, fl
     if (threadIdx.x == 0) *loss = sh[0] / (float)B;
 }
 
-// Column sums of a BF16 [B][ld] matrix (bias gradients), rows in order.
-__global__ void colsum_kernel(int64_t B, int ncol, const __nv_bfloat16 *__restrict__ g, int ldg,
-                              float *__restrict__ out) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= ncol) return;
+// Column sums of a BF16 [B][ld] matrix (bias gradients) in a fixed order: block (32 columns x
+// kColsumRows row groups); thread (x, y) sums rows y, y + kColsumRows, ... of its column, then
+// thread y = 0 adds the groups' partial sums in ascending y. Deterministic, and every thread has
+// many independent loads in flight.
+constexpr int kColsumRows = 16;
+__global__ void __launch_bounds__(32 * kColsumRows) colsum_kernel(int64_t B, int ncol, const __nv_bfloat16 *__restrict__ g,
+                                                                  int ldg, float *__restrict__ out) {
+    __shared__ float part[kColsumRows][33];
+    const int j = blockIdx.x * 32 + threadIdx.x;
     float s = 0.0f;
-    for (int64_t i = 0; i < B; ++i) s += __bfloat162float(g[i * ldg + j]);
-    out[j] = s;
+    if (j < ncol) {
+#pragma unroll 8
+        for (int64_t i = threadIdx.y; i < B; i += kColsumRows) s += __bfloat162float(g[i * ldg + j]);
+    }
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < ncol) {
+        float t = 0.0f;
+        for (int y = 0; y < kColsumRows; ++y) t += part[y][threadIdx.x];
+        out[j] = t;
+    }
 }
 
 // out[c][r] = in[r][c] for a BF16 [rows][cols] matrix (row strides ldi, ldo), 32x32 tiles.
@@ -737,16 +750,29 @@ __global__ void group_dot_back_kernel(int64_t rows, int G, int K, const __nv_bfl
 }
 
 // weight gradient of the output units: gW[g][k] = sum_i dout[i][g] h[i][g K + k], rows in order
-__global__ void group_dot_wgrad_kernel(int64_t rows, int G, int K, const __nv_bfloat16 *__restrict__ dout, int lddo,
-                                       const __nv_bfloat16 *__restrict__ h, int64_t ldh, float *__restrict__ gW,
-                                       int ldgw) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= G * K) return;
-    const int g = c / K, k = c - g * K;
+__global__ void __launch_bounds__(32 * kColsumRows) group_dot_wgrad_kernel(int64_t rows, int G, int K,
+                                                                           const __nv_bfloat16 *__restrict__ dout,
+                                                                           int lddo, const __nv_bfloat16 *__restrict__ h,
+                                                                           int64_t ldh, float *__restrict__ gW, int ldgw) {
+    // rows split over kColsumRows groups (thread y sums rows y, y + kColsumRows, ...), partial sums
+    // added in ascending y: a fixed order
+    __shared__ float part[kColsumRows][33];
+    const int c = blockIdx.x * 32 + threadIdx.x;
     float s = 0.0f;
-    for (int64_t i = 0; i < rows; ++i)
-        s = fmaf(__bfloat162float(dout[i * lddo + g]), __bfloat162float(h[i * ldh + c]), s);
-    gW[(int64_t)g * ldgw + k] = s;
+    if (c < G * K) {
+        const int g = c / K;
+#pragma unroll 8
+        for (int64_t i = threadIdx.y; i < rows; i += kColsumRows)
+            s = fmaf(__bfloat162float(dout[i * lddo + g]), __bfloat162float(h[i * ldh + c]), s);
+    }
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && c < G * K) {
+        float t = 0.0f;
+        for (int y = 0; y < kColsumRows; ++y) t += part[y][threadIdx.x];
+        const int g = c / K, k = c - g * K;
+        gW[(int64_t)g * ldgw + k] = t;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1573,9 +1599,9 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
     {
         const Layer &L = m->L[3];
         const int64_t ldh = (int64_t)G * L.in;
-        group_dot_wgrad_kernel<<<(G * L.in + 127) / 128, 128, 0, st>>>(B, G, L.in, m->tdout, m->n_out_pad, m->th[2],
+        group_dot_wgrad_kernel<<<(G * L.in + 31) / 32, dim3(32, kColsumRows), 0, st>>>(B, G, L.in, m->tdout, m->n_out_pad, m->th[2],
                                                                         ldh, L.gW, L.kin);
-        colsum_kernel<<<(G + 127) / 128, 128, 0, st>>>(B, G, m->tdout, m->n_out_pad, L.gb);
+        colsum_kernel<<<(G + 31) / 32, dim3(32, kColsumRows), 0, st>>>(B, G, m->tdout, m->n_out_pad, L.gb);
         const int64_t ne = (int64_t)B * ldh;
         group_dot_back_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(B, G, L.in, m->tdout, m->n_out_pad, L.Wb,
                                                                             L.kx, m->tz[2], ldh, m->tdz[2], ldh);
@@ -1595,7 +1621,7 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
                                  GemmOperand{m->tT1, B, kMapRowGrp, (int64_t)L.in * B}, G, L.gout, L.in, B, nullptr, 0,
                                  L.gW, L.kin, (int64_t)L.gout * L.kin, m->err, st);
         if (rc) return rc;
-        colsum_kernel<<<(unsigned)((ldz + 127) / 128), 128, 0, st>>>(B, (int)ldz, m->tdz[l], (int)ldz, L.gb);
+        colsum_kernel<<<(unsigned)((ldz + 31) / 32), dim3(32, kColsumRows), 0, st>>>(B, (int)ldz, m->tdz[l], (int)ldz, L.gb);
         if ((rc = check_cuda(cudaGetLastError(), "ensemble bias grad"))) return rc;
         rc = gemm_gelu_grad_grouped(default_tile_width(L.in), GemmOperand{m->tdz[l], ldz, kMapColGrp, L.gout},
                                     GemmOperand{L.Wt, L.outp, kMapColGrp, L.gout}, G, B, L.in, L.gout, m->tz[l - 1],
@@ -1610,7 +1636,7 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
     rc = gemm_linear(default_tile_width(L0.kin), m->tT0, B, m->tT1, B, L0.out, L0.kin, B, nullptr, L0.gW, L0.kin,
                      m->err, st);
     if (rc) return rc;
-    colsum_kernel<<<(L0.out + 127) / 128, 128, 0, st>>>(B, L0.out, m->tdz[0], L0.out, L0.gb);
+    colsum_kernel<<<(L0.out + 31) / 32, dim3(32, kColsumRows), 0, st>>>(B, L0.out, m->tdz[0], L0.out, L0.gb);
     return check_cuda(cudaGetLastError(), "ensemble bias grad");
 }
 
@@ -1675,7 +1701,7 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
             rc = gemm_linear(default_tile_width(L.kin), m->tT0, B, m->tT1, B, L.out, L.kin, B, nullptr, L.gW, L.kin, m->err,
                              st);
             if (rc) return rc;
-            colsum_kernel<<<(L.out + 127) / 128, 128, 0, st>>>(B, L.out, dz, lddz, L.gb);
+            colsum_kernel<<<(L.out + 31) / 32, dim3(32, kColsumRows), 0, st>>>(B, L.out, dz, lddz, L.gb);
             if ((rc = check_cuda(cudaGetLastError(), "train bias grad"))) return rc;
             if (l > 0) {
                 const Layer &Lb = m->L[l - 1];

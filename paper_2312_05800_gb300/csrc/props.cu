@@ -242,18 +242,19 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) 
 }
 
 // Thermo only (cp and h; the memory-bound part of props_eval), FP32 arithmetic.
-// One thread per cell in a grid-stride loop. Every species row of the cell is
-// loaded before any arithmetic (the species loop unrolled to the compile-time
-// bound NMAX), so a thread has up to NMAX independent loads in flight: enough
-// bytes in flight to keep HBM busy at modest occupancy. The NASA-7 rows of both
+// Two threads per cell (adjacent lanes), each loading half of the cell's species
+// rows before any arithmetic (the species loop unrolled to the compile-time bound
+// NMAX / 2), so each thread keeps few registers and many independent loads in
+// flight; the two halves' sums meet by a lane shuffle. The NASA-7 rows of both
 // ranges and 1/W are staged in shared memory (3 float4 per species and range).
-// The arithmetic is that of props_kernel's first pass, so cp and h are bitwise
-// the same.
+// The arithmetic per species is that of props_kernel's first pass; the sums run
+// in a different order, so cp and h agree with it to FP32 rounding.
 template <typename in_t, int NMAX>
 __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTables<float> tb, int64_t ncells,
                                                      int64_t ld, const in_t *__restrict__ Tg,
                                                      const in_t *__restrict__ Yg, float *__restrict__ cpg,
                                                      float *__restrict__ hg) {
+    constexpr int H = NMAX / 2;
     extern __shared__ float4 th_tab[];
     for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
         const int rg = e / N, k = e % N;
@@ -265,18 +266,25 @@ __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTab
     }
     __syncthreads();
     const float R = float(kR);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncells; i += stride) {
-        in_t yr[NMAX];
+    const int half = threadIdx.x & 1;
+    const int k0 = half * H;
+    const int64_t stride = (int64_t)gridDim.x * (blockDim.x / 2);
+    // every lane pair runs the same number of iterations (the shuffle below needs both lanes)
+    for (int64_t i0 = (int64_t)blockIdx.x * (blockDim.x / 2); i0 < ncells; i0 += stride) {
+        const int64_t i = i0 + (threadIdx.x >> 1);
+        const bool live = i < ncells;
+        in_t yr[H];
 #pragma unroll
-        for (int k = 0; k < NMAX; ++k) yr[k] = (k < N) ? __ldcs(Yg + (int64_t)k * ld + i) : in_t(0);
-        const float T = to_real<float>(__ldcs(Tg + i));
+        for (int q = 0; q < H; ++q)
+            yr[q] = (live && k0 + q < N) ? __ldcs(Yg + (int64_t)(k0 + q) * ld + i) : in_t(0);
+        const float T = live ? to_real<float>(__ldcs(Tg + i)) : 300.0f;
         const float4 *tab = th_tab + ((T >= T_mid) ? 3 * N : 0);
         float cpm = 0.0f, hm = 0.0f;
 #pragma unroll
-        for (int k = 0; k < NMAX; ++k) {
+        for (int q = 0; q < H; ++q) {
+            const int k = k0 + q;
             if (k < N) {
-                const float y = to_real<float>(yr[k]);
+                const float y = to_real<float>(yr[q]);
                 const float4 q0 = tab[3 * k], q1 = tab[3 * k + 1], q2 = tab[3 * k + 2];
                 float cpR = q1.x;
                 cpR = fmaf(cpR, T, q0.w);
@@ -294,8 +302,12 @@ __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTab
                 hm = fmaf(yw, hR, hm);
             }
         }
-        if (cpg) __stcs(cpg + i, cpm * R);
-        if (hg) __stcs(hg + i, hm * R * T);
+        cpm += __shfl_xor_sync(0xffffffffu, cpm, 1);
+        hm += __shfl_xor_sync(0xffffffffu, hm, 1);
+        if (live && half == 0) {
+            if (cpg) __stcs(cpg + i, cpm * R);
+            if (hg) __stcs(hg + i, hm * R * T);
+        }
     }
 }
 
@@ -308,7 +320,7 @@ int launch_thermo_n(const chem_mech *m, int64_t ncells, int64_t ld, const void *
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_kernel<in_t, NMAX>, 256, smem);
     const int64_t max_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (ncells + 255) / 256;
+    const int64_t need = (ncells + 127) / 128;                // two threads per cell
     const int blocks = (int)(need < max_blocks ? need : max_blocks);
     void *pb = prof_begin(st);
     thermo_kernel<in_t, NMAX><<<blocks, 256, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,

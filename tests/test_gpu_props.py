@@ -104,8 +104,10 @@ def test_full_size_sampled(oracle):
 
 @pytest.mark.parametrize("name,n", [("c2", 65531), ("c5", 8189)])
 def test_thermo_only_pass(oracle, name, n):
-    # without transport outputs props_eval runs the thermo-only kernel: cp and h bitwise equal to
-    # the full pass's (same FP32 arithmetic), from FP32 and from FP64 state; cells past n untouched
+    # without transport outputs props_eval runs the thermo-only kernel: the same FP32 arithmetic per
+    # species as the full pass, summed by two threads per cell (a different order), so cp and h agree
+    # with the full pass's to FP32 rounding of the sums; from FP32 and from FP64 state; cells past n
+    # untouched
     import torch
     from paper_2312_05800_gb300 import binding
     m = synth.get_mech(name)
@@ -119,5 +121,6 @@ def test_thermo_only_pass(oracle, name, n):
         binding.props_eval(dev_mech(name), n, ld, dtype, Td, pd, Yd, cp, h, None, None, None)
         torch.cuda.synchronize()
         cp, h = cp.double().cpu().numpy(), h.double().cpu().numpy()
-        assert np.array_equal(cp[:n], full[0][:n]) and np.array_equal(h[:n], full[1][:n])
+        assert np.all(np.abs(cp[:n] - full[0][:n]) <= 2e-6 * np.abs(full[0][:n]))
+        assert np.all(np.abs(h[:n] - full[1][:n]) <= 2e-6 * np.abs(full[1][:n]) + 1e-6 * np.abs(full[1][:n]).max())
         assert np.all(np.isnan(cp[n:])) and np.all(np.isnan(h[n:]))
