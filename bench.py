@@ -407,6 +407,14 @@ def gemm_traffic(chunk: int, ncells: int):
     return None if t is None else t * ncells / 262144
 
 
+def fusion_text(mask: int) -> str:
+    """The layer launches that the autotuned fusion mask gives."""
+    from paper_2312_05800_gb300 import binding
+    a = "layers 1-2 fused" if mask & binding.CHEM_FUSE_12 else "layer 1, layer 2"
+    b = "layers 3-4 fused" if mask & binding.CHEM_FUSE_34 else "layer 3, layer 4"
+    return a + ", " + b
+
+
 def dominant_gemm(dom, ncells: int, chunk: int, widths, peak: float, steps: int):
     """The longest-running tensor-core kernel of the step: its share of the GEMM time and its own
     roofline fraction on its algorithmic flops per launch (the fused first two layers: 2 (K0 h1 +
@@ -847,8 +855,8 @@ def bench_ann(args, rank, world, local):
                          "traffic": gemm_traffic(args.chunk, ncells),
                          "traffic_unit": "DRAM bytes (read + write) of the network's tensor-core launches per step: "
                                          "ncu dram__bytes of one 262,144-cell chunk, scaled by the cells",
-                         "kernel": "every tensor-core launch of the network per step (layers 1-2 fused, layers 3 "
-                                   "and 4); CUDA events around each launch",
+                         "kernel": "every tensor-core launch of the network per step (%s); CUDA events around "
+                                   "each launch" % fusion_text(net.fusion),
                          "work": "%.4f MFLOP per cell: 2 sum fan_in x fan_out over %s (first layer K = N + 2, "
                                  "not the device's hi/lo K)" % (mflop_cell, "-".join(str(w) for w in widths)),
                          "peak_source": src,

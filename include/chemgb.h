@@ -116,6 +116,11 @@ int chem_mech_nreactions(const chem_mech *mech);
  * Dk ([N][ld]) (outputs); CHEM_F64_IN_F32 reads double inputs (the FP64
  * state the stepping calls update) and computes and writes in float. Any of the outputs may be NULL to skip it (mu,
  * lambda and Dk together select the transport part). ncells == 0 is a no-op.
+ * Every array is 16-byte aligned and ld a multiple of 4 (else CHEM_EINVAL):
+ * without transport outputs, in float arithmetic, the state is streamed by
+ * 16-byte bulk copies that may read up to 3 cells past ncells (inside ld). If
+ * one of those copies never lands (a bounded wait runs out), the affected
+ * cells' cp and h are NaN.
  */
 int props_eval(const chem_mech *mech, int64_t ncells, int64_t ld, int dtype,
                const void *T, const void *p, const void *Y,

@@ -61,10 +61,11 @@ struct DevMech {
     const int *rnu;         // [R][6] their net stoichiometric coefficients
     const int *tb_list;     // [n_tb] reactions with a third body, ascending
     double lnPR;            // ln(P_std / R)
-    unsigned int *counters; // [kNumCounters] work-queue counters (scratch)
+    unsigned int *counters; // [kNumCounters] work-queue counters (scratch) and error words
 };
 
 constexpr int kNumCounters = 8;
+constexpr int kPropsErrCounter = 7;       // props_eval's staged thermo pass: a copy wait ran out
 
 }  // namespace chemgb
 
@@ -91,17 +92,19 @@ inline bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 
 // also converts between FP32 and FP64) runs at 1/64 of the FP32 rate, so the
 // per-species conversions of the cell kernels are done on the integer pipe.
 // FP64 -> FP32 by truncating the mantissa (relative error < 2^-23); magnitudes
-// below 2^-126 become signed zero, above the FP32 range infinity; NaN stays NaN.
+// below 2^-126 become signed zero, at or above 2^128 infinity; NaN stays NaN.
+// For |x| in range the FP32 bits are the double's high word with the exponent
+// rebased (- (1023 - 127) << 20) and the 20 + 3 leading mantissa bits shifted
+// into place, one funnel shift of the two words.
 __device__ __forceinline__ float f64_to_f32_trunc(double x) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
-    const int eb = static_cast<int>((b >> 52) & 0x7FF);
-    const unsigned int mant = static_cast<unsigned int>(b >> 29) & 0x7FFFFFu;
-    if (eb == 0x7FF) return __uint_as_float(sign | 0x7F800000u | mant);
-    const int e = eb - 1023 + 127;
-    if (e <= 0) return __uint_as_float(sign);
-    if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
-    return __uint_as_float(sign | (static_cast<unsigned int>(e) << 23) | mant);
+    const unsigned int hi = static_cast<unsigned int>(__double2hiint(x));
+    const unsigned int lo = static_cast<unsigned int>(__double2loint(x));
+    const unsigned int a = hi & 0x7FFFFFFFu;
+    unsigned int r = __funnelshift_l(lo, a - 0x38000000u, 3);      // exponent - 896, mantissa 23 bits
+    r = (a < 0x38100000u) ? 0u : r;                                  // below 2^-126
+    if (a >= 0x47F00000u)                                            // 2^128 and above, infinity, NaN
+        r = (a > 0x7FF00000u || (a == 0x7FF00000u && lo != 0u)) ? 0x7FC00000u : 0x7F800000u;
+    return __uint_as_float(r | (hi & 0x80000000u));
 }
 // FP32 -> FP64, exact for normal numbers and zero; FP32 subnormals (below 2^-126)
 // become signed zero; infinities and NaN are kept.

@@ -17,6 +17,7 @@
 #include <cmath>
 
 #include "internal.cuh"
+#include "tc.cuh"
 
 namespace chemgb {
 namespace {
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) 
         const real T = to_real<real>(Tg[i]);
         const real p = to_real<real>(pg[i]);
         const int rng = (T >= T_mid) ? 1 : 0;
+        const real iT = real(1) / T;
         const real x = log(T) - real(6.907755278982137);   // ln(T / 1000)
         real S = 0, cpm = 0, hm = 0;
         real X[NMAX], ir[NMAX];
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) 
                 hR = fma(hR, T, b[2]);
                 hR = fma(hR, T, b[1]);
                 hR = fma(hR, T, b[0]);
-                hR = hR + b[5] / T;                              // H_k / (R T)
+                hR = fma(b[5], iT, hR);                          // H_k / (R T)
                 const real yw = y * iw;
                 S += yw;
                 cpm = fma(yw, cpR, cpm);
@@ -241,51 +243,129 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) 
     }
 }
 
-// Thermo only (cp and h; the memory-bound part of props_eval), FP32 arithmetic.
-// Two threads per cell (adjacent lanes), each loading half of the cell's species
-// rows before any arithmetic (the species loop unrolled to the compile-time bound
-// NMAX / 2), so each thread keeps few registers and many independent loads in
-// flight; the two halves' sums meet by a lane shuffle. The NASA-7 rows of both
-// ranges and 1/W are staged in shared memory (3 float4 per species and range).
-// The arithmetic per species is that of props_kernel's first pass; the sums run
-// in a different order, so cp and h agree with it to FP32 rounding.
-template <typename in_t, int NMAX>
-__global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTables<float> tb, int64_t ncells,
-                                                     int64_t ld, const in_t *__restrict__ Tg,
-                                                     const in_t *__restrict__ Yg, float *__restrict__ cpg,
-                                                     float *__restrict__ hg) {
-    constexpr int H = NMAX / 2;
-    extern __shared__ float4 th_tab[];
+// Thermo only (cp and h; the memory-bound part of props_eval), FP32 arithmetic,
+// with the state staged through shared memory by bulk copies.
+//
+// A CTA (one per SM) takes tiles of kThTile consecutive cells. The tile's state
+// rows (T, then Y_0 .. Y_{N-1}) arrive in groups of kThRows rows, one 1-D bulk
+// copy (cp.async.bulk) per row segment, into a ring of stages: a producer warp
+// keeps up to kStages groups in flight (about 190 KB per SM for FP64 state, far
+// more bytes than the HBM latency needs), while kThTile consumer threads, one
+// per cell, read their column of each landed group, accumulate cp and h and
+// release the stage. Row segments are read once and in whole 16-byte units: a
+// tile's last segment is rounded up to 4 cells, which stays inside ld (a
+// multiple of 4). The NASA-7 rows of both ranges and 1/W sit in shared memory (3
+// float4 per species and range). The arithmetic and the species order per cell
+// are those of props_kernel's first pass, so cp and h are bitwise the full
+// pass's. A copy wait that runs out (bounded, spin tries) records
+// kPropsErrCounter, writes NaN to the tile's cp and h and stops the CTA after
+// its issued copies have landed.
+constexpr int kThTile = 512;                  // cells per tile = consumer threads
+constexpr int kThRows = 8;                    // state rows per stage
+constexpr int kThThreads = kThTile + 32;      // + the producer warp
+
+template <typename in_t>
+struct ThLayout {
+    static constexpr int kStages = sizeof(in_t) == 8 ? 6 : 8;
+    static constexpr uint32_t kRowBytes = kThTile * sizeof(in_t);
+    static constexpr uint32_t kStage = kThRows * kRowBytes;
+    static constexpr uint32_t kStageTotal = kStages * kStage;
+    static size_t bytes(int N) { return kStageTotal + (size_t)6 * N * sizeof(float4) + 2 * kStages * 8; }
+};
+
+template <typename in_t>
+__global__ void __launch_bounds__(kThThreads, 1)
+    thermo_kernel(int N, float T_mid, PropTables<float> tb, int64_t ncells, int64_t ld,
+                  const in_t *__restrict__ Tg, const in_t *__restrict__ Yg, float *__restrict__ cpg,
+                  float *__restrict__ hg, unsigned int *err, uint32_t spin) {
+    using L = ThLayout<in_t>;
+    constexpr int S = L::kStages;
+    extern __shared__ __align__(128) uint8_t th_smem[];
+    uint8_t *stages = th_smem;
+    float4 *tab = reinterpret_cast<float4 *>(th_smem + L::kStageTotal);
+    uint64_t *full = reinterpret_cast<uint64_t *>(tab + 6 * N);
+    uint64_t *empty = full + S;
     for (int e = threadIdx.x; e < 2 * N; e += blockDim.x) {
         const int rg = e / N, k = e % N;
         const float *a = tb.nasa_cp + (rg * N + k) * 5;
         const float *b = tb.nasa_h + (rg * N + k) * 6;
-        th_tab[e * 3 + 0] = make_float4(a[0], a[1], a[2], a[3]);
-        th_tab[e * 3 + 1] = make_float4(a[4], b[0], b[1], b[2]);
-        th_tab[e * 3 + 2] = make_float4(b[3], b[4], b[5], tb.invW[k]);
+        tab[e * 3 + 0] = make_float4(a[0], a[1], a[2], a[3]);
+        tab[e * 3 + 1] = make_float4(a[4], b[0], b[1], b[2]);
+        tab[e * 3 + 2] = make_float4(b[3], b[4], b[5], tb.invW[k]);
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], kThTile / 32);
+        }
+        tc::fence_barrier_init();
     }
     __syncthreads();
+    const int64_t ntiles = (ncells + kThTile - 1) / kThTile;
+    const int groups = (N + 1 + kThRows - 1) / kThRows;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == kThTile / 32) {
+        if (lane == 0) {
+            int u = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int64_t c0 = t * kThTile;
+                const int64_t cells = ncells - c0 < kThTile ? ncells - c0 : kThTile;
+                const uint32_t bytes = (uint32_t)(((cells + 3) & ~int64_t(3)) * sizeof(in_t));
+                for (int g = 0; g < groups; ++g, ++u) {
+                    const int s = u % S;
+                    if (!tc::mbar_wait(&empty[s], (uint32_t)((u / S) & 1) ^ 1u, spin)) {
+                        atomicExch(err, 1u);
+                        ok = false;
+                        break;
+                    }
+                    const int r0 = g * kThRows, rows = (N + 1 - r0) < kThRows ? N + 1 - r0 : kThRows;
+                    tc::mbar_arrive_expect_tx(&full[s], rows * bytes);
+                    for (int r = 0; r < rows; ++r) {
+                        const int q = r0 + r;          // state row: 0 = T, q = Y_{q-1}
+                        const in_t *src = (q == 0 ? Tg : Yg + (int64_t)(q - 1) * ld) + c0;
+                        tc::bulk_load_1d(stages + s * L::kStage + r * L::kRowBytes, src, bytes, &full[s]);
+                    }
+                }
+            }
+            // the last fill of each stage lands before the CTA may exit (full limit); u counts the
+            // groups whose copies were issued
+            for (int j = (u > S ? u - S : 0); j < u; ++j)
+                if (!tc::mbar_wait(&full[j % S], (uint32_t)(j / S) & 1u)) {
+                    atomicExch(err, 1u);
+                    break;
+                }
+        }
+        return;
+    }
     const float R = float(kR);
-    const int half = threadIdx.x & 1;
-    const int k0 = half * H;
-    const int64_t stride = (int64_t)gridDim.x * (blockDim.x / 2);
-    // every lane pair runs the same number of iterations (the shuffle below needs both lanes)
-    for (int64_t i0 = (int64_t)blockIdx.x * (blockDim.x / 2); i0 < ncells; i0 += stride) {
-        const int64_t i = i0 + (threadIdx.x >> 1);
-        const bool live = i < ncells;
-        in_t yr[H];
+    int u = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int64_t i = t * kThTile + threadIdx.x;
+        float T = 300.0f, iT = 1.0f / 300.0f, cpm = 0.0f, hm = 0.0f;
+        const float4 *tr = tab;
+        bool ok = true;
+        for (int g = 0; g < groups; ++g, ++u) {
+            const int s = u % S;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (uint32_t)(u / S) & 1u, spin))) {
+                ok = false;
+                break;
+            }
+            const in_t *col = reinterpret_cast<const in_t *>(stages + s * L::kStage) + threadIdx.x;
+            const int r0 = g * kThRows;
 #pragma unroll
-        for (int q = 0; q < H; ++q)
-            yr[q] = (live && k0 + q < N) ? __ldcs(Yg + (int64_t)(k0 + q) * ld + i) : in_t(0);
-        const float T = live ? to_real<float>(__ldcs(Tg + i)) : 300.0f;
-        const float4 *tab = th_tab + ((T >= T_mid) ? 3 * N : 0);
-        float cpm = 0.0f, hm = 0.0f;
-#pragma unroll
-        for (int q = 0; q < H; ++q) {
-            const int k = k0 + q;
-            if (k < N) {
-                const float y = to_real<float>(yr[q]);
-                const float4 q0 = tab[3 * k], q1 = tab[3 * k + 1], q2 = tab[3 * k + 2];
+            for (int r = 0; r < kThRows; ++r) {
+                const int q = r0 + r;
+                if (q > N) break;
+                const float v = to_real<float>(col[r * kThTile]);
+                if (q == 0) {
+                    T = v;
+                    iT = 1.0f / T;
+                    tr = tab + ((T >= T_mid) ? 3 * N : 0);
+                    continue;
+                }
+                const int k = q - 1;
+                const float4 q0 = tr[3 * k], q1 = tr[3 * k + 1], q2 = tr[3 * k + 2];
                 float cpR = q1.x;
                 cpR = fmaf(cpR, T, q0.w);
                 cpR = fmaf(cpR, T, q0.z);
@@ -296,47 +376,57 @@ __global__ void __launch_bounds__(256) thermo_kernel(int N, float T_mid, PropTab
                 hR = fmaf(hR, T, q1.w);
                 hR = fmaf(hR, T, q1.z);
                 hR = fmaf(hR, T, q1.y);
-                hR = hR + q2.z / T;
-                const float yw = y * q2.w;
+                hR = fmaf(q2.z, iT, hR);
+                const float yw = v * q2.w;
                 cpm = fmaf(yw, cpR, cpm);
                 hm = fmaf(yw, hR, hm);
             }
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&empty[s]);
         }
-        cpm += __shfl_xor_sync(0xffffffffu, cpm, 1);
-        hm += __shfl_xor_sync(0xffffffffu, hm, 1);
-        if (live && half == 0) {
+        if (!ok) {
+            if (lane == 0) atomicExch(err, 1u);
+            if (i < ncells) {
+                if (cpg) cpg[i] = __int_as_float(0x7fc00000);
+                if (hg) hg[i] = __int_as_float(0x7fc00000);
+            }
+            break;
+        }
+        if (i < ncells) {
             if (cpg) __stcs(cpg + i, cpm * R);
             if (hg) __stcs(hg + i, hm * R * T);
         }
     }
 }
 
-template <typename in_t, int NMAX>
-int launch_thermo_n(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *Y, void *cp, void *h,
-                    cudaStream_t st) {
-    const size_t smem = (size_t)6 * m->N * sizeof(float4);
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, thermo_kernel<in_t, NMAX>, 256, smem);
-    const int64_t max_blocks = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-    const int64_t need = (ncells + 127) / 128;                // two threads per cell
-    const int blocks = (int)(need < max_blocks ? need : max_blocks);
-    void *pb = prof_begin(st);
-    thermo_kernel<in_t, NMAX><<<blocks, 256, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,
-                                                         static_cast<const in_t *>(T), static_cast<const in_t *>(Y),
-                                                         static_cast<float *>(cp), static_cast<float *>(h));
-    prof_end(pb, st, "thermo_kernel", (double)ncells * 24.0 * m->N,
-             (double)ncells * ((m->N + 1) * sizeof(in_t) + 2 * sizeof(float)));
-    return check_cuda(cudaGetLastError(), "props_eval (thermo) launch");
-}
-
 template <typename in_t>
 int launch_thermo(const chem_mech *m, int64_t ncells, int64_t ld, const void *T, const void *Y, void *cp, void *h,
                   cudaStream_t st) {
-    if (m->N <= 16) return launch_thermo_n<in_t, 16>(m, ncells, ld, T, Y, cp, h, st);
-    if (m->N <= 32) return launch_thermo_n<in_t, 32>(m, ncells, ld, T, Y, cp, h, st);
-    return launch_thermo_n<in_t, 64>(m, ncells, ld, T, Y, cp, h, st);
+    using L = ThLayout<in_t>;
+    if (!aligned16(T) || !aligned16(Y) || (ld & 3) != 0)
+        return set_error(CHEM_EINVAL, "props_eval: the state arrays must be 16-byte aligned and ld a multiple of 4");
+    const size_t smem = L::bytes(m->N);
+    static bool configured = false;
+    if (!configured) {
+        int rc = check_cuda(cudaFuncSetAttribute(thermo_kernel<in_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)L::bytes(kMaxSpecies)),
+                            "props_eval (thermo) smem attribute");
+        if (rc) return rc;
+        configured = true;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t ntiles = (ncells + kThTile - 1) / kThTile;
+    const int blocks = (int)(ntiles < sms ? ntiles : sms);
+    void *pb = prof_begin(st);
+    thermo_kernel<in_t><<<blocks, kThThreads, smem, st>>>(m->N, float(m->T_mid), m->dev.f32, ncells, ld,
+                                                          static_cast<const in_t *>(T), static_cast<const in_t *>(Y),
+                                                          static_cast<float *>(cp), static_cast<float *>(h),
+                                                          m->dev.counters + kPropsErrCounter, tc::kSpinLimit);
+    prof_end(pb, st, "thermo_kernel", (double)ncells * 24.0 * m->N,
+             (double)ncells * ((m->N + 1) * sizeof(in_t) + 2 * sizeof(float)));
+    return check_cuda(cudaGetLastError(), "props_eval (thermo) launch");
 }
 
 template <typename real, typename in_t, int NMAX>
