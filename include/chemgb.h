@@ -401,24 +401,16 @@ int chem_mlp_load(const chem_mech *mech, const char *path, chem_mlp **out);
  * Synchronises the stream; results are bitwise
  * the same for every tile width. */
 int chem_mlp_autotune(chem_mlp *mlp, int64_t rows, int32_t *tiles_out, chem_stream_t stream);
-/* Layer fusion of the BF16 forward (no counterpart in the paper). mask is a
- * set of CHEM_FUSE_* bits (default: both):
- *  - CHEM_FUSE_12: the multi-output network's first two hidden layers run as
- *    one tensor-core launch in which h1 is made on chip, 64 columns at a time,
- *    and consumed at once as layer 2's operand, so it never round-trips through
- *    memory. It applies when the first layer's K is 64 (the two BF16 terms of
- *    at most 32 inputs, i.e. at most 30 species), h1 is a multiple of 64 and h2
- *    a multiple of 16.
- *  - CHEM_FUSE_34: the last hidden layer and the output layer run as one
- *    launch in which h3 is made on chip and multiplied at once by the output
- *    weights. It applies to a last hidden layer of 400 units and at most 32
- *    outputs.
- * The results are bitwise those of the separate layers. Where a fusion does
- * not apply, and for E4M3, training and the per-species ensemble, the layers
- * run one by one. chem_mlp_autotune times each fused launch against its two
- * layers and keeps the faster. chem_mlp_get_fusion returns the mask of the
- * fusions the forward uses. */
-enum { CHEM_FUSE_12 = 1, CHEM_FUSE_34 = 2 };
+/* Layer fusion of the BF16 forward (no counterpart in the paper). mask is 0
+ * or CHEM_FUSE_34 (the default): the last hidden layer and the output layer
+ * run as one launch in which h3 is made on chip and multiplied at once by the
+ * output weights. It applies to a last hidden layer of 400 units and at most
+ * 32 outputs; the results are bitwise those of the two separate layers. Where
+ * it does not apply, and for E4M3, training and the per-species ensemble, the
+ * layers run one by one. chem_mlp_autotune times the fused launch against its
+ * two layers and keeps the faster. chem_mlp_get_fusion returns the mask the
+ * forward uses. */
+enum { CHEM_FUSE_34 = 2 };
 int chem_mlp_set_fusion(chem_mlp *mlp, int mask);
 int chem_mlp_get_fusion(const chem_mlp *mlp);
 /* Sticky error word of the network's pipeline waits (0 = none); synchronises the device.

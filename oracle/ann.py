@@ -9,7 +9,8 @@ prologue -> network -> epilogue, written out plainly:
   T' : h(T', Y') = h(T, Y)  (adiabatic, constant p), Newton to |dT| < 1e-10 K.
 round_bf16 rounds the operands at the points where the GPU stores BF16 (the
 weights and each hidden activation; the network input, formed in FP32, as the
-sum of two BF16 terms hi + lo); accumulation stays FP64.
+sum of two BF16 terms hi + lo, and the first layer's weights likewise, with the
+product taken as z_hi W_hi + z_lo W_hi + z_hi W_lo); accumulation stays FP64.
 """
 from __future__ import annotations
 
@@ -72,8 +73,13 @@ def calibrate_fp8(layers, z):
     """E4M3 activation scales s_i = fl32(max |h_i| / 448) of the BF16 forward's h1, h2."""
     h = split_bf16(z)
     s = []
-    for W, b in layers[:2]:
-        h = to_bf16(M.gelu(h @ to_bf16(W).T + b))
+    for i, (W, b) in enumerate(layers[:2]):
+        if i == 0:
+            Wh = to_bf16(W)
+            pre = h @ Wh.T + to_bf16(h) @ to_bf16(W - Wh).T + b
+        else:
+            pre = h @ to_bf16(W).T + b
+        h = to_bf16(M.gelu(pre))
         s.append(float(np.float32(np.abs(h).max() / E4M3_MAX)))
     return s
 
@@ -103,6 +109,9 @@ def network(layers, z, round_bf16=False, fp8_scales=None):
             Wq, sw = quantize_rows(W)
             cs = (sw * np.float64(np.float32(fp8_scales[i - 1]))).astype(np.float32).astype(np.float64)
             pre = (h @ Wq.T) * cs + b
+        elif i == 0 and (round_bf16 or fp8_scales is not None):
+            Wh = to_bf16(W)
+            pre = h @ Wh.T + to_bf16(h) @ to_bf16(W - Wh).T + b
         else:
             Wq = to_bf16(W) if (round_bf16 or fp8_scales is not None) else W
             pre = h @ Wq.T + b

@@ -49,7 +49,7 @@ class chem_hfrd_params(ctypes.Structure):
 
 
 CHEM_PREC_BF16, CHEM_PREC_FP8 = 0, 1
-CHEM_FUSE_12, CHEM_FUSE_34 = 1, 2
+CHEM_FUSE_34 = 2
 
 
 def library_path() -> str:
@@ -341,9 +341,9 @@ class Mlp:
         return sm.value, sq.value
 
     def set_fusion(self, mask):
-        """CHEM_FUSE_* bits (True: both fusions, False: none)."""
+        """0 or CHEM_FUSE_34 (True: CHEM_FUSE_34, False: none)."""
         if mask is True:
-            mask = CHEM_FUSE_12 | CHEM_FUSE_34
+            mask = CHEM_FUSE_34
         elif mask is False:
             mask = 0
         _check(lib().chem_mlp_set_fusion(self.handle, int(mask)))

@@ -259,12 +259,6 @@ int gemm_linear_grouped(int bn, const GemmOperand &X, const GemmOperand &W, int 
 int gemm_gelu_grad_grouped(int bn, const GemmOperand &X, const GemmOperand &W, int G, int M, int N, int K,
                            const float *z, int64_t ldz, int64_t g_z, void *out, int64_t ldo, int64_t g_out, int *err,
                            cudaStream_t st, int max_ctas = 0);
-// The network's first two hidden layers in one launch, h1 kept on chip (gemm_fused.cuh):
-// h2 = bf16(GELU(bf16(GELU(X W1^T + b1)) W2^T + b2)), bitwise the result of gemm_gelu for layer 1
-// then layer 2. X [M][ldx] BF16 with K1 = 64 columns, W1 [N1][ldw1], W2 [N2][ldw2] (K = N1).
-bool fused12_supported(int K1, int N1, int N2);
-int gemm_fused12(const void *X, int64_t ldx, int K1, const void *W1, int64_t ldw1, const void *W2, int64_t ldw2, int M,
-                 int N1, int N2, const float *b1, const float *b2, void *h2, int64_t ldh2, int *err, cudaStream_t st);
 // The last hidden layer and the output layer in one launch, h3 kept on chip (gemm_fused34.cuh):
 // u = bf16(GELU(X W3^T + b3)) W4^T + b4 in FP32, bitwise gemm_gelu (layer 3) then gemm_linear
 // (layer 4). X [M][ldx] BF16 with K3 columns, W3 [N3][ldw3], W4 [N4][ldw4] (K = N3), u [M][ldu].

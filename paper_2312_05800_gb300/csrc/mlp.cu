@@ -26,6 +26,12 @@ namespace chemgb {
 namespace {
 
 constexpr int kLayers = 4;
+// The first layer's input rows carry three BF16 terms, [z_hi | z_lo | z_hi], against the weight
+// rows [W_hi | W_hi | W_lo] (hi = bf16(v), lo = bf16(v - hi)): z W^T to about 2^-16 relative in
+// both factors (the z_lo W_lo term, ~2^-18, is dropped). Measured on trained networks, rounding
+// the first layer's weights to one BF16 term moved dY by up to 5e-4 relative, the largest single
+// rounding point of the forward.
+constexpr int kXTerms = 3;
 constexpr int kOodMaxBins = 64;
 constexpr int kOodMaxGrids = 2;     // grids of the out-of-distribution test (a cell must pass all)
 constexpr int kOodBlocks = 512;
@@ -47,11 +53,11 @@ struct Layer {
     int in, out;          // logical widths (an ensemble: in per network, out over all networks)
     int gout;             // output width of one network (out / G)
     int kin;              // padded input width (row length of W, multiple of 8)
-    int kx;               // forward GEMM K and row length of Wb: 2 kin for the first layer, whose
-                          // input is carried as two BF16 terms (hi + lo), else kin
+    int kx;               // forward GEMM K and row length of Wb: kXTerms kin for the first layer
+                          // (input and weights as hi + lo BF16 terms), else kin
     int outp;             // padded output width (multiple of 8)
     float *W, *b;         // FP32 master [out][kin], [outp]
-    __nv_bfloat16 *Wb;    // BF16 [out][kx] (the first layer: [W | W] for the hi and lo input terms)
+    __nv_bfloat16 *Wb;    // BF16 [out][kx] (the first layer: [W_hi | W_hi | W_lo], see kXTerms)
     __nv_bfloat16 *Wt;    // BF16 transposed [in][outp]
     float *mW, *vW, *mb, *vb;   // Adam moments
     float *gW, *gb;       // gradients of the last training step
@@ -103,7 +109,6 @@ struct chem_mlp {
     int device;
     uint64_t seed;
     uint32_t wait_limit;                    // tries of each GEMM pipeline wait (chem_mlp_set_wait_limit)
-    int fuse12;                             // layers 1 and 2 of the BF16 forward in one launch (where supported)
     int fuse34;                             // layers 3 and 4 of the BF16 forward in one launch (where supported)
     // physics terms of the training loss (chem_mlp_set_physics_loss): weights and scales, and the
     // mechanism's FP32 NASA-7 enthalpy rows [2][N][6] and 1/W [N] for the heat release
@@ -121,8 +126,8 @@ namespace {
 
 // Rows z = (x - mu) / sigma, x = (T, p, F(Y_1..Y_N)), F(Y) = (max(Y,0)^0.1 - 1)/0.1, each value as
 // two BF16 terms z = hi + lo (hi = bf16(z), lo = bf16(z - hi): 16 significant bits, so the state
-// reaches the first layer at about 2^-17 relative instead of BF16's 2^-9). Row layout:
-// [hi(0 .. n_in_pad) | lo(0 .. n_in_pad)]; padding columns are 0.
+// reaches the first layer at about 2^-17 relative instead of BF16's 2^-9). Row layout (kXTerms):
+// [hi(0 .. n_in_pad) | lo(0 .. n_in_pad) | hi(0 .. n_in_pad)]; padding columns are 0.
 __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict__ T, const double *__restrict__ p,
                                 const double *__restrict__ Y, const int32_t *__restrict__ idx, int N, int n_in_pad,
                                 const float *__restrict__ mu, const float *__restrict__ isd,
@@ -130,7 +135,7 @@ __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t c = idx ? (int64_t)idx[i] : i;
-    __nv_bfloat16 *row = out + i * 2 * n_in_pad;
+    __nv_bfloat16 *row = out + i * kXTerms * n_in_pad;
     for (int j0 = 0; j0 < n_in_pad; j0 += 8) {
         __align__(16) __nv_bfloat16 hi[8], lo[8];
 #pragma unroll
@@ -151,6 +156,7 @@ __global__ void prologue_kernel(int64_t n, int64_t ld, const double *__restrict_
         }
         *reinterpret_cast<uint4 *>(row + j0) = *reinterpret_cast<const uint4 *>(hi);
         *reinterpret_cast<uint4 *>(row + n_in_pad + j0) = *reinterpret_cast<const uint4 *>(lo);
+        *reinterpret_cast<uint4 *>(row + 2 * n_in_pad + j0) = *reinterpret_cast<const uint4 *>(hi);
     }
 }
 
@@ -586,7 +592,10 @@ __global__ void adam_kernel(int out, int in, int kin, int kx, int outp, float *_
         W[q] = w;
         const __nv_bfloat16 wb = __float2bfloat16_rn(w);
         Wb[(int64_t)o * kx + k] = wb;
-        if (kx != kin) Wb[(int64_t)o * kx + kin + k] = wb;   // the lo-term copy of the first layer
+        if (kx != kin) {                                      // the first layer: [W_hi | W_hi | W_lo]
+            Wb[(int64_t)o * kx + kin + k] = wb;
+            Wb[(int64_t)o * kx + 2 * kin + k] = __float2bfloat16_rn(w - __bfloat162float(wb));
+        }
         Wt[(int64_t)k * outp + o] = wb;
     } else if (t < nW + out) {
         const int o = (int)(t - nW);
@@ -605,9 +614,13 @@ __global__ void refresh_bf16_kernel(int out, int in, int kin, int kx, int outp, 
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)out * kin) return;
     const int o = (int)(t / kin), k = (int)(t % kin);
-    const __nv_bfloat16 wb = __float2bfloat16_rn(k < in ? W[t] : 0.0f);
+    const float w = k < in ? W[t] : 0.0f;
+    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
     Wb[(int64_t)o * kx + k] = wb;
-    if (kx != kin) Wb[(int64_t)o * kx + kin + k] = wb;
+    if (kx != kin) {                                          // the first layer: [W_hi | W_hi | W_lo]
+        Wb[(int64_t)o * kx + kin + k] = wb;
+        Wb[(int64_t)o * kx + 2 * kin + k] = __float2bfloat16_rn(w - __bfloat162float(wb));
+    }
     if (k < in) Wt[(int64_t)k * outp + o] = wb;
 }
 
@@ -887,9 +900,6 @@ PhysLoss phys_loss(const chem_mlp *m) {
 
 // whether the BF16 forward runs layers 1 and 2 as one fused launch (multi-output network, the
 // first layer's K of 64 and widths the fused kernel takes)
-bool fused12_on(const chem_mlp *m) {
-    return m->fuse12 && !m->ens && fused12_supported(m->L[0].kx, m->L[0].out, m->L[1].out);
-}
 // the same for layers 3 and 4 (the last hidden layer and the output layer)
 bool fused34_on(const chem_mlp *m) {
     return m->fuse34 && !m->ens && fused34_supported(m->L[2].kx, m->L[2].out, m->L[3].out);
@@ -905,11 +915,11 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
     void *pb = prof_begin(st);
     prologue_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, T, p, Y, nullptr, m->N, m->n_in_pad, m->mu_x,
                                                                  m->isd_x, m->a0);
-    prof_end(pb, st, "prologue_kernel", 0.0, (double)n * ((m->N + 2) * 8 + m->n_in_pad * 4));
+    prof_end(pb, st, "prologue_kernel", 0.0, (double)n * ((m->N + 2) * 8 + m->n_in_pad * 2 * kXTerms));
     int rc = check_cuda(cudaGetLastError(), "prologue");
     if (rc) return rc;
     const void *x = m->a0;
-    int64_t ldx = 2 * m->n_in_pad;
+    int64_t ldx = kXTerms * m->n_in_pad;
     if (m->ens) {
         // the G first layers read the same input: one GEMM over their stacked weights
         const Layer &L0 = m->L[0];
@@ -920,20 +930,9 @@ int forward_chunk(const chem_mlp *m, int64_t n, int64_t ld, const double *T, con
         if (rc || nlayers < kLayers) return rc;
         return ens_output(m, n, m->h[2], m->out, st);
     }
-    int l0 = 0;
-    if (prec == CHEM_PREC_BF16 && nlayers == kLayers && fused12_on(m)) {
-        // layers 1 and 2 in one launch: h1 stays on chip, h2 is written (bitwise the two-launch result)
-        const Layer &L0 = m->L[0], &L1 = m->L[1];
-        rc = gemm_fused12(x, ldx, L0.kx, L0.Wb, L0.kx, L1.Wb, L1.kx, (int)n, L0.out, L1.out, L0.b, L1.b, m->h[1],
-                          L1.out, m->err, st);
-        if (rc) return rc;
-        x = m->h[1];
-        ldx = L1.out;
-        l0 = 2;
-    }
     // layers 3 and 4 in one launch: h3 stays on chip, the outputs are written
     const bool f34 = prec == CHEM_PREC_BF16 && nlayers == kLayers && fused34_on(m);
-    for (int l = l0; l < (f34 ? 2 : 3) && l < nlayers; ++l) {
+    for (int l = 0; l < (f34 ? 2 : 3) && l < nlayers; ++l) {
         const Layer &L = m->L[l];
         if (prec == CHEM_PREC_FP8) {
             const bool f8in = fp8_layer(l), f8out = fp8_layer(l + 1);
@@ -1032,7 +1031,6 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     m->max_batch = desc->max_batch > 0 ? (desc->max_batch + 7) / 8 * 8 : 4096;
     m->seed = seed;
     m->wait_limit = tc::kSpinLimit;
-    m->fuse12 = 1;
     m->fuse34 = 1;
     m->widths[0] = m->n_in;
     for (int i = 0; i < 3; ++i) m->widths[1 + i] = desc->n_hidden[i];
@@ -1045,7 +1043,7 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
         L.gout = (m->ens && l == kLayers - 1) ? 1 : m->widths[l + 1];
         L.out = m->ens ? m->G * L.gout : L.gout;
         L.kin = (int)pad8(L.in);
-        L.kx = (l == 0) ? 2 * L.kin : L.kin;
+        L.kx = (l == 0) ? kXTerms * L.kin : L.kin;
         L.outp = (int)pad8(L.out);
         L.kin8 = (int)pad16(L.in);
         // an ensemble's grouped layers tile one network's width
@@ -1082,12 +1080,12 @@ extern "C" int chem_mlp_create(const chem_mech *mech, const chem_mlp_desc *desc,
     parts.push_back({(void **)&m->out_sp_dev, (size_t)64 * 4});
     parts.push_back({(void **)&m->err, 64});
     const int64_t C = m->chunk, B = m->max_batch;
-    parts.push_back({(void **)&m->a0, (size_t)C * m->n_in_pad * 4});
+    parts.push_back({(void **)&m->a0, (size_t)C * m->n_in_pad * 2 * kXTerms});
     for (int i = 0; i < 3; ++i) parts.push_back({(void **)&m->h[i], (size_t)C * m->L[i].out * 2});
     parts.push_back({(void **)&m->out, (size_t)C * m->n_out_pad * 4});
     int maxw = m->n_in_pad > m->n_out_pad ? m->n_in_pad : m->n_out_pad;
     for (int i = 0; i < 3; ++i) maxw = m->L[i].out > maxw ? m->L[i].out : maxw;
-    parts.push_back({(void **)&m->tx0, (size_t)B * m->n_in_pad * 4});
+    parts.push_back({(void **)&m->tx0, (size_t)B * m->n_in_pad * 2 * kXTerms});
     for (int i = 0; i < 3; ++i) {
         parts.push_back({(void **)&m->th[i], (size_t)B * m->L[i].out * 2});
         parts.push_back({(void **)&m->tz[i], (size_t)B * m->L[i].out * 4});
@@ -1585,7 +1583,7 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
                      float *loss_dev, cudaStream_t st) {
     const int G = m->G;
     const Layer &L0 = m->L[0];
-    int rc = gemm_gelu(L0.tile, m->tx0, 2 * m->n_in_pad, L0.Wb, L0.kx, B, L0.out, L0.kx, L0.b, m->th[0], L0.out,
+    int rc = gemm_gelu(L0.tile, m->tx0, kXTerms * m->n_in_pad, L0.Wb, L0.kx, B, L0.out, L0.kx, L0.b, m->th[0], L0.out,
                        m->tz[0], L0.out, m->err, st);
     for (int l = 1; l < 3 && !rc; ++l) rc = ens_hidden(m, l, m->L[l].tile, B, m->th[l - 1], m->th[l], m->tz[l], st);
     if (!rc) rc = ens_output(m, B, m->th[2], m->tout, st);
@@ -1631,7 +1629,7 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
     // the stacked first layers: one product over all networks (their input is shared)
     transpose_kernel<<<dim3((L0.out + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, L0.out, m->tdz[0], L0.out, m->tT0, B);
     transpose_kernel<<<dim3((m->n_in_pad + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, m->n_in_pad, m->tx0,
-                                                                                  2 * m->n_in_pad, m->tT1, B);
+                                                                                  kXTerms * m->n_in_pad, m->tT1, B);
     if ((rc = check_cuda(cudaGetLastError(), "ensemble transpose"))) return rc;
     rc = gemm_linear(default_tile_width(L0.kin), m->tT0, B, m->tT1, B, L0.out, L0.kin, B, nullptr, L0.gW, L0.kin,
                      m->err, st);
@@ -1666,7 +1664,7 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
         if (rc) return rc;
     } else {
         const __nv_bfloat16 *x = m->tx0;
-        int64_t ldx = 2 * m->n_in_pad;
+        int64_t ldx = kXTerms * m->n_in_pad;
         for (int l = 0; l < 3; ++l) {
             const Layer &L = m->L[l];
             rc = gemm_gelu(L.tile, x, ldx, L.Wb, L.kx, B, L.out, L.kx, L.b, m->th[l], L.out, m->tz[l], L.out, m->err, st);
@@ -1693,7 +1691,7 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
             // the first layer's weight gradient takes the hi input term (BF16 precision suffices for a gradient)
             const __nv_bfloat16 *hin = (l == 0) ? m->tx0 : m->th[l - 1];
             const int wh = (l == 0) ? m->n_in_pad : m->L[l - 1].out;
-            const int ldh = (l == 0) ? 2 * m->n_in_pad : wh;
+            const int ldh = (l == 0) ? kXTerms * m->n_in_pad : wh;
             dim3 tb(32, 8);
             transpose_kernel<<<dim3((lddz + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, lddz, dz, lddz, m->tT0, B);
             transpose_kernel<<<dim3((wh + 31) / 32, (B + 31) / 32), tb, 0, st>>>(B, wh, hin, ldh, m->tT1, B);
@@ -1767,16 +1765,15 @@ extern "C" int chem_mlp_fit_physics_scales(chem_mlp *m, int64_t n, int64_t ld, c
 }
 
 extern "C" int chem_mlp_set_fusion(chem_mlp *m, int mask) {
-    if (!m || mask < 0 || mask > 3)
-        return set_error(CHEM_EINVAL, "chem_mlp_set_fusion: null handle or mask outside 0..3");
-    m->fuse12 = (mask & CHEM_FUSE_12) ? 1 : 0;
+    if (!m || (mask != 0 && mask != CHEM_FUSE_34))
+        return set_error(CHEM_EINVAL, "chem_mlp_set_fusion: null handle or mask other than 0 or CHEM_FUSE_34");
     m->fuse34 = (mask & CHEM_FUSE_34) ? 1 : 0;
     return CHEM_OK;
 }
 
 extern "C" int chem_mlp_get_fusion(const chem_mlp *m) {
     if (!m) return set_error(CHEM_EINVAL, "chem_mlp_get_fusion: null handle");
-    return (fused12_on(m) ? CHEM_FUSE_12 : 0) | (fused34_on(m) ? CHEM_FUSE_34 : 0);
+    return fused34_on(m) ? CHEM_FUSE_34 : 0;
 }
 
 extern "C" int chem_mlp_set_wait_limit(chem_mlp *m, uint32_t tries) {
@@ -1966,7 +1963,7 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
             continue;
         }
         const __nv_bfloat16 *x = (l == 0) ? m->a0 : m->h[l - 1];
-        const int64_t ldx = (l == 0) ? 2 * m->n_in_pad : m->L[l - 1].out;
+        const int64_t ldx = (l == 0) ? kXTerms * m->n_in_pad : m->L[l - 1].out;
         const int width = (m->ens && l > 0) ? L.gout : L.out;    // output columns of one product
         float best = 3.4e38f;
         int best_bn = L.tile;
@@ -2001,23 +1998,6 @@ extern "C" int chem_mlp_autotune(chem_mlp *m, int64_t rows, int32_t *tiles_out, 
         L.tile = best_bn;
         best_ms[l] = best;
         if (tiles_out) tiles_out[l] = best_bn;
-    }
-    // layers 1 and 2 fused into one launch, against the best two-launch pair
-    if (!rc && !m->ens && fused12_supported(m->L[0].kx, m->L[0].out, m->L[1].out)) {
-        const Layer &L0 = m->L[0], &L1 = m->L[1];
-        float ms_sum = 0.0f;
-        for (int rep = 0; rep < 4 && !rc; ++rep) {
-            rc = check_cuda(cudaEventRecord(e0, st), "autotune record");
-            if (!rc)
-                rc = gemm_fused12(m->a0, 2 * m->n_in_pad, L0.kx, L0.Wb, L0.kx, L1.Wb, L1.kx, (int)rows, L0.out, L1.out,
-                                  L0.b, L1.b, m->h[1], L1.out, m->err, st);
-            if (!rc) rc = check_cuda(cudaEventRecord(e1, st), "autotune record");
-            if (!rc) rc = check_cuda(cudaEventSynchronize(e1), "autotune sync");
-            float ms = 0.0f;
-            if (!rc) cudaEventElapsedTime(&ms, e0, e1);
-            if (rep > 0) ms_sum += ms;
-        }
-        if (!rc) m->fuse12 = ms_sum < best_ms[0] + best_ms[1] ? 1 : 0;
     }
     // layers 3 and 4 fused into one launch, against the best two-launch pair
     if (!rc && !m->ens && fused34_supported(m->L[2].kx, m->L[2].out, m->L[3].out)) {

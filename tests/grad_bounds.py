@@ -6,8 +6,9 @@ The device forward and backward round at these points, each a relative error of
 at most 2^-9 (BF16, round to nearest), and otherwise accumulate in FP32, whose
 error over K <= 2048 terms (about K 2^-24 relative) is far below one BF16
 rounding:
-  forward   W -> bf16(W); h_l = bf16(GELU(pre_l)); pre_l in FP32; the network
-            input as two BF16 terms (16 significant bits);
+  forward   W -> bf16(W), the first layer's W as two BF16 terms (16 significant
+            bits); h_l = bf16(GELU(pre_l)); pre_l in FP32; the network input as
+            two BF16 terms (16 significant bits);
   backward  dL/du = sign(u - u*)/B exactly; dX = g bf16(W); g_{l-1} =
             bf16(dX GELU'(pre_{l-1})) with the device's own FP32 pre-activation;
             dW = g^T h with the stored BF16 h (the first layer: the input's hi
@@ -17,7 +18,7 @@ like sqrt(K), not K (probabilistic rounding-error analysis, as in Higham and
 Mary 2019). The helper propagates standard deviations s (each rounding taken
 as s = 2^-9 |value|, above the 2^-9 |value| / sqrt 3 of a uniform error) with
 squares, through the FP64 values of the oracle:
-  s_pre(l)^2 = s_h(l-1)^2 (W_l^2)^T + 2^-18 (h_{l-1}^2)(W_l^2)^T
+  s_pre(l)^2 = s_h(l-1)^2 (W_l^2)^T + r_W (h_{l-1}^2)(W_l^2)^T   (r_W = 2^-18; 2^-32 for l = 1)
   s_h(l)^2   = GELU'(pre_l)^2 s_pre(l)^2 + 2^-18 h_l^2
   s_dX^2     = s_g^2 W^2 + 2^-18 g^2 W^2
   s_g(l-1)^2 = s_dX^2 GELU'^2 + dX^2 GELU''(pre)^2 s_pre^2 + 2^-18 g_{l-1}^2
@@ -54,7 +55,7 @@ def gradients_with_sigma(layers, z, target, sign_from, dout=None):
     for i, (W, b) in enumerate(layers):
         W2 = W * W
         pre = h @ W.T + b
-        vpre = vh @ W2.T + R2 * ((h * h) @ W2.T)
+        vpre = vh @ W2.T + (R2 if i > 0 else 2.0 ** -32) * ((h * h) @ W2.T)
         pres.append(pre)
         vpres.append(vpre)
         if i < nl - 1:

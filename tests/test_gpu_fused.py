@@ -1,15 +1,12 @@
-"""The fused layer pairs (gemm_fused.cuh: layers 1 and 2 with h1 made on chip and
-consumed as layer 2's operand; gemm_fused34.cuh: layers 3 and 4 with h3 made on
-chip and multiplied by the output weights) against the separate launches and
-the oracle.
+"""The fused output layers (gemm_fused34.cuh: layers 3 and 4 with h3 made on chip
+and multiplied by the output weights) against the separate launches and the
+oracle.
 
-* Bitwise: every output of chem_mlp_forward with both fusions equals the
-  output with either one or none (the same BF16 roundings and k order per
-  element), at the paper's widths (two passes of 400 columns), a one-pass
-  first pair, a ragged last pass (h2 = 560: the second pass covers 160
-  columns), a last hidden layer the output fusion does not take (64 units) and
-  a ragged row count over several chunks.
-* chem_step_ann with fusion on matches the oracle as in test_gpu_mlp.py (the
+* Bitwise: every output of chem_mlp_forward with the fusion equals the output
+  without it (the same BF16 roundings and k order per element), at the
+  paper's widths, over one and several chunks with a ragged row count, and a
+  last hidden layer the fusion does not take (64 units: off).
+* chem_mlp_forward with fusion on matches the oracle as in test_gpu_mlp.py (the
   default path of the learned step).
 Weights, statistics and states come from the seeded generator, never from the GPU.
 """
@@ -59,15 +56,16 @@ def test_fused_layers_are_bitwise_the_two_launches(n, hidden, chunk):
     from paper_2312_05800_gb300 import binding
     mech, T, p, Y, widths, layers, stats = _problem(n, hidden, 2071)
     net = _net(widths, layers, stats, chunk=chunk)
-    expect = binding.CHEM_FUSE_12 | (binding.CHEM_FUSE_34 if hidden[2] == 400 else 0)
+    expect = binding.CHEM_FUSE_34 if hidden[2] == 400 else 0
     assert net.fusion == expect
     uf = _u(net, T, p, Y, n)
     k = widths[4]
-    for mask in (0, binding.CHEM_FUSE_12, binding.CHEM_FUSE_34):
-        net.set_fusion(mask)
-        assert net.fusion == mask & expect
-        u2 = _u(net, T, p, Y, n)
-        assert np.array_equal(uf[:, :k], u2[:, :k]), (mask, np.argwhere(uf[:, :k] != u2[:, :k])[:5])
+    net.set_fusion(0)
+    assert net.fusion == 0
+    u2 = _u(net, T, p, Y, n)
+    assert np.array_equal(uf[:, :k], u2[:, :k]), np.argwhere(uf[:, :k] != u2[:, :k])[:5]
+    net.set_fusion(binding.CHEM_FUSE_34)
+    assert net.fusion == expect
     # and against the oracle with the device's BF16 rounding points
     uq = A.forward_u(mech, layers, stats, T[:n], p[:n], Y[:, :n], round_bf16=True)
     rms = np.sqrt(np.mean(uq ** 2))
@@ -80,7 +78,10 @@ def test_fused_layers_are_bitwise_the_two_launches(n, hidden, chunk):
 
 
 def test_fusion_is_off_where_it_does_not_apply():
-    mech, T, p, Y, widths, layers, stats = _problem(256, (600, 200, 96), 2072)    # h1 not a multiple of 64
+    from paper_2312_05800_gb300 import binding
+    mech, T, p, Y, widths, layers, stats = _problem(256, (600, 200, 96), 2072)    # h3 not 400 units
     net = _net(widths, layers, stats)
     assert not net.fused
+    with pytest.raises(binding.ChemError):
+        net.set_fusion(1)                        # only CHEM_FUSE_34 (or 0) is a fusion mask
     net.free()

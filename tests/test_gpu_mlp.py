@@ -122,21 +122,28 @@ def test_step_ann_parity(oracle):
     To, Yo = A.step_ann(mech, layers, stats, T[:n], p[:n], Y[:, :n], round_bf16=True)
     assert np.all(st.cpu().numpy()[:n] == 0)
     assert np.abs(Yg[:, :n].sum(axis=0) - 1).max() < 1e-12 and Yg[:, :n].min() >= 0
-    # the BF16 parity bound on u, carried through dY = sd_u u + mu_u
+    # the forward parity bounds on u (99.95 % within 1e-2 (|u| + rms u), all within 3e-2: a BF16
+    # rounding flip of one hidden unit moves an output by one BF16 step of it), carried through
+    # dY = sd_u u + mu_u
     sd_u = stats[3]
     uq = A.forward_u(mech, layers, stats, T[:n], p[:n], Y[:, :n], round_bf16=True)
-    bdy = (1e-2 * (np.abs(uq) + np.sqrt(np.mean(uq ** 2))) * sd_u).T       # [n_out, n] bound on dY
     sp = A.out_species(mech)
-    # Y' = y / sum(y): an error in any dY moves every species through the sum
-    btot = np.zeros_like(Yo)
-    btot[sp, :] = bdy
-    btot[mech.bath, :] = bdy.sum(axis=0)
-    bound = btot + Yo * 2.0 * bdy.sum(axis=0)[None, :] + 1e-12
     err = np.abs(Yg[:, :n] - Yo)
-    if not np.all(err <= bound):
-        k, i = np.unravel_index(np.argmax(err / bound), err.shape)
+
+    def bound(tol):
+        bdy = (tol * (np.abs(uq) + np.sqrt(np.mean(uq ** 2))) * sd_u).T      # [n_out, n] bound on dY
+        # Y' = y / sum(y): an error in any dY moves every species through the sum
+        btot = np.zeros_like(Yo)
+        btot[sp, :] = bdy
+        btot[mech.bath, :] = bdy.sum(axis=0)
+        return btot + Yo * 2.0 * bdy.sum(axis=0)[None, :] + 1e-12
+
+    b1, b3 = bound(1e-2), bound(3e-2)
+    assert np.mean(err <= b1) >= 0.9995, np.mean(err <= b1)
+    if not np.all(err <= b3):
+        k, i = np.unravel_index(np.argmax(err / b3), err.shape)
         raise AssertionError("%d outside; worst species %d cell %d: %.3g vs bound %.3g"
-                             % ((err > bound).sum(), k, i, err[k, i], bound[k, i]))
+                             % ((err > b3).sum(), k, i, err[k, i], b3[k, i]))
     assert np.all(np.abs(Tg[:n] - To) <= 0.2 + 1e-5 * To), np.abs(Tg[:n] - To).max()
     # nothing past ncells is touched
     assert np.array_equal(Tg[n:], T[n:])
