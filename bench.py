@@ -57,7 +57,10 @@ HIDDEN = {"c2": (1600, 800, 400), "c5": (2048, 1024, 512)}
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of the network's tensor-core launches of one
 # 262,144-cell chunk of the timed step, from one capture of the current kernels; a mechanism without
 # a capture reports null.
-GEMM_CHUNK_TRAFFIC = {}
+# DRAM bytes (read + write) of the network's tensor-core launches for one 262,144-cell chunk (ncu
+# dram__bytes_read.sum + dram__bytes_write.sum of layer 1, layer 2 and the fused layers 3-4; the
+# capture is summarised in profiles/gemm_layers_c2_262k_chunk_traffic.md)
+GEMM_CHUNK_TRAFFIC = {"c2": 2514188800}
 CELLS = {("ann", "c2"): NCELLS_ANN, ("stiff", "c2"): NCELLS, ("ann", "c5"): 16777216, ("stiff", "c5"): 1048576}
 SEED = 2002
 METRIC = "chem+props cells/s at stated dY/T error: ANN (BF16/FP8) vs stiff integrator, 1 GB300"
@@ -487,7 +490,7 @@ def bench_ann(args, rank, world, local):
         ens = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3004, chunk=args.ens_chunk, max_batch=4096, ensemble=True)
         train.fit_norm(ens, data)
         t0 = time.perf_counter()
-        ens_hist = train.train(ens, data, epochs=args.ens_epochs, batch=4096, lr0=args.lr)
+        ens_hist = train.train(ens, data, epochs=args.ens_epochs, batch=4096, lr0=args.ens_lr)
         torch.cuda.synchronize()
         ens_train = {"pairs": args.train_pairs, "epochs": args.ens_epochs, "batch": 4096,
                      "loss_first_epoch": ens_hist[0], "loss_last_epoch": ens_hist[-1],
@@ -1004,8 +1007,9 @@ def main():
                     help="cells per GPU (default 4,194,304 for ann, 2,097,152 for stiff); smaller values only for "
                          "profiling captures")
     ap.add_argument("--train-pairs", type=int, default=2097152)
-    ap.add_argument("--epochs", type=int, default=300)
-    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--ens-lr", type=float, default=1e-3, help="first learning rate of the ensemble's training")
     ap.add_argument("--eval-cells", type=int, default=32768)
     ap.add_argument("--stiff-sample", type=int, default=262144)
     ap.add_argument("--ood-kmin", type=int, default=1,
