@@ -241,14 +241,11 @@ __global__ void __launch_bounds__(128, (NMAX <= 32 ? 8 : 4)) epilogue_kernel(int
     const float *ur = u + i * ldu;
     const float T0 = (float)T[i];
     const int r0 = (T0 >= T_mid) ? 1 : 0;
-    float yf[NMAX];
     float sum = 0.0f, h0 = 0.0f;
 #pragma unroll
     for (int k = 0; k < NMAX; ++k) {
-        yf[k] = 0.0f;
         if (k < N) {
             const float y = f64_to_f32_trunc(Y[(int64_t)k * ld + i]);
-            yf[k] = y;
             float d = 0.0f;
             if (k != bath) {
                 const int j = (k < bath) ? k : k - 1;   // outputs: the non-bath species, ascending
@@ -279,32 +276,56 @@ __global__ void __launch_bounds__(128, (NMAX <= 32 ? 8 : 4)) epilogue_kernel(int
         return;
     }
     dyS[bath][t] = -sum;
-    float s = 0.0f;
+    // Newton on h(T', Y') = h0 with Y' = max(Y + dY, 0) / sum. The mixture's cp/R and H/R are
+    // polynomials in T whose coefficients are sum_k (Y'_k / W_k) a_k: formed once per cell for the
+    // range in use (again, from the state and dY, only if T' crosses T_mid), so that an iteration
+    // is two polynomial evaluations instead of a pass over the species' NASA rows. The provisional
+    // Y' is not kept: the state is re-read from cache.
+    float mc[5], mh[6];
+    auto mix = [&](int rg) {
 #pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-        if (k < N) {
-            yf[k] = fmaxf(yf[k] + dyS[k][t], 0.0f);
-            s += yf[k];
-        }
-    }
-    const float invs = 1.0f / s;
-    float Tn = T0;
-    for (int it = 0; it < 30; ++it) {
-        const int rg = (Tn >= T_mid) ? 1 : 0;
-        float h1 = 0.0f, c1 = 0.0f;
+        for (int j = 0; j < 5; ++j) mc[j] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) mh[j] = 0.0f;
+        float s = 0.0f;
 #pragma unroll
         for (int k = 0; k < NMAX; ++k) {
             if (k < N) {
+                const float y = fmaxf(f64_to_f32_trunc(Y[(int64_t)k * ld + i]) + dyS[k][t], 0.0f);
+                s += y;
                 const float4 *q = tab + (rg * NMAX + k) * 3;
                 const float4 q0 = q[0], q1 = q[1], q2 = q[2];
-                const float c = fmaf(fmaf(fmaf(fmaf(q1.x, Tn, q0.w), Tn, q0.z), Tn, q0.y), Tn, q0.x);
-                float hh = fmaf(fmaf(fmaf(fmaf(q2.y, Tn, q2.x), Tn, q1.w), Tn, q1.z), Tn, q1.y);
-                hh = hh * Tn + q2.z;
-                const float yw = yf[k] * invs * q2.w;
-                h1 = fmaf(yw, hh, h1);
-                c1 = fmaf(yw, c, c1);
+                const float yw = y * q2.w;
+                mc[0] = fmaf(yw, q0.x, mc[0]);
+                mc[1] = fmaf(yw, q0.y, mc[1]);
+                mc[2] = fmaf(yw, q0.z, mc[2]);
+                mc[3] = fmaf(yw, q0.w, mc[3]);
+                mc[4] = fmaf(yw, q1.x, mc[4]);
+                mh[0] = fmaf(yw, q1.y, mh[0]);
+                mh[1] = fmaf(yw, q1.z, mh[1]);
+                mh[2] = fmaf(yw, q1.w, mh[2]);
+                mh[3] = fmaf(yw, q2.x, mh[3]);
+                mh[4] = fmaf(yw, q2.y, mh[4]);
+                mh[5] = fmaf(yw, q2.z, mh[5]);
             }
         }
+        const float invs = 1.0f / s;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) mc[j] *= invs;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) mh[j] *= invs;
+    };
+    float Tn = T0;
+    int rc = -1;
+    for (int it = 0; it < 30; ++it) {
+        const int rg = (Tn >= T_mid) ? 1 : 0;
+        if (rg != rc) {
+            mix(rg);
+            rc = rg;
+        }
+        const float c1 = fmaf(fmaf(fmaf(fmaf(mc[4], Tn, mc[3]), Tn, mc[2]), Tn, mc[1]), Tn, mc[0]);
+        float h1 = fmaf(fmaf(fmaf(fmaf(mh[4], Tn, mh[3]), Tn, mh[2]), Tn, mh[1]), Tn, mh[0]);
+        h1 = fmaf(h1, Tn, mh[5]);
         const float d = (h1 - h0) / c1;        // both in units of R
         Tn -= d;
         if (fabsf(d) < 1e-4f) break;
