@@ -193,6 +193,9 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) 
             const real *d3 = dif + (3 * N + k) * Np;
             const real *d4 = dif + (4 * N + k) * Np;
             real a0 = 0, ds = 0, gs = 0;
+            [[maybe_unused]] uint64_t a02 = 0, ds2 = 0, gs2 = 0;       // FP32: (even j, odd j) sums
+            [[maybe_unused]] const uint64_t rk2 = sizeof(real) == 4 ? pk2(float(rk), float(rk)) : 0;
+            [[maybe_unused]] const uint64_t x2 = sizeof(real) == 4 ? pk2(float(x), float(x)) : 0;
 #pragma unroll
             for (int j4 = 0; j4 < NMAX; j4 += 4) {
                 if (j4 < N) {
@@ -216,17 +219,47 @@ __global__ void __launch_bounds__(128, sizeof(real) == 4 && NMAX <= 32 ? 4 : 1) 
                         load4(d3 + j4, g3[0], g3[1], g3[2], g3[3]);
                         load4(d4 + j4, g4[0], g4[1], g4[2], g4[3]);
                     }
+                    if constexpr (sizeof(real) == 4) {
+                        // two species j at a time on the packed FP32x2 pipe (even and odd j summed
+                        // apart, joined after the loop)
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int j = j4 + u;   // padded columns have zero weights
-                        // Phi_kj = T0 + t (T1 + t T2) with t = r_k / r_j
-                        const real t = ir[j] * rk;
-                        a0 = fma(fma(t, fma(t, w2[u], w1[u]), w0[u]), X[j], a0);
-                        real g = fma(fma(fma(fma(g4[u], x, g3[u]), x, g2[u]), x, g1[u]), x, g0[u]);
-                        ds = fma(g, X[j], ds);
-                        gs += g;
+                        for (int u = 0; u < 4; u += 2) {
+                            const int j = j4 + u;   // padded columns have zero weights
+                            // Phi_kj = T0 + t (T1 + t T2) with t = r_k / r_j
+                            const uint64_t t = mul2(pk2(ir[j], ir[j + 1]), rk2);
+                            const uint64_t phi =
+                                fma2(t, fma2(t, pk2(w2[u], w2[u + 1]), pk2(w1[u], w1[u + 1])), pk2(w0[u], w0[u + 1]));
+                            const uint64_t Xj = pk2(X[j], X[j + 1]);
+                            a02 = fma2(phi, Xj, a02);
+                            uint64_t g = fma2(pk2(g4[u], g4[u + 1]), x2, pk2(g3[u], g3[u + 1]));
+                            g = fma2(g, x2, pk2(g2[u], g2[u + 1]));
+                            g = fma2(g, x2, pk2(g1[u], g1[u + 1]));
+                            g = fma2(g, x2, pk2(g0[u], g0[u + 1]));
+                            ds2 = fma2(g, Xj, ds2);
+                            gs2 = add2(gs2, g);
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int j = j4 + u;   // padded columns have zero weights
+                            // Phi_kj = T0 + t (T1 + t T2) with t = r_k / r_j
+                            const real t = ir[j] * rk;
+                            a0 = fma(fma(t, fma(t, w2[u], w1[u]), w0[u]), X[j], a0);
+                            real g = fma(fma(fma(fma(g4[u], x, g3[u]), x, g2[u]), x, g1[u]), x, g0[u]);
+                            ds = fma(g, X[j], ds);
+                            gs += g;
+                        }
                     }
                 }
+            }
+            if constexpr (sizeof(real) == 4) {
+                float e, o;
+                upk2(a02, e, o);
+                a0 = e + o;
+                upk2(ds2, e, o);
+                ds = e + o;
+                upk2(gs2, e, o);
+                gs = e + o;
             }
             const real den = a0;
             mu = fma(Xk, muk / den, mu);
