@@ -514,6 +514,26 @@ int chem_step_ann_props(const chem_mech *mech, const chem_mlp *mlp, int64_t ncel
 int mlp_train_step(chem_mlp *mlp, int64_t batch, const int32_t *idx, int64_t ld, const double *T, const double *p,
                    const double *Y, const double *Y1, float lr, float *loss_dev, chem_stream_t stream);
 
+/* mlp_train_step in two halves, for data-parallel training (each rank a shard
+ * of the batch, one gradient all-reduce per step between them):
+ *  - mlp_train_grads: the forward, the loss and the back-propagation of
+ *    mlp_train_step (same arguments but lr), leaving dL/dW and dL/db of this
+ *    batch in the handle's gradient buffers;
+ *  - chem_mlp_grad_buffers: device pointers to those buffers for layer 0..3
+ *    (gW: nW floats, the layer's W layout [out][in padded to a multiple of 8];
+ *    gb: nb floats), owned by the handle and valid until it is destroyed, so
+ *    that a collective can reduce them in place. Padding entries are zero;
+ *  - mlp_adam_step: the Adam update of mlp_train_step from the buffers'
+ *    current contents.
+ * mlp_train_grads then mlp_adam_step on one stream is bitwise mlp_train_step.
+ * With the L1 loss of Eq. 5 averaged over the batch, the mean over R ranks of
+ * the gradients of R equal shards is the gradient of the whole batch (up to
+ * the FP32 order of the sums). */
+int mlp_train_grads(chem_mlp *mlp, int64_t batch, const int32_t *idx, int64_t ld, const double *T, const double *p,
+                    const double *Y, const double *Y1, float *loss_dev, chem_stream_t stream);
+int chem_mlp_grad_buffers(const chem_mlp *mlp, int layer, float **gW, int64_t *nW, float **gb, int64_t *nb);
+int mlp_adam_step(chem_mlp *mlp, float lr, chem_stream_t stream);
+
 /* Physics terms of the training loss (Sec. 3.2 adds the principles of
  * mass-fraction unity, energy conservation and heat release to Eq. 5, with no
  * formula or weight; the forms below are this library's reading). For sample

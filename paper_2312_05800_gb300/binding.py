@@ -120,6 +120,10 @@ def lib() -> ctypes.CDLL:
     L.chem_step_ann_props.argtypes = [vp, vp, i64, i64, d, i32, ctypes.POINTER(chem_ode_opts), vp, vp, vp, vp,
                                       vp, vp, vp, vp, vp, vp]
     L.mlp_train_step.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, ctypes.c_float, vp, vp]
+    L.mlp_train_grads.argtypes = [vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
+    L.mlp_adam_step.argtypes = [vp, ctypes.c_float, vp]
+    L.chem_mlp_grad_buffers.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]
     L.chem_prof_enable.argtypes = [i32]
     L.chem_prof_read.argtypes = [ctypes.c_char_p, i64]
     L.chem_last_error.restype = ctypes.c_char_p
@@ -477,6 +481,40 @@ def chem_step_ann_props(mech: Mech, mlp: Mlp, ncells: int, ld: int, dt: float, p
 def mlp_train_step(mlp: Mlp, batch: int, idx, ld: int, T, p, Y, Y1, lr: float, loss=None, stream=None):
     _check(lib().mlp_train_step(mlp.handle, batch, _ptr(idx), ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Y1),
                                 ctypes.c_float(lr), _ptr(loss), _stream(stream)))
+
+
+def mlp_train_grads(mlp: Mlp, batch: int, idx, ld: int, T, p, Y, Y1, loss=None, stream=None):
+    """The forward, loss and back-propagation of mlp_train_step: the batch's gradients in the handle."""
+    _check(lib().mlp_train_grads(mlp.handle, batch, _ptr(idx), ld, _ptr(T), _ptr(p), _ptr(Y), _ptr(Y1), _ptr(loss),
+                                 _stream(stream)))
+
+
+def mlp_adam_step(mlp: Mlp, lr: float, stream=None):
+    """The Adam update of mlp_train_step from the handle's current gradients."""
+    _check(lib().mlp_adam_step(mlp.handle, ctypes.c_float(lr), _stream(stream)))
+
+
+class _DeviceF32:
+    """A float32 device array at a library-owned address (__cuda_array_interface__, no copy)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def grad_buffers(mlp: Mlp):
+    """The handle's gradient buffers as float32 CUDA tensors aliasing its memory, layer by layer
+    [gW_0, gb_0, ..., gW_3, gb_3]: a collective may reduce them in place between mlp_train_grads and
+    mlp_adam_step."""
+    import torch
+    out = []
+    for layer in range(4):
+        gw, nw, gb, nb = ctypes.c_void_p(), ctypes.c_int64(), ctypes.c_void_p(), ctypes.c_int64()
+        _check(lib().chem_mlp_grad_buffers(mlp.handle, layer, ctypes.byref(gw), ctypes.byref(nw), ctypes.byref(gb),
+                                           ctypes.byref(nb)))
+        out.append(torch.as_tensor(_DeviceF32(gw.value, nw.value), device="cuda"))
+        out.append(torch.as_tensor(_DeviceF32(gb.value, nb.value), device="cuda"))
+    return out
 
 
 def chem_prof_enable(on: bool):

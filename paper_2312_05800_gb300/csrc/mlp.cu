@@ -1662,19 +1662,23 @@ int ens_train_passes(chem_mlp *m, int B, const int32_t *idx, int64_t ld, const d
 }  // namespace
 }  // namespace chemgb
 
-extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, int64_t ld, const double *T,
-                              const double *p, const double *Y, const double *Y1, float lr, float *loss_dev,
-                              chem_stream_t stream) {
-    if (!m) return set_error(CHEM_EINVAL, "mlp_train_step: null handle");
+namespace chemgb {
+namespace {
+
+// forward with saved activations, loss (Eq. 5 and the physics terms) and back-propagation: the
+// gradients of one batch in the handle's gW / gb
+int train_grads_impl(chem_mlp *m, int64_t batch, const int32_t *idx, int64_t ld, const double *T, const double *p,
+                     const double *Y, const double *Y1, float *loss_dev, cudaStream_t st, const char *who) {
+    const std::string w(who);
+    if (!m) return set_error(CHEM_EINVAL, w + ": null handle");
     if (batch < 8 || batch > m->max_batch || batch % 8 != 0)
-        return set_error(CHEM_EINVAL, "mlp_train_step: batch must be a multiple of 8 in [8, max_batch]");
-    int rc = check_state_args(idx ? ld : batch, ld, T, p, Y, "mlp_train_step");
+        return set_error(CHEM_EINVAL, w + ": batch must be a multiple of 8 in [8, max_batch]");
+    int rc = check_state_args(idx ? ld : batch, ld, T, p, Y, who);
     if (rc) return rc;
     if (!Y1 || !aligned16(Y1) || (loss_dev && !aligned16(loss_dev)))
-        return set_error(CHEM_EINVAL, "mlp_train_step: Y1 and loss must be 16-byte aligned");
+        return set_error(CHEM_EINVAL, w + ": Y1 and loss must be 16-byte aligned");
     std::string why;
-    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "mlp_train_step: " + why);
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, w + ": " + why);
     WaitLimitScope wl(m->wait_limit);
     const int B = (int)batch;
     // forward with saved pre-activations
@@ -1732,7 +1736,11 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
             }
         }
     }
-    // Adam
+    return CHEM_OK;
+}
+
+// Adam on the gradients in the handle's gW / gb
+int adam_impl(chem_mlp *m, float lr, cudaStream_t st) {
     m->adam_t += 1;
     m->fp8_ready = 0;
     const float bc1 = 1.0f - std::pow(kAdamB1, (float)m->adam_t);
@@ -1744,6 +1752,42 @@ extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, in
                                                                  L.vW, L.mb, L.vb, L.Wb, L.Wt, lr, bc1, bc2);
     }
     return check_cuda(cudaGetLastError(), "train adam");
+}
+
+}  // namespace
+}  // namespace chemgb
+
+extern "C" int mlp_train_step(chem_mlp *m, int64_t batch, const int32_t *idx, int64_t ld, const double *T,
+                              const double *p, const double *Y, const double *Y1, float lr, float *loss_dev,
+                              chem_stream_t stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int rc = train_grads_impl(m, batch, idx, ld, T, p, Y, Y1, loss_dev, st, "mlp_train_step");
+    return rc ? rc : adam_impl(m, lr, st);
+}
+
+extern "C" int mlp_train_grads(chem_mlp *m, int64_t batch, const int32_t *idx, int64_t ld, const double *T,
+                               const double *p, const double *Y, const double *Y1, float *loss_dev,
+                               chem_stream_t stream) {
+    return train_grads_impl(m, batch, idx, ld, T, p, Y, Y1, loss_dev, reinterpret_cast<cudaStream_t>(stream),
+                            "mlp_train_grads");
+}
+
+extern "C" int mlp_adam_step(chem_mlp *m, float lr, chem_stream_t stream) {
+    if (!m) return set_error(CHEM_EINVAL, "mlp_adam_step: null handle");
+    std::string why;
+    if (!device_ok(&why)) return set_error(CHEM_EUNSUPPORTED, "mlp_adam_step: " + why);
+    return adam_impl(m, lr, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int chem_mlp_grad_buffers(const chem_mlp *m, int layer, float **gW, int64_t *nW, float **gb, int64_t *nb) {
+    if (!m || !gW || !nW || !gb || !nb || layer < 0 || layer >= kLayers)
+        return set_error(CHEM_EINVAL, "chem_mlp_grad_buffers: null argument or layer outside 0..3");
+    const Layer &L = m->L[layer];
+    *gW = L.gW;
+    *nW = (int64_t)L.out * L.kin;
+    *gb = L.gb;
+    *nb = (int64_t)L.outp;
+    return CHEM_OK;
 }
 
 extern "C" int chem_mlp_set_physics_loss(chem_mlp *m, double lam_m, double lam_q, double s_m, double s_q) {

@@ -177,3 +177,38 @@ def train(net: binding.Mlp, data: TrainingSet, epochs: int, batch: int = 4096, l
         if step >= total:
             break
     return hist
+
+
+# ---------------------------------------------------------------------------
+# data-parallel training: each rank a shard of every batch, one gradient all-reduce per step
+# ---------------------------------------------------------------------------
+
+def shard_rows(rows, rank: int, world: int):
+    """Rank's contiguous, equal share of a batch's rows (len(rows) a multiple of world)."""
+    n = len(rows) // world
+    if n * world != len(rows):
+        raise ValueError("the batch does not split into %d equal shards" % world)
+    return rows[rank * n:(rank + 1) * n]
+
+
+def allreduce_mean_(tensors, world: int, group=None):
+    """Each tensor summed over the ranks, in place, then divided by world: with Eq. 5 averaged over
+    each shard, the mean over equal shards is the gradient of the whole batch."""
+    import torch.distributed as dist
+    for t in tensors:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+        t.div_(world)
+    return tensors
+
+
+def train_step_dp(net: binding.Mlp, rows, data: TrainingSet, lr: float, rank: int, world: int, loss=None,
+                  group=None):
+    """One data-parallel step: this rank's shard of the batch rows (int32, device) through
+    mlp_train_grads, the mean of the handle's gradient buffers over the ranks (in place), then
+    mlp_adam_step. Ranks that start with the same parameters and Adam state end with the same."""
+    shard = shard_rows(rows, rank, world)
+    binding.mlp_train_grads(net, len(shard), shard, data.ld, data.T, data.p, data.Y, data.Y1, loss)
+    if world > 1:
+        allreduce_mean_(binding.grad_buffers(net), world, group)
+    binding.mlp_adam_step(net, lr)
+
