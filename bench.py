@@ -60,7 +60,9 @@ HIDDEN = {"c2": (1600, 800, 400), "c5": (2048, 1024, 512)}
 # DRAM bytes (read + write) of the network's tensor-core launches for one 262,144-cell chunk (ncu
 # dram__bytes_read.sum + dram__bytes_write.sum of layer 1, layer 2 and the fused layers 3-4; the
 # capture is summarised in profiles/gemm_layers_c2_262k_chunk_traffic.md)
-GEMM_CHUNK_TRAFFIC = {"c2": 2514188800}
+GEMM_CHUNK_TRAFFIC = {"c2": {"gemm_tn_kernel<256> 1600x96": 50694144 + 783133440,
+                              "gemm_tn_kernel<208> 800x1600": 841469696 + 387382784,
+                              "gemm_fused34_kernel 400x800+29x400": 426411008 + 25097728}}
 CELLS = {("ann", "c2"): NCELLS_ANN, ("stiff", "c2"): NCELLS, ("ann", "c5"): 16777216, ("stiff", "c5"): 1048576}
 SEED = 2002
 METRIC = "chem+props cells/s at stated dY/T error: ANN (BF16/FP8) vs stiff integrator, 1 GB300"
@@ -402,12 +404,16 @@ def measured_peak(key: str, fallback: float):
         return fallback, "fallback"
 
 
-def gemm_traffic(chunk: int, ncells: int):
-    """DRAM bytes of the network's tensor-core launches per step, from GEMM_CHUNK_TRAFFIC (one ncu
-    capture of a 262,144-cell chunk of the current kernels), scaled by the cells; None when the
-    current kernels have not been captured for this mechanism."""
+def gemm_traffic(ncells: int, kernel=None):
+    """DRAM bytes from GEMM_CHUNK_TRAFFIC (one ncu capture of a 262,144-cell chunk of the current
+    kernels) scaled to ncells: of one launch kernel, or (kernel None) of all the network's tensor-core
+    launches; None when that launch was not captured for this mechanism."""
     t = GEMM_CHUNK_TRAFFIC.get(MECH)
-    return None if t is None else t * ncells / 262144
+    if t is None:
+        return None
+    if kernel is None:
+        return sum(t.values()) * ncells / 262144
+    return t[kernel] * ncells / 262144 if kernel in t else None
 
 
 def fusion_text(mask: int) -> str:
@@ -435,6 +441,33 @@ def dominant_gemm(dom, ncells: int, chunk: int, widths, peak: float, steps: int)
     achieved = cells_per_launch * per_cell / (avg_ms / 1e3) / 1e12
     return {"kernel": name, "launches": launches, "avg_ms": avg_ms, "cells_per_launch": cells_per_launch,
             "mflop_per_cell": per_cell / 1e6, "achieved": achieved, "frac": achieved / peak}
+
+
+def roofline_line(dom, peak: float, src: str, agg_achieved, agg_traffic, mflop_cell: float, widths, net, gemm):
+    """The roofline object of the step: the dominant (longest) tensor-core launch on its algorithmic
+    flops per launch and its ncu DRAM bytes per launch, with the aggregate of all the network's
+    tensor-core launches (the method's 2 sum fan_in fan_out per cell) beside it."""
+    out = {"bound": "tensor", "achieved": dom["achieved"] if dom else None, "peak": peak, "unit": "TFLOP/s",
+           "frac": dom["frac"] if dom else None,
+           "traffic": gemm_traffic(dom["cells_per_launch"], dom["kernel"]) if dom else None,
+           "traffic_unit": "DRAM bytes (read + write) per launch: ncu dram__bytes of the launch on one "
+                           "262,144-cell chunk, scaled to the launch's cells",
+           "kernel": dom["kernel"] if dom else None, "launches": dom["launches"] if dom else None,
+           "avg_ms": dom["avg_ms"] if dom else None, "cells_per_launch": dom["cells_per_launch"] if dom else None,
+           "work": ("%.4f MFLOP per cell (2 fan_in fan_out of the layer)" % dom["mflop_per_cell"]) if dom else None,
+           "peak_source": src,
+           "mlp_aggregate": {
+               "achieved": agg_achieved, "frac": (agg_achieved / peak) if agg_achieved else None,
+               "traffic": agg_traffic,
+               "traffic_unit": "DRAM bytes (read + write) of the network's tensor-core launches per step",
+               "kernel": "every tensor-core launch of the network per step (%s); CUDA events around each launch"
+                         % fusion_text(net.fusion),
+               "work": "%.4f MFLOP per cell: 2 sum fan_in x fan_out over %s (first layer K = N + 2, not the "
+                       "device's three-term K)" % (mflop_cell, "-".join(str(w) for w in widths)),
+               "per_shape": {k: {"launches": v[0], "ms": v[1],
+                                 "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
+                             for k, v in gemm.items()}}}
+    return out
 
 
 def accuracy(mech, T0, Y0, Ta, Ya, Tr, Yr, n):
@@ -715,6 +748,7 @@ def bench_ann(args, rank, world, local):
     peak, src = measured_peak("bf16_tflops", 1900.0)
     achieved = g_fl / (g_ms / 1e3) / 1e12 if g_ms > 0 else None
     dom = max(gemm.items(), key=lambda kv: kv[1][1]) if gemm else None
+    dom_line = dominant_gemm(dom, ncells, args.chunk, widths, peak, args.steps)
     # ---- the plain method on a sample of the same cells (stiff at the throughput setting + props)
     ns = min(args.stiff_sample, ncells)
     torch.cuda.synchronize()
@@ -852,20 +886,8 @@ def bench_ann(args, rank, world, local):
             "training": {"pairs": args.train_pairs, "epochs": args.epochs, "batch": 4096,
                          "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1], "data_s": t_data,
                          "train_s": t_train},
-            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": gemm_traffic(args.chunk, ncells),
-                         "traffic_unit": "DRAM bytes (read + write) of the network's tensor-core launches per step: "
-                                         "ncu dram__bytes of one 262,144-cell chunk, scaled by the cells",
-                         "kernel": "every tensor-core launch of the network per step (%s); CUDA events around "
-                                   "each launch" % fusion_text(net.fusion),
-                         "work": "%.4f MFLOP per cell: 2 sum fan_in x fan_out over %s (first layer K = N + 2, "
-                                 "not the device's hi/lo K)" % (mflop_cell, "-".join(str(w) for w in widths)),
-                         "peak_source": src,
-                         "dominant": dominant_gemm(dom, ncells, args.chunk, widths, peak, args.steps),
-                         "per_shape": {k: {"launches": v[0], "ms": v[1],
-                                           "tflops": v[2] / (v[1] / 1e3) / 1e12 if v[1] > 0 else None}
-                                       for k, v in gemm.items()}},
+            "roofline": roofline_line(dom_line, peak, src, achieved, gemm_traffic(ncells), mflop_cell, widths, net,
+                                      gemm),
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
             "guard": {"ood": not args.untrained,
                       "grid": "64^3 over (T, h/R, Y_s) for s in %s, neighbourhood >= %d; outside any grid -> fallback"
