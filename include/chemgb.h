@@ -310,8 +310,11 @@ int chem_dense_bf16(int64_t M, int N, int K, const void *x, int64_t ldx, const v
  *    layer l is [G * out_l][in_l] (network g's rows after network g - 1's), b
  *    is [G * out_l]; with out_3 = 1 the last layer is [G][h3], [G].
  * Layers run on the tensor cores in BF16 with FP32 accumulation; parameters
- * are kept in FP32. The bath species is closed by mass conservation
- * (dY_bath = -sum dY_k).
+ * are kept in FP32. The first layer carries its input and its weights as two
+ * BF16 terms each (hi = bf16(v), lo = bf16(v - hi)) and multiplies
+ * z_hi W_hi + z_lo W_hi + z_hi W_lo, so the state and the first layer's
+ * weights enter at about 16 significant bits. The bath species is closed by
+ * mass conservation (dY_bath = -sum dY_k).
  */
 typedef struct chem_mlp chem_mlp;
 
