@@ -737,9 +737,9 @@ def bench_ann(args, rank, world, local):
         ens.free()
     total_s = max_over_ranks(ev[0].elapsed_time(ev[1]) / 1e3, world)
     value = job_rate(ncells * args.steps, world, total_s)
-    # every tensor-core launch of the network (the fused first two layers and the two-launch
-    # layers); the work is the method's: 2 sum fan_in fan_out per cell with the first layer's true
-    # K of N + 2 inputs (the device's hi/lo input split doubles K but is not the method's work)
+    # every tensor-core launch of the network (single layers and the fused output layers); the work
+    # is the method's: 2 sum fan_in fan_out per cell with the first layer's true K of N + 2 inputs
+    # (the device's three-term first layer triples K but is not the method's work)
     gemm = {k: v for k, v in prof.items() if k.startswith("gemm_")}
     g_ms = sum(v[1] for v in gemm.values())
     widths = [N + 2, *hidden, N - 1]
