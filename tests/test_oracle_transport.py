@@ -6,7 +6,8 @@ W and viscosity mix to that viscosity; the off-diagonal Wilke weights, recovered
 from binary-mixture viscosities, obey Wilke's reciprocity and reproduce the
 conductivity, which mixes with the same weights; the binary mixture-averaged diffusion
 coefficient has a closed form in the binary coefficient; D scales as 1/p while
-mu and lambda do not depend on p; and the fitted species values stay within the
+mu and lambda do not depend on p; a monatomic gas has the kinetic-theory conductivity
+(15/4) mu R / W; and the fitted species values stay within the
 fit residual of the raw Chapman-Enskog expressions the fits were made from.
 """
 import numpy as np
@@ -34,6 +35,19 @@ def test_pure_species_limits(oracle):
             cpR = oracle.species_thermo(m, k, T)[0]
             assert abs(mu[i] - muk) <= 1e-13 * muk
             assert abs(lam[i] - muk * (cpR + 1.25) * synth.R_GAS / m.W[k]) <= 1e-12 * lam[i]
+
+
+def test_monatomic_conductivity_is_the_kinetic_theory_value(oracle):
+    # For a monatomic gas (cp = 5R/2 per mole) the first Chapman-Enskog approximation gives
+    # lambda = (15/4) mu R / W, a textbook result independent of the Eucken form the oracle
+    # uses for every species; the two coincide here.
+    vis = np.array([-10.7, 0.7, -0.03, 0.002, 0.0])
+    m = tiny_mech([(2.5, 0.0, 18.0), (2.5, 0.0, 18.0)], [dict(reac=[0], prod=[1], A=1.0)], W=[0.040, 0.040])
+    m.visc_fit = np.stack([vis, vis])
+    Ts = np.array([300.0, 1200.0, 2500.0])
+    Y = np.array([[1.0, 0.4, 0.0], [0.0, 0.6, 1.0]])
+    cp, h, mu, lam, Dk = oracle.props(m, Ts, np.full(3, P), Y)
+    assert np.allclose(lam, 3.75 * mu * synth.R_GAS / 0.040, rtol=1e-13, atol=0)
 
 
 def test_equal_species_mix_to_same_viscosity(oracle):
