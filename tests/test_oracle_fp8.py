@@ -11,6 +11,8 @@
   equals the BF16 network to FP32 rounding of the scales: this pins where the
   scales multiply and divide and which operand is transposed. On random
   weights it stays within the E4M3 error level of the FP64 network.
+* The activation scales of the calibration, worked by hand for a network whose
+  hidden activations are its biases' GELUs.
 """
 import numpy as np
 import pytest
@@ -120,3 +122,18 @@ def test_fp8_network_error_level_on_random_weights():
     # two quantised weight matrices and two quantised activations
     rel = np.sqrt(np.mean((u8 - u64) ** 2)) / np.sqrt(np.mean(u64 ** 2))
     assert 1e-4 < rel < 4 * 2.0 ** -4
+
+
+def test_calibration_scales_worked_by_hand():
+    # zero weights: the hidden activations are bf16(GELU(bias)) for every input row.
+    # h1 = bf16(GELU(-9, 4, 2)) = (-0.0, 4.0, 1.953125): GELU(4) = 4 Phi(4) = 3.99987 rounds to 4,
+    # GELU(2) = 1.9545 to the BF16 1.953125 and GELU(-9) is -1e-18; so s1 = fl32(4 / 448), where the
+    # pre-activations' max |.| would have given 9 / 448.
+    # h2 = bf16(GELU(1, -2, 8)) = (0.83984375, -0.0454..., 8.0): s2 = fl32(8 / 448).
+    widths = [5, 3, 3, 2, 1]
+    layers = [(np.zeros((o, i)), np.zeros(o)) for i, o in zip(widths[:-1], widths[1:])]
+    layers[0] = (layers[0][0], np.array([-9.0, 4.0, 2.0]))
+    layers[1] = (layers[1][0], np.array([1.0, -2.0, 8.0]))
+    z = np.random.default_rng(3).normal(size=(7, 5))
+    s = A.calibrate_fp8(layers, z)
+    assert s == [float(np.float32(4.0 / 448.0)), float(np.float32(8.0 / 448.0))]
