@@ -55,3 +55,22 @@ def test_bad_arguments_are_rejected_before_any_device_work(libpath):
     h = ctypes.c_void_p()
     assert L.chem_mech_load_bytes(b"XXXXXXXX", 8, ctypes.byref(h)) == binding.CHEM_EIO
     assert "magic" in binding.chem_last_error()
+
+
+def test_host_defaults_fill_the_structs_the_binding_declares(libpath):
+    """The two host-only default calls write exactly the ctypes layouts of the binding: the header's
+    documented values land in the right fields, and bytes past the end of each struct stay untouched
+    (a C struct larger than its ctypes twin would overwrite them)."""
+    from paper_2312_05800_gb300 import binding
+    L = ctypes.CDLL(libpath)
+    for cls, fn in ((binding.chem_ode_opts, L.chem_ode_opts_default),
+                    (binding.chem_hfrd_params, L.chem_hfrd_params_default)):
+        size = ctypes.sizeof(cls)
+        buf = (ctypes.c_ubyte * (size + 64))(*([0xA5] * (size + 64)))
+        fn.restype = None
+        fn(ctypes.byref(buf))
+        assert bytes(buf[size:]) == b"\xa5" * 64, cls.__name__
+    o = binding.chem_ode_opts()
+    L.chem_ode_opts_default(ctypes.byref(o))
+    # chem_ode_opts' documented defaults
+    assert (o.rtol, o.atol_Y, o.atol_T, o.h0, o.max_steps, o.mode) == (1e-6, 1e-12, 1e-6, 1e-9, 10000, 0)
