@@ -85,6 +85,32 @@ def test_adam_first_step_closed_form():
     assert layers[0]["b"][0] == 0.5
 
 
+def test_adam_constant_gradient_moves_lr_per_step():
+    # with a constant g the bias corrections give m_hat = g and v_hat = g^2 at every t, so each
+    # step moves by lr g / (|g| + eps); a wrong correction exponent drifts away from this
+    layers = [{"W": np.array([[0.0, 0.0]]), "b": np.array([0.0])}]
+    grads = [{"W": np.array([[2.5, -0.01]]), "b": np.array([1.0])}]
+    st = M.adam_init(layers)
+    for _ in range(25):
+        M.adam_step(layers, grads, st, lr=1e-3)
+    g = grads[0]["W"]
+    assert np.allclose(layers[0]["W"], -25e-3 * g / (np.abs(g) + M.ADAM_EPS), rtol=1e-12, atol=0)
+    assert np.isclose(layers[0]["b"][0], -25e-3 / (1.0 + M.ADAM_EPS), rtol=1e-12, atol=0)
+
+
+def test_adam_two_steps_worked_by_hand():
+    # g = +1 then -1, beta1 = 0.9, beta2 = 0.999:
+    # t = 1: m = 0.1, v = 0.001 -> m_hat = 1, v_hat = 1: step -lr / (1 + eps)
+    # t = 2: m = 0.09 - 0.1 = -0.01, v = 0.000999 + 0.001 = 0.001999
+    #        m_hat = -0.01 / (1 - 0.81) = -1/19, v_hat = 0.001999 / (1 - 0.998001) = 1: step +lr / (19 (1 + eps))
+    layers = [{"W": np.array([[0.0]]), "b": np.array([0.0])}]
+    st = M.adam_init(layers)
+    lr = 1e-3
+    M.adam_step(layers, [{"W": np.array([[1.0]]), "b": np.array([0.0])}], st, lr)
+    M.adam_step(layers, [{"W": np.array([[-1.0]]), "b": np.array([0.0])}], st, lr)
+    assert np.isclose(layers[0]["W"][0, 0], -lr * (18.0 / 19.0) / (1.0 + M.ADAM_EPS), rtol=1e-12, atol=0)
+
+
 def test_two_term_bf16_input():
     # the network input is carried as hi + lo BF16 terms: 16 significant bits
     from oracle import ann as A
