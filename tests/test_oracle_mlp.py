@@ -111,6 +111,15 @@ def test_adam_two_steps_worked_by_hand():
     assert np.isclose(layers[0]["W"][0, 0], -lr * (18.0 / 19.0) / (1.0 + M.ADAM_EPS), rtol=1e-12, atol=0)
 
 
+def test_zscore_statistics_by_hand():
+    # per column: the mean and the population standard deviation (divisor n); a constant column
+    # (the 1 atm pressure) gets sigma = 1
+    x = np.array([[5.0, 1.0, -2.0], [5.0, 2.0, 2.0], [5.0, 3.0, -2.0], [5.0, 4.0, 2.0]])
+    mu, sd = M.zscore_stats(x)
+    assert np.array_equal(mu, [5.0, 2.5, 0.0])
+    assert np.allclose(sd, [1.0, np.sqrt(1.25), 2.0], rtol=1e-15, atol=0)
+
+
 def test_two_term_bf16_input():
     # the network input is carried as hi + lo BF16 terms: 16 significant bits
     from oracle import ann as A
