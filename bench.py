@@ -15,7 +15,10 @@ Paths (see --path):
       4,194,304 cells. The network is trained first (untimed) on pairs the GPU
       stiff integrator generates; its error against a tight stiff integration
       is measured on held-out cells and printed with the throughput, beside the
-      plain method (stiff + props) timed on a sample of the same cells.
+      plain method (stiff + props) timed on a sample of the same cells. Side
+      lines, outside the timed region: the random-data generation of Sec. 3.1
+      on the same cells ("hfrd") and one training step at batch 4096 with and
+      without the physics terms ("training_step").
   "stiff": chem_step_stiff (FP64 Rodas3 at rtol 1e-2: of rtol 1e-3, 3e-3, 1e-2,
       3e-2 and 1e-1, the loosest whose error against a tight integration meets
       the learned step's bars, 1e-3 relative on dY of the major species and 2 K,
@@ -470,6 +473,117 @@ def roofline_line(dom, peak: float, src: str, agg_achieved, agg_traffic, mflop_c
     return out
 
 
+def guarded(fn):
+    """A side line of the bench: its result, or the error that stopped it (the headline stays)."""
+    try:
+        return fn()
+    except Exception as e:          # reported in the line, never allowed to end the run
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def bench_hfrd(dm, smech, T, p, Y, T0, p0, Y0, n: int, ld: int, dev, reps: int = 5):
+    """chem_hfrd_perturb (Sec. 3.1: Eq. 1-4, the renormalisation and the Table 1 filter) on the bench's n
+    cells as base states, with seeded uniform draws c in [-1, 1] made on the device: time per launch
+    (CUDA events, after two warm-up launches). Its FP64 work per state, with a power as one exp and one
+    log at 20 flops each (the stiff kernel's convention): Eq. 1-3 12 flops, Eq. 4 42 per non-bath
+    species, the sum and the scaling 2 per non-bath species, the scale factor 2, the element moles 9 per
+    species, the ratios 6: 53 N - 24 flops, about 2 flops per byte of its reads (2N + 5) x 8 and writes
+    (N + 2) x 8 + 1, ten
+    times the FP64 ridge, so the roofline is the FP64 rate; the HBM fraction is reported beside it."""
+    import torch
+    from paper_2312_05800_gb300 import binding, synth
+    N, b = smech.N, smech.bath
+    prm = binding.hfrd_params(T_min=float(T[:n].min()), T_max=float(T[:n].max()), p_min=float(p[:n].min()),
+                              p_max=float(p[:n].max()), Yb_min=float(Y[b, :n].min()), Yb_max=float(Y[b, :n].max()))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2085)
+    c = torch.rand((3 + N, ld), dtype=torch.float64, device=dev, generator=gen) * 2.0 - 1.0
+    T2 = torch.empty(ld, dtype=torch.float64, device=dev)
+    p2 = torch.empty_like(T2)
+    Y2 = torch.empty((N, ld), dtype=torch.float64, device=dev)
+    keep = torch.empty(ld, dtype=torch.uint8, device=dev)
+    chon = synth.element_table(smech)
+    stream = torch.cuda.current_stream(dev)
+
+    def call():
+        binding.chem_hfrd_perturb(dm, prm, chon, n, ld, T0, p0, Y0, c, T2, p2, Y2, keep, stream)
+
+    for _ in range(2):
+        call()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        call()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    per_state = (2 * N + 5) * 8 + (N + 2) * 8 + 1
+    flop_state = 53 * N - 24
+    gbs = n * per_state / (ms / 1e3) / 1e9
+    hbm, hbm_src = measured_peak("hbm_gbs", 6800.0)
+    tf = n * flop_state / (ms / 1e3) / 1e12
+    return {"value": n / (ms / 1e3), "unit": "states/s", "ms": ms, "launches": reps,
+            "kept_fraction": float(keep[:n].float().mean().item()),
+            "roofline": {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tf / FP64_PEAK_TFLOPS, "flops_per_state": flop_state,
+                         "peak_source": "FP64 nominal: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz", "kernel": "hfrd_kernel",
+                         "hbm": {"achieved_GBps": gbs, "peak_GBps": hbm, "frac": gbs / hbm,
+                                 "bytes_per_state": per_state, "peak_source": hbm_src}},
+            "workload": "chem_hfrd_perturb on the %d bench cells as base states, seeded uniform draws" % n}
+
+
+def bench_train_step(dm, smech, hidden, dev, batch: int = 4096, steps: int = 20, pairs: int = 65536):
+    """mlp_train_step (Sec. 3.2: forward, the Eq. 5 loss, back-propagation, Adam) at the bench's batch on
+    a fresh handle and freshly integrated pairs: ms per step with Eq. 5 alone and with the two physics
+    terms (weights 0.1, scales fitted on the pairs), each after three warm-up steps, CUDA events on the
+    launching stream; the tensor-core rate on the algorithmic flops of a step (the forward product, dW
+    and dX of every layer, the first layer without dX) against the measured BF16 peak."""
+    import torch
+    from paper_2312_05800_gb300 import binding, train
+    data = train.make_training_set(dm, smech, pairs, seed=2107)
+    net = binding.Mlp(dm, hidden=hidden, dt=DT, seed=3007, chunk=pairs, max_batch=batch)
+    try:
+        train.fit_norm(net, data)
+        s_m, s_q = net.fit_physics_scales(data.n, data.ld, data.T, data.Y, data.Y1)
+        loss = torch.zeros(4, dtype=torch.float32, device=dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2108)
+        rows = [torch.randperm(data.n, generator=gen, device=dev)[:batch].to(torch.int32) for _ in range(steps)]
+        stream = torch.cuda.current_stream(dev)
+
+        def timed():
+            for i in range(3):
+                binding.mlp_train_step(net, batch, rows[i], data.ld, data.T, data.p, data.Y, data.Y1, 1e-4, loss)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for i in range(steps):
+                binding.mlp_train_step(net, batch, rows[i], data.ld, data.T, data.p, data.Y, data.Y1, 1e-4, loss)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
+
+        ms_l1 = timed()
+        net.set_physics_loss(0.1, 0.1, s_m, s_q)
+        ms_phys = timed()
+        err = net.error()
+    finally:
+        net.free()
+    widths = [smech.N + 2, *hidden, smech.N - 1]
+    fwd = 2.0 * sum(a * b_ for a, b_ in zip(widths[:-1], widths[1:]))
+    flop = batch * (3.0 * fwd - 2.0 * widths[0] * widths[1])
+    peak, src = measured_peak("bf16_tflops", 1900.0)
+    tf = flop / (ms_l1 / 1e3) / 1e12
+    return {"batch": batch, "steps": steps, "ms_per_step": ms_l1, "ms_per_step_physics_terms": ms_phys,
+            "physics_terms_overhead": ms_phys / ms_l1 - 1.0, "physics_scales": [s_m, s_q], "device_error": err,
+            "mflop_per_sample": flop / batch / 1e6,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "peak_source": src},
+            "workload": "%d GPU-integrated pairs, network %s, one Adam step per batch"
+                        % (pairs, "-".join(str(w) for w in widths))}
+
+
 def accuracy(mech, T0, Y0, Ta, Ya, Tr, Yr, n):
     """Per major species relative L2 of dY, and |T error| max / p99.9, against a reference."""
     import numpy as np
@@ -867,6 +981,9 @@ def bench_ann(args, rank, world, local):
     e2e_value = world * ncells * e2e_steps / (e0.elapsed_time(e1) / 1e3)
     assert all(int((q["ost"][:q["n"]] >= 2).sum()) == 0 for q in parts)
     del parts
+    # ---- the upstream and training rows beside the step (outside the timed region)
+    hfrd_line = guarded(lambda: bench_hfrd(dm, smech, T, p, Y, T0, p0, Y0, ncells, ld, dev))
+    train_line = None if args.untrained else guarded(lambda: bench_train_step(dm, smech, hidden, dev))
     chunks = (ncells + args.chunk - 1) // args.chunk
     line = {"metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -901,6 +1018,8 @@ def bench_ann(args, rank, world, local):
             "ensemble": ens_line,
             "pasr": pasr_line,
             "props_thermo": props_thermo,
+            "hfrd": hfrd_line,
+            "training_step": train_line,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "overlap": "%d parts of the cells; host-to-device and device-to-host copies on two streams "
                                "beside the compute stream" % E2E_PARTS},

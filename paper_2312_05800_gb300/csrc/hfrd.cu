@@ -136,7 +136,8 @@ extern "C" int chem_hfrd_perturb(const chem_mech *m, const chem_hfrd_params *prm
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     void *pb = prof_begin(st);
     hfrd_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, ld, a, m->dev.W, T, p, Y, c, T2, p2, Y2, keep);
-    prof_end(pb, st, "hfrd_kernel", 0.0, (double)n * (8.0 * (2 * m->N + 3 + m->N + 2 + m->N) + 1.0));
+    // algorithmic bytes: reads T, p, Y and the 3 + N draws; writes T', p', Y' and the keep byte
+    prof_end(pb, st, "hfrd_kernel", 0.0, (double)n * (8.0 * ((2 * m->N + 5) + (m->N + 2)) + 1.0));
     return check_cuda(cudaGetLastError(), "chem_hfrd_perturb launch");
 }
 
