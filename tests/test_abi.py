@@ -74,3 +74,11 @@ def test_host_defaults_fill_the_structs_the_binding_declares(libpath):
     L.chem_ode_opts_default(ctypes.byref(o))
     # chem_ode_opts' documented defaults
     assert (o.rtol, o.atol_Y, o.atol_T, o.h0, o.max_steps, o.mode) == (1e-6, 1e-12, 1e-6, 1e-9, 10000, 0)
+
+
+def test_binding_calls_every_declared_entry_point():
+    """The Python binding has a call for every entry point the header declares (no C function is
+    reachable only from C)."""
+    src = open(os.path.join(ROOT, "paper_2312_05800_gb300", "binding.py")).read()
+    missing = [n for n in _declared() if ("lib()." + n) not in src and ("L." + n) not in src]
+    assert not missing, missing
