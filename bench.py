@@ -70,6 +70,7 @@ CELLS = {("ann", "c2"): NCELLS_ANN, ("stiff", "c2"): NCELLS, ("ann", "c5"): 1677
 SEED = 2002
 METRIC = "chem+props cells/s at stated dY/T error: ANN (BF16/FP8) vs stiff integrator, 1 GB300"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FFMA/clk/SM x 2 flop x max SM clock
 
 
 def env_rank():
@@ -479,6 +480,22 @@ def guarded(fn):
         return fn()
     except Exception as e:          # reported in the line, never allowed to end the run
         return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
+def props_full_line(prof, ncells: int, steps: int, N: int):
+    """The full properties pass of the timed steps (cp, h, mu, lambda, D_k) on the FP32 CUDA cores: its
+    algorithmic flops per cell, about 16 N^2 + 30 N (the Wilke pair terms of mu and lambda and the
+    diffusion resistance sums over species pairs, plus the per-species fits), over its time in the
+    library's profiler, against the nominal FP32 rate (no measured FP32 peak is available)."""
+    ms = sum(v[1] for k, v in prof.items() if k.startswith("props_kernel")) / steps
+    if ms <= 0:
+        return None
+    flop = 16 * N * N + 30 * N
+    tf = ncells * flop / (ms / 1e3) / 1e12
+    return {"ms_per_step": ms, "cells_per_launch": ncells,
+            "roofline": {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": tf / FP32_PEAK_TFLOPS, "flops_per_cell": flop, "kernel": "props_kernel",
+                         "peak_source": "FP32 nominal: 152 SM x 128 FMA/clk x 2 x 2.07 GHz"}}
 
 
 def bench_hfrd(dm, smech, T, p, Y, T0, p0, Y0, n: int, ld: int, dev, reps: int = 5):
@@ -1018,6 +1035,7 @@ def bench_ann(args, rank, world, local):
             "ensemble": ens_line,
             "pasr": pasr_line,
             "props_thermo": props_thermo,
+            "props_full": guarded(lambda: props_full_line(prof, ncells, args.steps, N)),
             "hfrd": hfrd_line,
             "training_step": train_line,
             "e2e": {"value": e2e_value, "unit": "cells/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
