@@ -53,3 +53,18 @@ def test_network_flops_per_cell():
     # 2 sum fan_in fan_out over 32-1600-800-400-29: the 3.3256 MFLOP per cell of the aggregate
     mflop = 2.0 * sum(a * b for a, b in zip(WIDTHS[:-1], WIDTHS[1:])) / 1e6
     assert mflop == pytest.approx(3.3256, abs=1e-4)
+
+
+def test_props_full_line():
+    # 10 timed steps, 31.5 ms of props launches: 3.15 ms per step on 16 N^2 + 30 N flops per cell
+    prof = {"props_kernel<f32>": (10, 31.5, 0.0, 0.0), "gemm_tn_kernel<208> 800x1600": (20, 76.0, 0.0, 0.0)}
+    line = bench.props_full_line(prof, 4194304, 10, 30)
+    assert line["ms_per_step"] == pytest.approx(3.15)
+    assert line["roofline"]["flops_per_cell"] == 15300
+    assert line["roofline"]["achieved"] == pytest.approx(4194304 * 15300 / 3.15e-3 / 1e12)
+    assert bench.props_full_line({}, 4194304, 10, 30) is None
+
+
+def test_guarded_keeps_the_error():
+    out = bench.guarded(lambda: 1 / 0)
+    assert out == {"error": "ZeroDivisionError: division by zero"}
